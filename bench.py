@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Benchmark of the McMg online solve on one B300 (or N replicas).
+
+A step is one full solve of the workload to true FP64 relative residual 1e-6:
+restarted flexible GMRES preconditioned by one McMg V-cycle per iteration
+(every row of the hot path: operator, lift, smoothing, restriction,
+prolongation, projection, Krylov orthogonalisation, solution update).
+
+Default workload: 256^2 Gaussian-random-field medium (c in [1, 3], correlation
+16 cells), 8 points per wavelength at c = 1, 16-cell sponge, 4 levels with
+8/16/32/64 channels, FP32 channel mixing, one point source.  Inputs and the
+setup are resident on the device before the timed region; each timed solve
+is bracketed by CUDA events on its stream and L2 is flushed (a 256 MiB write)
+between solves, outside the events.
+
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (a few FGMRES iterations per step, scaled to a
+full solve by the oracle's iteration count).
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s and V-cycles/s to rel. residual 1e-6; p50/p99 solve latency"
+# Iteration cap per workload (the restart length is the workload's FGMRES(m)).
+MAX_ITERS = {"helm2d_n64_homogeneous": 2000, "helm2d_n64_slmg": 2000, "helm2d_n256_grf": 4000,
+             "helm2d_n1024_layers": 8000, "helm3d_n256_grf": 8000}
+FP32_LANES_PER_SM = 128
+NUM_SMS = 148
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="mcmg", choices=["mcmg", "reference"])
+    p.add_argument("--workload", default="helm2d_n256_grf")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-iters", type=int, default=12)
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+            "sm_max_mhz": 2032.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def setup_workload(name):
+    from paper_2606_30495_b300 import inputs as I
+    wl = I.workload(name)
+    c = I.medium_for(wl)
+    omega = I.omega_for_ppw(c.min(), wl["ppw"], wl["n"])
+    w = I.weights_for(wl)
+    return wl, c, omega, w
+
+
+def smooth_flops(C, d, first):
+    """Algorithmic real flops per node of one smoothing launch: complex MACs
+    (8 flops each) of the stencil, K_A, K_S and W^(i); the first pre-step
+    (e = 0) has only K_S and W^(i)."""
+    return 8 * (2 if first else (2 * d + 4)) * C * C
+
+
+def time_smoothing(h, wl, torch, stream, reps=20):
+    """CUDA-event time of every smoothing launch class of one V-cycle, through
+    the C ABI on `stream`.  Returns (total flops, total seconds, launches, detail)."""
+    d = wl["dim"]
+    total_f, total_t, launches = 0.0, 0.0, 0
+    detail = []
+    for l in range(wl["levels"]):
+        C = wl["channels"][l]
+        shp = tuple(n >> l for n in (wl["n"],) * d) + (C,)
+        nodes = math.prod(shp[:-1])
+        r = torch.randn(shp, dtype=torch.complex64, device="cuda")
+        e = torch.randn(shp, dtype=torch.complex64, device="cuda")
+        o = torch.empty_like(e)
+        n_full = wl["nu_pre"][l] + wl["nu_post"][l] - (1 if wl["nu_pre"][l] > 0 else 0)
+        n_first = 1 if wl["nu_pre"][l] > 0 else 0
+        for first, count in ((True, n_first), (False, n_full)):
+            if count == 0:
+                continue
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    h.smooth(l, 0, r, None if first else e, o, stream=stream)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    h.smooth(l, 0, r, None if first else e, o, stream=stream)
+                e1.record(stream)
+            e1.synchronize()
+            per = e0.elapsed_time(e1) / 1e3 / reps
+            fl = smooth_flops(C, d, first) * nodes
+            total_f += fl * count
+            total_t += per * count
+            launches += count
+            detail.append(dict(level=l, C=C, first=first, count=count, us=per * 1e6,
+                               tflops=fl / per / 1e12))
+    return total_f, total_t, launches, detail
+
+
+def oracle_rate(wl, c, omega, w, iters_full, sample_iters):
+    """The FP64 oracle timed on the host: `sample_iters` FGMRES iterations
+    (one V-cycle + Gram-Schmidt each), scaled to a full solve of iters_full."""
+    import numpy as np
+
+    from oracle import mcmg_oracle as O
+    from paper_2606_30495_b300 import inputs as I
+    q = O.wavenumber_coef(c, omega, wl["sponge"], wl["gamma_max"])
+    feats = O.setup(q, w)
+    f = I.point_source(c.shape)
+    t0 = time.perf_counter()
+    O.fgmres(lambda u: O.apply_A(q, u), lambda v: O.vcycle(w, feats, v), f,
+             m=sample_iters + 1, tol=1e-300, max_iters=sample_iters)
+    dt = time.perf_counter() - t0
+    per_iter = dt / sample_iters
+    return dict(per_iter_s=per_iter, solve_s=per_iter * iters_full, wall_s=dt)
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def golden_iters(name):
+    path = os.path.join(ROOT, "tests", "golden", "oracle_solves.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        if name in d:
+            return d[name]["iters"], "oracle"
+    return None, None
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl, c, omega, w = setup_workload(args.workload)
+    iters, src = golden_iters(args.workload)
+    if iters is None:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"no stored oracle iteration count for {args.workload}"}))
+        return
+    k = max(2, args.cpu_sample_iters // 4)
+    for _ in range(args.warmup):
+        oracle_rate(wl, c, omega, w, iters, 1)
+    times = []
+    for _ in range(args.steps):
+        times.append(oracle_rate(wl, c, omega, w, iters, k)["solve_s"])
+    total = sum(times)
+    value = args.steps / total
+    cores = cpu_cores()
+    sample = (f"{k} FGMRES iterations of the FP64 numpy oracle per step, scaled to the "
+              f"oracle's {iters}-iteration solve")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [wl["n"]] * wl["dim"],
+                   "levels": wl["levels"], "channels": wl["channels"]},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    from paper_2606_30495_b300 import build as B
+    B.build()
+    from paper_2606_30495_b300 import inputs as I
+    from paper_2606_30495_b300 import mcmg
+
+    wl, c, omega, w = setup_workload(args.workload)
+    sp = dict(restart=wl["restart"], max_iters=MAX_ITERS[args.workload])
+    prec = mcmg.BF16 if wl["precision"] == "bf16" else mcmg.FP32
+    ctx = mcmg.Context(local)
+    t0 = time.perf_counter()
+    h = mcmg.Handle(ctx, c, omega, wl["sponge"], wl["gamma_max"], w, precision=prec)
+    t_setup = time.perf_counter() - t0
+    shape = c.shape
+    n = int(np.prod(shape))
+    f_host = I.point_source(shape)
+    f = torch.from_numpy(f_host).to("cuda", torch.complex128)
+    u = torch.zeros(shape, dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def solve():
+        with torch.cuda.stream(stream):
+            u.zero_()
+        return h.solve(f, u, tol=wl["tol"], restart_m=sp["restart"], max_iters=sp["max_iters"],
+                       stream=stream)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = Clocks(local)
+    clk.start()
+    launches0 = mcmg.kernel_launches()
+    times, infos = [], []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, info = solve()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        infos.append((st, info))
+    torch.cuda.synchronize()
+    launches = mcmg.kernel_launches() - launches0 - 0
+    clocks = clk.stop()
+    total = sum(times)
+    if world > 1:
+        t = torch.tensor([total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+        dist.barrier()
+    iters = [i["iters"] for _, i in infos]
+    res = max(i["rel_residual"] for _, i in infos)
+    conv = all(i["converged"] for _, i in infos)
+    value = args.steps * world / total
+
+    # final answer checked against the FP64 operator (oracle) on rank 0
+    true_res = None
+    if rank == 0:
+        from oracle import mcmg_oracle as O
+        q = O.wavenumber_coef(c, omega, wl["sponge"], wl["gamma_max"])
+        un = u.cpu().numpy()
+        true_res = float(np.linalg.norm(f_host - O.apply_A(q, un)) / np.linalg.norm(f_host))
+
+    # standalone V-cycle rate (graph replay, steady state)
+    r = torch.randn(shape, dtype=torch.complex64, device="cuda")
+    e = torch.empty_like(r)
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            h.vcycle(r, e, stream=stream)
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        nv = 50
+        for _ in range(nv):
+            h.vcycle(r, e, stream=stream)
+        v1.record(stream)
+    v1.synchronize()
+    vc_s = v0.elapsed_time(v1) / 1e3 / nv
+
+    # dominant kernel: the fused smoothing step (all launch classes of one V-cycle)
+    fl, tsec, nl, detail = time_smoothing(h, wl, torch, stream)
+    pk, pk_src = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2032.0)
+    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    achieved = fl / tsec / 1e12
+
+    # end to end through the C ABI with host buffers (copies inside the call)
+    f_pin = torch.from_numpy(f_host).pin_memory()
+    u_pin = torch.zeros(shape, dtype=torch.complex128).pin_memory()
+    e2e_times = []
+    for k in range(max(2, args.steps // 2)):
+        u_pin.zero_()
+        t1 = time.perf_counter()
+        h.solve_host(f_pin, u_pin, tol=wl["tol"], restart_m=sp["restart"],
+                     max_iters=sp["max_iters"])
+        e2e_times.append(time.perf_counter() - t1)
+    e2e_value = len(e2e_times) * world / sum(e2e_times)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        it_o, src = golden_iters(args.workload)
+        it_o = it_o or int(statistics.median(iters))
+        o = oracle_rate(wl, c, omega, w, it_o, args.cpu_sample_iters)
+        cpu = {"value": 1.0 / o["solve_s"], "unit": "solves/s", "cores": cpu_cores(),
+               "kind": "oracle",
+               "sample": (f"{args.cpu_sample_iters} FGMRES iterations of the FP64 numpy oracle "
+                          f"({o['wall_s']:.1f} s), scaled to a {it_o}-iteration solve"
+                          f" ({'oracle count' if src else 'GPU count'})")}
+
+    lat = sorted(times)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == mcmg.FP32 else "bf16/f32", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [wl["n"]] * wl["dim"],
+                   "levels": wl["levels"], "channels": wl["channels"],
+                   "nu_pre": wl["nu_pre"], "nu_post": wl["nu_post"],
+                   "fgmres_restart": sp["restart"], "tol": wl["tol"],
+                   "l2": "flushed between solves (256 MiB write)", "parallelism": f"replicas{world}"},
+        "vcycles_per_s": sum(iters) * world / total,
+        "vcycles_per_s_standalone": 1.0 / vc_s,
+        "iters_per_solve": iters, "rel_residual_fp64": res, "true_rel_residual_oracle": true_res,
+        "converged": conv,
+        "latency_ms": {"p50": 1e3 * p50, "p99": 1e3 * p99},
+        "setup_s": t_setup,
+        "roofline": {"bound": "alu", "kernel": "k_smooth (fused smoothing step, FP32 FFMA)",
+                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
+                     "detail": detail},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 16 * n * 2,
+                "d2h_bytes_per_step": 16 * n},
+        "peaks_source": pk_src,
+    }
+    if cpu:
+        out["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(out))
+    h.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,866 @@
+// C ABI of the McMg online solve (include/mcmg.h): context and allocation,
+// setup (Algorithm 1), the V-cycle launcher (Algorithm 2, captured once per
+// workspace as a CUDA graph), the synchronous solve and the request server.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstring>
+#include <memory>
+#include <unordered_map>
+
+#include "mcmg_internal.cuh"
+
+// ------------------------------------------------------------------ context --
+struct Request {
+  uint64_t ticket = 0;
+  mcmg_handle_s* h = nullptr;
+  const double2* f = nullptr;
+  double2* u = nullptr;
+  mcmg_solve_opts o{};
+  std::vector<mcmg::Krylov*> kry;   // one per right-hand side
+  std::vector<int> done;
+  cudaStream_t st = nullptr;
+  size_t bytes_needed = 0;
+  std::chrono::steady_clock::time_point t_submit;
+  mcmg_status status = MCMG_PENDING;
+  mcmg_solve_info info{};
+};
+
+struct mcmg_ctx_s {
+  int device = 0;
+  size_t budget = 0;
+  std::atomic<size_t> used{0};
+  // server
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request*> queue;
+  std::vector<Request*> active;
+  std::unordered_map<uint64_t, Request*> finished;
+  uint64_t next_ticket = 1;
+  std::thread worker;
+  bool stop = false;
+  bool running = false;
+  size_t max_queue = 4096;
+};
+
+namespace mcmg {
+
+static thread_local std::string g_last_error;
+std::atomic<unsigned long long> g_launches{0};
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+mcmg_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("CUDA error in %s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? MCMG_ERR_OOM : MCMG_ERR_CUDA;
+}
+
+mcmg_status dev_alloc(mcmg_handle_s* h, DevArena& a, void** p, size_t bytes) {
+  mcmg_ctx_s* c = h->ctx;
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (c->budget) {
+    size_t cur = c->used.load();
+    if (cur + bytes > c->budget) {
+      set_error("HBM budget exhausted: %zu used + %zu requested > %zu", cur, bytes, c->budget);
+      return MCMG_ERR_OOM;
+    }
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "cudaMalloc");
+  }
+  c->used += bytes;
+  a.ptrs.push_back(*p);
+  a.bytes += bytes;
+  return MCMG_OK;
+}
+
+void arena_free(mcmg_handle_s* h, DevArena& a) {
+  for (void* p : a.ptrs) cudaFree(p);
+  if (h && h->ctx) h->ctx->used -= a.bytes;
+  a.ptrs.clear();
+  a.bytes = 0;
+}
+
+// ------------------------------------------------------------ V-cycle work --
+mcmg_status vwork_create(mcmg_handle_s* h, int nrhs, VWork** out) {
+  VWork* w = new VWork();
+  w->nrhs = nrhs;
+  for (int l = 0; l < h->L; ++l) {
+    const Level& L = h->lv[l];
+    size_t b = sizeof(float2) * (size_t)L.g.nodes() * L.C * nrhs;
+    mcmg_status s;
+    if ((s = dev_alloc(h, w->arena, (void**)&w->r[l], b)) ||
+        (s = dev_alloc(h, w->arena, (void**)&w->e[l], b)) ||
+        (s = dev_alloc(h, w->arena, (void**)&w->e2[l], b)) ||
+        (s = dev_alloc(h, w->arena, (void**)&w->t[l], b))) {
+      vwork_destroy(h, w);
+      return s;
+    }
+  }
+  *out = w;
+  return MCMG_OK;
+}
+
+void vwork_destroy(mcmg_handle_s* h, VWork* w) {
+  if (!w) return;
+  if (w->graph) cudaGraphExecDestroy(w->graph);
+  arena_free(h, w->arena);
+  delete w;
+}
+
+// The level sequence of Algorithm 2 on workspace w, nrhs fields, after r_1
+// has been written to w->r[0].  Returns the buffer that holds e_1.
+static mcmg_status enqueue_levels(mcmg_handle_s* h, VWork* w, int nrhs, cudaStream_t st,
+                                  float2** e1_out) {
+  const int L = h->L;
+  float2* ecur[MCMG_MAX_LEVELS];
+  for (int l = 0; l < L; ++l) {                       // down cycle
+    const Level& lv = h->lv[l];
+    float2* cur = nullptr;
+    for (int i = 0; i < lv.nu_pre; ++i) {
+      float2* out = (cur == w->e[l]) ? w->e2[l] : w->e[l];
+      MCMG_TRY(launch_smooth(lv, i, w->r[l], cur, out, 0, nrhs, st));
+      cur = out;
+    }
+    if (!cur) {
+      MCMG_CUDA(cudaMemsetAsync(w->e[l], 0, sizeof(float2) * lv.g.nodes() * lv.C * nrhs, st));
+      cur = w->e[l];
+    }
+    ecur[l] = cur;
+    if (l < L - 1) {                                  // residual + restriction
+      MCMG_TRY(launch_smooth(lv, 0, w->r[l], cur, w->t[l], 1, nrhs, st));
+      MCMG_TRY(launch_restrict(lv, w->t[l], w->r[l + 1], nrhs, st));
+    }
+  }
+  for (int l = L - 2; l >= 0; --l) {                  // up cycle
+    const Level& lv = h->lv[l];
+    MCMG_TRY(launch_prolong_add(lv, ecur[l + 1], ecur[l], nrhs, st));
+    for (int i = 0; i < lv.nu_post; ++i) {
+      float2* out = (ecur[l] == w->e[l]) ? w->e2[l] : w->e[l];
+      MCMG_TRY(launch_smooth(lv, lv.nu_pre + i, w->r[l], ecur[l], out, 0, nrhs, st));
+      ecur[l] = out;
+    }
+  }
+  *e1_out = ecur[0];
+  return MCMG_OK;
+}
+
+static mcmg_status capture_levels(mcmg_handle_s* h, VWork* w) {
+  cudaStream_t cs;
+  MCMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  float2* e1 = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  const unsigned long long before = g_launches.load();
+  mcmg_status s = enqueue_levels(h, w, w->nrhs, cs, &e1);
+  w->graph_kernels = g_launches.load() - before;
+  g_launches.fetch_sub(w->graph_kernels);   // counted when the graph runs
+  e = cudaStreamEndCapture(cs, &graph);
+  cudaStreamDestroy(cs);
+  if (s != MCMG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&w->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  w->e1 = e1;
+  return MCMG_OK;
+}
+
+mcmg_status vcycle_run(mcmg_handle_s* h, VWork* w, const float2* r, float2* e, int nrhs,
+                       cudaStream_t st) {
+  if (nrhs != w->nrhs) {
+    set_error("workspace holds %d fields, call asks for %d", w->nrhs, nrhs);
+    return MCMG_ERR_ARG;
+  }
+  const Level& l0 = h->lv[0];
+  MCMG_TRY(launch_lift(r, h->lift, w->r[0], l0.C, l0.g.nodes(), nrhs, st));
+  if (!w->graph) MCMG_TRY(capture_levels(h, w));
+  MCMG_CUDA(cudaGraphLaunch(w->graph, st));
+  count_launch(w->graph_kernels);
+  MCMG_TRY(launch_project(w->e1, h->proj, e, l0.C, l0.g.nodes(), nrhs, st));
+  return MCMG_OK;
+}
+
+}  // namespace mcmg
+
+using namespace mcmg;
+
+// ------------------------------------------------------------- entry points --
+// (C linkage comes from the declarations in mcmg.h)
+
+const char* mcmg_last_error(void) { return g_last_error.c_str(); }
+const char* mcmg_version(void) { return "mcmg-b300 0.1 (sm_103a)"; }
+uint64_t mcmg_kernel_launches(void) { return g_launches.load(); }
+
+mcmg_status mcmg_ctx_create(int device, size_t hbm_budget_bytes, mcmg_ctx* out) {
+  if (!out) { set_error("out is NULL"); return MCMG_ERR_ARG; }
+  int ndev = 0;
+  MCMG_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) {
+    set_error("device %d out of range (%d devices)", device, ndev);
+    return MCMG_ERR_ARG;
+  }
+  MCMG_CUDA(cudaSetDevice(device));
+  mcmg_ctx_s* c = new mcmg_ctx_s();
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  *out = c;
+  return MCMG_OK;
+}
+
+static void server_stop(mcmg_ctx_s* c);
+
+mcmg_status mcmg_ctx_destroy(mcmg_ctx c) {
+  if (!c) return MCMG_OK;
+  server_stop(c);
+  for (auto& kv : c->finished) delete kv.second;
+  delete c;
+  return MCMG_OK;
+}
+
+mcmg_status mcmg_ctx_memory(mcmg_ctx c, size_t* used) {
+  if (!c || !used) { set_error("NULL argument"); return MCMG_ERR_ARG; }
+  *used = c->used.load();
+  return MCMG_OK;
+}
+
+static bool pow2_channels(int C) {
+  return C == 1 || C == 2 || C == 4 || C == 8 || C == 16 || C == 32 || C == 64;
+}
+
+// Reads the weight blob into device layouts.  See mcmg.h for the order.
+struct BlobReader {
+  const double* p;
+  size_t left;
+  bool ok = true;
+  const double* take(size_t n) {
+    if (n > left) { ok = false; return nullptr; }
+    const double* r = p;
+    p += n;
+    left -= n;
+    return r;
+  }
+};
+
+static std::vector<float> to_f32(const double* src, size_t n) {
+  std::vector<float> v(n);
+  for (size_t i = 0; i < n; ++i) v[i] = (float)src[i];
+  return v;
+}
+
+// complex M[b][co][ci] (nb blocks) -> float2 M^T[b][ci][co]
+static std::vector<float2> transpose_blocks(const double* src, int nb, int co_n, int ci_n) {
+  std::vector<float2> v((size_t)nb * co_n * ci_n);
+  for (int b = 0; b < nb; ++b)
+    for (int co = 0; co < co_n; ++co)
+      for (int ci = 0; ci < ci_n; ++ci) {
+        const double* s = src + 2 * (((size_t)b * co_n + co) * ci_n + ci);
+        v[((size_t)b * ci_n + ci) * co_n + co] = make_float2((float)s[0], (float)s[1]);
+      }
+  return v;
+}
+
+template <typename T>
+static mcmg_status upload(mcmg_handle_s* h, DevArena& a, const std::vector<T>& v, T** out) {
+  MCMG_TRY(dev_alloc(h, a, (void**)out, sizeof(T) * std::max<size_t>(v.size(), 1)));
+  MCMG_CUDA(cudaMemcpy(*out, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return MCMG_OK;
+}
+
+static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
+                              const mcmg_weights* w, mcmg_handle_s* h) {
+  const int d = m->dim;
+  const int L = w->levels;
+  Grid g0;
+  g0.d = d;
+  if (d == 2) { g0.ny = m->n[0]; g0.nx = m->n[1]; g0.nz = 1; }
+  else { g0.nz = m->n[0]; g0.ny = m->n[1]; g0.nx = m->n[2]; }
+  const int T = 2 * d + 1, T3 = d == 3 ? 27 : 9;
+  h->g0 = g0;
+  h->L = L;
+  h->precision = w->precision;
+  // shapes
+  Grid g = g0;
+  for (int l = 0; l < L; ++l) {
+    if (!pow2_channels(w->channels[l])) {
+      set_error("channels[%d] = %d not in {1,2,4,8,16,32,64}", l, w->channels[l]);
+      return MCMG_ERR_SHAPE;
+    }
+    if (g.nx < 2 || g.ny < 2 || (d == 3 && g.nz < 2)) {
+      set_error("level %d grid smaller than 2 nodes per axis", l);
+      return MCMG_ERR_SHAPE;
+    }
+    if (l < L - 1 && ((g.nx | g.ny | (d == 3 ? g.nz : 0)) & 1)) {
+      set_error("level %d grid %dx%dx%d not divisible by 2", l, g.nz, g.ny, g.nx);
+      return MCMG_ERR_SHAPE;
+    }
+    if (w->nu_pre[l] < 0 || w->nu_post[l] < 0 || (l == L - 1 && w->nu_post[l] != 0)) {
+      set_error("bad smoothing counts on level %d", l);
+      return MCMG_ERR_ARG;
+    }
+    h->lv[l].g = g;
+    h->lv[l].C = w->channels[l];
+    h->lv[l].Cn = l < L - 1 ? w->channels[l + 1] : 0;
+    h->lv[l].nu_pre = w->nu_pre[l];
+    h->lv[l].nu_post = w->nu_post[l];
+    g = g.coarse();
+  }
+  // ---- parse the blob
+  BlobReader br{w->blob, w->blob_len};
+  const int C0 = w->channels[0];
+  const double* flw = br.take((size_t)2 * C0 * 2 * T3);
+  const double* flb = br.take((size_t)2 * C0);
+  struct LvBlob { const double *W, *KA, *KS, *Ws, *fsw, *fsb, *R, *P, *faw, *fab; };
+  std::vector<LvBlob> lb(L);
+  for (int l = 0; l < L; ++l) {
+    const int C = w->channels[l];
+    const int ns = w->nu_pre[l] + w->nu_post[l];
+    lb[l].W = br.take((size_t)2 * T * C * C);
+    lb[l].KA = br.take((size_t)2 * C * C);
+    lb[l].KS = br.take((size_t)2 * C * C);
+    lb[l].Ws = br.take((size_t)2 * ns * C * C);
+    lb[l].fsw = br.take((size_t)2 * C * 2 * C * T3);
+    lb[l].fsb = br.take((size_t)2 * C);
+    if (l < L - 1) {
+      const int Cn = w->channels[l + 1];
+      lb[l].R = br.take((size_t)2 * T3 * Cn * C);
+      lb[l].P = br.take((size_t)2 * T3 * C * Cn);
+      lb[l].faw = br.take((size_t)2 * Cn * 2 * C * T3);
+      lb[l].fab = br.take((size_t)2 * Cn);
+    }
+  }
+  const double* gl = br.take((size_t)2 * C0);
+  const double* gp = br.take((size_t)2 * C0);
+  if (!br.ok || br.left != 0) {
+    set_error("weight blob length %zu does not match the model (%s)", w->blob_len,
+              br.ok ? "too long" : "too short");
+    return MCMG_ERR_ARG;
+  }
+  cudaStream_t st = h->stream;
+  // ---- medium -> q
+  const long long N = g0.nodes();
+  DevArena tmp;
+  double* c_dev = nullptr;
+  auto cleanup = [&]() { arena_free(h, tmp); };
+  mcmg_status s;
+  if ((s = dev_alloc(h, tmp, (void**)&c_dev, sizeof(double) * N))) return cleanup(), s;
+  MCMG_CUDA(cudaMemcpy(c_dev, m->c, sizeof(double) * N, cudaMemcpyHostToDevice));
+  if ((s = dev_alloc(h, h->arena, (void**)&h->q32, sizeof(float2) * N))) return cleanup(), s;
+  if ((s = dev_alloc(h, h->arena, (void**)&h->q64, sizeof(double2) * N))) return cleanup(), s;
+  if ((s = launch_make_q(c_dev, omega, m->sponge_width, m->gamma_max, g0, h->q32, h->q64, st)))
+    return cleanup(), s;
+  // ---- weights to device layouts
+  for (int l = 0; l < L; ++l) {
+    Level& lv = h->lv[l];
+    const int C = lv.C, ns = lv.nu_pre + lv.nu_post;
+    if ((s = upload(h, h->arena, transpose_blocks(lb[l].W, T, C, C), &lv.Wt)) ||
+        (s = upload(h, h->arena, transpose_blocks(lb[l].KA, 1, C, C), &lv.KAt)) ||
+        (s = upload(h, h->arena, transpose_blocks(lb[l].KS, 1, C, C), &lv.KSt)) ||
+        (s = upload(h, h->arena, transpose_blocks(lb[l].Ws, std::max(ns, 1), C, C), &lv.Wsmt)))
+      return cleanup(), s;
+    if (l < L - 1) {
+      const int Cn = lv.Cn;
+      if ((s = upload(h, h->arena, transpose_blocks(lb[l].R, T3, Cn, C), &lv.Rt)) ||
+          (s = upload(h, h->arena, transpose_blocks(lb[l].P, T3, C, Cn), &lv.Pt)))
+        return cleanup(), s;
+    }
+    if ((s = dev_alloc(h, h->arena, (void**)&lv.a, sizeof(float2) * lv.g.nodes() * C)) ||
+        (s = dev_alloc(h, h->arena, (void**)&lv.s, sizeof(float2) * lv.g.nodes() * C)))
+      return cleanup(), s;
+  }
+  {
+    std::vector<float2> vl(C0), vp(C0);
+    for (int c2 = 0; c2 < C0; ++c2) {
+      vl[c2] = make_float2((float)gl[2 * c2], (float)gl[2 * c2 + 1]);
+      vp[c2] = make_float2((float)gp[2 * c2], (float)gp[2 * c2 + 1]);
+    }
+    if ((s = upload(h, h->arena, vl, &h->lift)) || (s = upload(h, h->arena, vp, &h->proj)))
+      return cleanup(), s;
+  }
+  // ---- Algorithm 1 on the device
+  float *m_in = nullptr, *net_a = nullptr, *net_s = nullptr, *net_n = nullptr;
+  float *fw = nullptr, *fb = nullptr;
+  if ((s = dev_alloc(h, tmp, (void**)&m_in, sizeof(float) * 2 * N))) return cleanup(), s;
+  if ((s = launch_setup_input(h->q64, m_in, g0, st))) return cleanup(), s;
+  {
+    std::vector<float> wv = to_f32(flw, (size_t)2 * C0 * 2 * T3), bv = to_f32(flb, 2 * C0);
+    if ((s = upload(h, tmp, wv, &fw)) || (s = upload(h, tmp, bv, &fb))) return cleanup(), s;
+    if ((s = dev_alloc(h, tmp, (void**)&net_a, sizeof(float) * 2 * C0 * N))) return cleanup(), s;
+    if ((s = launch_conv3_gelu(m_in, 2, net_a, 2 * C0, fw, fb, g0, 1, st))) return cleanup(), s;
+  }
+  double2* ql = h->q64;
+  for (int l = 0; l < L; ++l) {
+    Level& lv = h->lv[l];
+    const int C = lv.C;
+    const long long nl = lv.g.nodes();
+    std::vector<float> sw = to_f32(lb[l].fsw, (size_t)2 * C * 2 * C * T3), sb = to_f32(lb[l].fsb, 2 * C);
+    float *dsw, *dsb;
+    if ((s = upload(h, tmp, sw, &dsw)) || (s = upload(h, tmp, sb, &dsb))) return cleanup(), s;
+    if ((s = dev_alloc(h, tmp, (void**)&net_s, sizeof(float) * 2 * C * nl))) return cleanup(), s;
+    if ((s = launch_conv3_gelu(net_a, 2 * C, net_s, 2 * C, dsw, dsb, lv.g, 1, st)))
+      return cleanup(), s;
+    if ((s = launch_assemble_features(net_a, net_s, ql, lv.a, lv.s, C, lv.g, l, w->feat_sl,
+                                      w->feat_eps, w->sl_shift_re, w->sl_shift_im, st)))
+      return cleanup(), s;
+    if (l < L - 1) {
+      const int Cn = lv.Cn;
+      const Grid gc = lv.g.coarse();
+      std::vector<float> aw = to_f32(lb[l].faw, (size_t)2 * Cn * 2 * C * T3), ab = to_f32(lb[l].fab, 2 * Cn);
+      float *daw, *dab;
+      if ((s = upload(h, tmp, aw, &daw)) || (s = upload(h, tmp, ab, &dab))) return cleanup(), s;
+      if ((s = dev_alloc(h, tmp, (void**)&net_n, sizeof(float) * 2 * Cn * gc.nodes())))
+        return cleanup(), s;
+      if ((s = launch_conv3_gelu(net_a, 2 * C, net_n, 2 * Cn, daw, dab, lv.g, 2, st)))
+        return cleanup(), s;
+      double2* qn;
+      if ((s = dev_alloc(h, tmp, (void**)&qn, sizeof(double2) * gc.nodes()))) return cleanup(), s;
+      if ((s = launch_fw_restrict_q(ql, qn, lv.g, st))) return cleanup(), s;
+      ql = qn;
+      net_a = net_n;
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "setup");
+  return MCMG_OK;
+}
+
+mcmg_status mcmg_setup(mcmg_ctx c, const mcmg_medium* m, double omega, const mcmg_weights* w,
+                       mcmg_handle* out) {
+  if (!c || !m || !w || !out || !m->c || !w->blob) {
+    set_error("NULL argument");
+    return MCMG_ERR_ARG;
+  }
+  if (m->dim != 2 && m->dim != 3) { set_error("dim must be 2 or 3"); return MCMG_ERR_ARG; }
+  if (w->levels < 1 || w->levels > MCMG_MAX_LEVELS) {
+    set_error("levels must be in 1..%d", MCMG_MAX_LEVELS);
+    return MCMG_ERR_ARG;
+  }
+  if (w->precision != MCMG_FP32 && w->precision != MCMG_BF16) {
+    set_error("unknown precision %d", w->precision);
+    return MCMG_ERR_ARG;
+  }
+  for (int a = 0; a < m->dim; ++a)
+    if (m->n[a] < 2) { set_error("grid axis %d too small", a); return MCMG_ERR_SHAPE; }
+  MCMG_CUDA(cudaSetDevice(c->device));
+  mcmg_handle_s* h = new mcmg_handle_s();
+  h->ctx = c;
+  h->device = c->device;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaStreamCreate"); }
+  mcmg_status s = setup_impl(c, m, omega, w, h);
+  if (s != MCMG_OK) {
+    mcmg_destroy(h);
+    return s;
+  }
+  *out = h;
+  return MCMG_OK;
+}
+
+mcmg_status mcmg_destroy(mcmg_handle h) {
+  if (!h) return MCMG_OK;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->kry) krylov_destroy(h, h->kry);
+  if (h->work) vwork_destroy(h, h->work);
+  arena_free(h, h->arena);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return MCMG_OK;
+}
+
+static mcmg_status ensure_work(mcmg_handle_s* h, int nrhs) {
+  if (h->work && h->work->nrhs == nrhs) return MCMG_OK;
+  if (h->work) {
+    MCMG_CUDA(cudaDeviceSynchronize());
+    vwork_destroy(h, h->work);
+    h->work = nullptr;
+  }
+  return vwork_create(h, nrhs, &h->work);
+}
+
+mcmg_status mcmg_vcycle(mcmg_handle h, const void* r, void* e, int nrhs, void* stream) {
+  if (!h || !r || !e || nrhs < 1) { set_error("bad argument"); return MCMG_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(h->mu);
+  MCMG_CUDA(cudaSetDevice(h->device));
+  MCMG_TRY(ensure_work(h, nrhs));
+  return vcycle_run(h, h->work, (const float2*)r, (float2*)e, nrhs, (cudaStream_t)stream);
+}
+
+static mcmg_status check_opts(const mcmg_solve_opts* o) {
+  if (!o || !(o->tol > 0.0) || o->restart_m < 1 || o->nrhs < 1 || o->max_iters < 0) {
+    set_error("bad solve options");
+    return MCMG_ERR_ARG;
+  }
+  return MCMG_OK;
+}
+
+mcmg_status mcmg_solve(mcmg_handle h, const void* f, void* u, const mcmg_solve_opts* o,
+                       mcmg_solve_info* info) {
+  if (!h || !f || !u) { set_error("NULL argument"); return MCMG_ERR_ARG; }
+  MCMG_TRY(check_opts(o));
+  if (o->flags & MCMG_SOLVE_STATIONARY) {
+    set_error("the stationary iteration is not available in this build");
+    return MCMG_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(h->mu);
+  MCMG_CUDA(cudaSetDevice(h->device));
+  if (h->kry && krylov_m(h->kry) != o->restart_m) {
+    krylov_destroy(h, h->kry);
+    h->kry = nullptr;
+  }
+  if (!h->kry) MCMG_TRY(krylov_create(h, o->restart_m, &h->kry));
+  const long long N = h->g0.nodes();
+  mcmg_solve_info agg{};
+  agg.converged = 1;
+  mcmg_status worst = MCMG_OK;
+  auto t0 = std::chrono::steady_clock::now();
+  for (int k = 0; k < o->nrhs; ++k) {
+    cudaStream_t st = o->stream ? (cudaStream_t)o->stream : h->stream;
+    MCMG_TRY(krylov_begin(h->kry, (const double2*)f + (size_t)k * N, (double2*)u + (size_t)k * N,
+                          *o, st));
+    int done = 0;
+    while (!done) MCMG_TRY(krylov_advance(h->kry, true, &done));
+    mcmg_solve_info one;
+    mcmg_status fs;
+    krylov_info(h->kry, &one, &fs);
+    agg.iters = std::max(agg.iters, one.iters);
+    agg.restarts = std::max(agg.restarts, one.restarts);
+    agg.rel_residual = std::max(agg.rel_residual, one.rel_residual);
+    agg.converged &= one.converged;
+    if (fs != MCMG_OK && worst == MCMG_OK) worst = fs;
+  }
+  agg.t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = agg;
+  if (worst == MCMG_ERR_NOT_CONVERGED) set_error("max_iters reached above tolerance");
+  return worst;
+}
+
+mcmg_status mcmg_solve_host(mcmg_handle h, const void* f_host, void* u_host,
+                            const mcmg_solve_opts* o, mcmg_solve_info* info) {
+  if (!h || !f_host || !u_host) { set_error("NULL argument"); return MCMG_ERR_ARG; }
+  MCMG_TRY(check_opts(o));
+  MCMG_CUDA(cudaSetDevice(h->device));
+  const size_t bytes = sizeof(double2) * (size_t)h->g0.nodes() * o->nrhs;
+  DevArena a;
+  void *fd = nullptr, *ud = nullptr;
+  mcmg_status s;
+  if ((s = dev_alloc(h, a, &fd, bytes)) || (s = dev_alloc(h, a, &ud, bytes))) {
+    arena_free(h, a);
+    return s;
+  }
+  cudaError_t e = cudaMemcpyAsync(fd, f_host, bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ud, u_host, bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) { arena_free(h, a); return cuda_fail(e, "copy in"); }
+  s = mcmg_solve(h, fd, ud, o, info);
+  e = cudaMemcpyAsync(u_host, ud, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  arena_free(h, a);
+  if (e != cudaSuccess) return cuda_fail(e, "copy out");
+  return s;
+}
+
+// ---------------------------------------------------------- single steps ----
+static mcmg_status check_level(mcmg_handle h, int level, bool need_next) {
+  if (!h || level < 0 || level >= h->L || (need_next && level >= h->L - 1)) {
+    set_error("level %d out of range", level);
+    return MCMG_ERR_ARG;
+  }
+  return MCMG_OK;
+}
+
+mcmg_status mcmg_apply_A(mcmg_handle h, const void* x, void* y, int fp64, int nrhs, void* stream) {
+  if (!h || !x || !y || nrhs < 1) { set_error("bad argument"); return MCMG_ERR_ARG; }
+  MCMG_CUDA(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (fp64) return launch_apply_A64(h->q64, (const double2*)x, (double2*)y, h->g0, nrhs, st);
+  return launch_apply_A32(h->q32, (const float2*)x, (float2*)y, h->g0, nrhs, st);
+}
+
+mcmg_status mcmg_get_feature(mcmg_handle h, int level, int which, void* out) {
+  MCMG_TRY(check_level(h, level, false));
+  if (!out || (which != 0 && which != 1)) { set_error("bad argument"); return MCMG_ERR_ARG; }
+  const Level& lv = h->lv[level];
+  MCMG_CUDA(cudaMemcpy(out, which == 0 ? lv.a : lv.s, sizeof(float2) * lv.g.nodes() * lv.C,
+                       cudaMemcpyDeviceToDevice));
+  return MCMG_OK;
+}
+
+mcmg_status mcmg_lift(mcmg_handle h, const void* r, void* r1, int nrhs, void* stream) {
+  if (!h || !r || !r1 || nrhs < 1) { set_error("bad argument"); return MCMG_ERR_ARG; }
+  return launch_lift((const float2*)r, h->lift, (float2*)r1, h->lv[0].C, h->g0.nodes(), nrhs,
+                     (cudaStream_t)stream);
+}
+
+mcmg_status mcmg_project(mcmg_handle h, const void* e1, void* e, int nrhs, void* stream) {
+  if (!h || !e1 || !e || nrhs < 1) { set_error("bad argument"); return MCMG_ERR_ARG; }
+  return launch_project((const float2*)e1, h->proj, (float2*)e, h->lv[0].C, h->g0.nodes(), nrhs,
+                        (cudaStream_t)stream);
+}
+
+mcmg_status mcmg_smooth(mcmg_handle h, int level, int step, const void* r, const void* e_in,
+                        void* e_out, int nrhs, void* stream) {
+  MCMG_TRY(check_level(h, level, false));
+  const Level& lv = h->lv[level];
+  if (!r || !e_out || nrhs < 1 || step < 0 || step >= lv.nu_pre + lv.nu_post) {
+    set_error("bad argument");
+    return MCMG_ERR_ARG;
+  }
+  return launch_smooth(lv, step, (const float2*)r, (const float2*)e_in, (float2*)e_out, 0, nrhs,
+                       (cudaStream_t)stream);
+}
+
+mcmg_status mcmg_residual_restrict(mcmg_handle h, int level, const void* r, const void* e,
+                                   void* rc, int nrhs, void* stream) {
+  MCMG_TRY(check_level(h, level, true));
+  if (!r || !e || !rc || nrhs < 1) { set_error("bad argument"); return MCMG_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(h->mu);
+  MCMG_TRY(ensure_work(h, nrhs));
+  const Level& lv = h->lv[level];
+  cudaStream_t st = (cudaStream_t)stream;
+  MCMG_TRY(launch_smooth(lv, 0, (const float2*)r, (const float2*)e, h->work->t[level], 1, nrhs, st));
+  return launch_restrict(lv, h->work->t[level], (float2*)rc, nrhs, st);
+}
+
+mcmg_status mcmg_prolong_add(mcmg_handle h, int level, const void* ec, void* e, int nrhs,
+                             void* stream) {
+  MCMG_TRY(check_level(h, level, true));
+  if (!ec || !e || nrhs < 1) { set_error("bad argument"); return MCMG_ERR_ARG; }
+  return launch_prolong_add(h->lv[level], (const float2*)ec, (float2*)e, nrhs, (cudaStream_t)stream);
+}
+
+mcmg_status mcmg_cgs2(mcmg_handle h, const void* V, int k, size_t n, void* w, double* h_host,
+                      double* norm_host) {
+  if (!h || !V || !w || !h_host || !norm_host || k < 1 || n < 1) {
+    set_error("bad argument");
+    return MCMG_ERR_ARG;
+  }
+  MCMG_CUDA(cudaSetDevice(h->device));
+  return cgs2_once(h, (const float2*)V, k, (long long)n, (float2*)w, h_host, norm_host, h->stream);
+}
+
+// ------------------------------------------------------------------ server --
+// One worker thread.  Admission: queued requests start in arrival order when
+// their Krylov and V-cycle workspaces fit the context's HBM budget.  Every
+// admitted request runs on its own stream; the worker polls each request's
+// last event and enqueues its next FGMRES stage as soon as it completes, so
+// the stages of different requests overlap on the device.
+
+static size_t request_bytes(mcmg_handle_s* h, const mcmg_solve_opts& o) {
+  const size_t n = (size_t)h->g0.nodes();
+  const int m = o.restart_m;
+  size_t b = sizeof(float2) * n * (2 * (size_t)m + 2) + sizeof(double2) * n;
+  for (int l = 0; l < h->L; ++l) b += 4 * sizeof(float2) * (size_t)h->lv[l].g.nodes() * h->lv[l].C;
+  b += sizeof(double2) * (size_t)m * (m + 1) + (size_t)1 << 20;
+  return b * o.nrhs;
+}
+
+static void release(Request* r) {
+  for (auto* k : r->kry) krylov_destroy(r->h, k);
+  r->kry.clear();
+  if (r->st) { cudaStreamDestroy(r->st); r->st = nullptr; }
+}
+
+static bool try_admit(mcmg_ctx_s* c, Request* r) {
+  if (c->budget && c->used.load() + r->bytes_needed > c->budget) return false;
+  if (cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const size_t N = (size_t)r->h->g0.nodes();
+  for (int k = 0; k < r->o.nrhs; ++k) {
+    Krylov* kr = nullptr;
+    mcmg_status s = krylov_create(r->h, r->o.restart_m, &kr);
+    if (s != MCMG_OK) {
+      release(r);
+      cudaGetLastError();
+      return false;
+    }
+    r->kry.push_back(kr);
+    r->done.push_back(0);
+    s = krylov_begin(kr, r->f + k * N, r->u + k * N, r->o, r->st);
+    if (s != MCMG_OK) {
+      r->status = s;
+      return true;
+    }
+  }
+  return true;
+}
+
+static void server_loop(mcmg_ctx_s* c) {
+  cudaSetDevice(c->device);
+  std::unique_lock<std::mutex> lk(c->mu);
+  while (!c->stop) {
+    // admit in arrival order
+    while (!c->queue.empty()) {
+      Request* r = c->queue.front();
+      if (!try_admit(c, r)) {
+        if (c->active.empty()) {   // can never fit: fail it
+          r->status = MCMG_ERR_OOM;
+          c->queue.pop_front();
+          c->finished[r->ticket] = r;
+          continue;
+        }
+        break;
+      }
+      c->queue.pop_front();
+      c->active.push_back(r);
+    }
+    if (c->active.empty()) {
+      c->cv.notify_all();
+      c->cv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
+      continue;
+    }
+    lk.unlock();
+    bool progressed = false;
+    std::vector<Request*> fin;
+    for (Request* r : c->active) {
+      bool all = r->status != MCMG_PENDING;
+      if (!all) {
+        all = true;
+        for (size_t k = 0; k < r->kry.size(); ++k) {
+          if (r->done[k]) continue;
+          int d = 0;
+          mcmg_status s = krylov_advance(r->kry[k], false, &d);
+          if (s != MCMG_OK) { r->status = s; d = 1; }
+          if (d) { r->done[k] = 1; progressed = true; }
+          else all = false;
+        }
+      }
+      if (all) fin.push_back(r);
+    }
+    for (Request* r : fin) {
+      mcmg_solve_info agg{};
+      agg.converged = 1;
+      mcmg_status worst = r->status == MCMG_PENDING ? MCMG_OK : r->status;
+      for (auto* k : r->kry) {
+        mcmg_solve_info one;
+        mcmg_status fs;
+        krylov_info(k, &one, &fs);
+        agg.iters = std::max(agg.iters, one.iters);
+        agg.restarts = std::max(agg.restarts, one.restarts);
+        agg.rel_residual = std::max(agg.rel_residual, one.rel_residual);
+        agg.converged &= one.converged;
+        if (fs != MCMG_OK && worst == MCMG_OK) worst = fs;
+      }
+      if (r->st) cudaStreamSynchronize(r->st);
+      agg.t_solve_s =
+          std::chrono::duration<double>(std::chrono::steady_clock::now() - r->t_submit).count();
+      r->info = agg;
+      r->status = worst;
+      release(r);
+    }
+    lk.lock();
+    for (Request* r : fin) {
+      c->active.erase(std::find(c->active.begin(), c->active.end(), r));
+      c->finished[r->ticket] = r;
+    }
+    if (!fin.empty()) c->cv.notify_all();
+    if (!progressed && fin.empty()) {
+      lk.unlock();
+      std::this_thread::yield();
+      lk.lock();
+    }
+  }
+}
+
+static void server_start(mcmg_ctx_s* c) {
+  if (c->running) return;
+  c->stop = false;
+  c->running = true;
+  c->worker = std::thread(server_loop, c);
+}
+
+static void server_stop(mcmg_ctx_s* c) {
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!c->running) return;
+    c->stop = true;
+  }
+  c->cv.notify_all();
+  c->worker.join();
+  c->running = false;
+  for (Request* r : c->active) { release(r); delete r; }
+  for (Request* r : c->queue) delete r;
+  c->active.clear();
+  c->queue.clear();
+}
+
+mcmg_status mcmg_submit(mcmg_ctx c, mcmg_handle h, const void* f, void* u,
+                        const mcmg_solve_opts* o, uint64_t* ticket) {
+  if (!c || !h || !f || !u || !ticket || h->ctx != c) {
+    set_error("bad argument");
+    return MCMG_ERR_ARG;
+  }
+  MCMG_TRY(check_opts(o));
+  if (o->flags & MCMG_SOLVE_STATIONARY) {
+    set_error("the stationary iteration is not available in this build");
+    return MCMG_ERR_ARG;
+  }
+  Request* r = new Request();
+  r->h = h;
+  r->f = (const double2*)f;
+  r->u = (double2*)u;
+  r->o = *o;
+  r->bytes_needed = request_bytes(h, *o);
+  r->t_submit = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->queue.size() >= c->max_queue) {
+      delete r;
+      set_error("server queue full");
+      return MCMG_ERR_BUSY;
+    }
+    r->ticket = c->next_ticket++;
+    c->queue.push_back(r);
+    *ticket = r->ticket;
+    server_start(c);
+  }
+  c->cv.notify_all();
+  return MCMG_OK;
+}
+
+mcmg_status mcmg_poll(mcmg_ctx c, uint64_t ticket, mcmg_solve_info* info) {
+  if (!c) { set_error("NULL context"); return MCMG_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->finished.find(ticket);
+  if (it == c->finished.end()) {
+    for (Request* r : c->queue)
+      if (r->ticket == ticket) return MCMG_PENDING;
+    for (Request* r : c->active)
+      if (r->ticket == ticket) return MCMG_PENDING;
+    set_error("unknown ticket %llu", (unsigned long long)ticket);
+    return MCMG_ERR_ARG;
+  }
+  Request* r = it->second;
+  if (info) *info = r->info;
+  mcmg_status s = r->status;
+  c->finished.erase(it);
+  delete r;
+  return s;
+}
+
+mcmg_status mcmg_drain(mcmg_ctx c) {
+  if (!c) { set_error("NULL context"); return MCMG_ERR_ARG; }
+  std::unique_lock<std::mutex> lk(c->mu);
+  c->cv.wait(lk, [&] { return c->queue.empty() && c->active.empty(); });
+  return MCMG_OK;
+}

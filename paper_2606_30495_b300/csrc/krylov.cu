@@ -1,0 +1,569 @@
+// Flexible GMRES(m) on the device (the outer iteration of GMRES+McMg,
+// Section 3.3 and Table 2, in Saad's flexible right-preconditioned form).
+//
+// Precision split: the Krylov basis V and the preconditioned vectors Z are
+// complex64 (the V-cycle's input and output precision).  The Arnoldi work
+// vector w = A z_j is formed in FP64 from the complex64 z_j and stays FP64
+// through Gram-Schmidt; every inner product and norm accumulates in FP64; the
+// Hessenberg matrix, Givens rotations and least-squares solve are FP64; the
+// solution u and the true residual f - A u (at every restart) are complex128.
+// Forming A z in FP32 would lose up to ||A|| ||z|| / ||A z|| times the FP32
+// rounding, which for an indefinite Helmholtz operator and a preconditioned
+// z is large enough to separate the implicit and true residuals.
+// Orthogonalisation is classical Gram-Schmidt with one full
+// re-orthogonalisation (CGS2): two passes of (h = V^H w, w -= V h).
+//
+// The solve is a resumable state machine so that a server can interleave many
+// solves on separate streams: every stage enqueues device work, records an
+// event, and the host reads the few scalars it needs (residual estimates)
+// from mapped pinned memory once the event has completed.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "mcmg_internal.cuh"
+
+namespace mcmg {
+
+constexpr int KV = 8;         // vectors per block in the multi-dot
+constexpr int RED_T = 256;    // threads per reduction block
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ void store_w(float2* p, double re, double im) {
+  *p = make_float2((float)re, (float)im);
+}
+__device__ __forceinline__ void store_w(double2* p, double re, double im) {
+  *p = make_double2(re, im);
+}
+
+// part[(bx * ktot + i) * 2 + {0,1}] = sum over this block's range of conj(v_i) w,
+// v_i = V[i * ldv + .] for i < k, v_k = w when ktot = k + 1.
+template <typename WT>
+__global__ void __launch_bounds__(RED_T) k_multidot(const float2* __restrict__ V, long long ldv,
+                                                    int k, int ktot, const WT* __restrict__ w,
+                                                    long long n, double* __restrict__ part) {
+  const int i0 = blockIdx.y * KV;
+  double ar[KV], ai[KV];
+#pragma unroll
+  for (int i = 0; i < KV; ++i) ar[i] = ai[i] = 0.0;
+  for (long long p = (long long)blockIdx.x * RED_T + threadIdx.x; p < n;
+       p += (long long)gridDim.x * RED_T) {
+    const double2 wd = to_d2(w[p]);
+    const double wr = wd.x, wi = wd.y;
+#pragma unroll
+    for (int i = 0; i < KV; ++i) {
+      const int ii = i0 + i;
+      if (ii < ktot) {
+        const double2 v = ii < k ? to_d2(V[(long long)ii * ldv + p]) : wd;
+        ar[i] += v.x * wr + v.y * wi;
+        ai[i] += v.x * wi - v.y * wr;
+      }
+    }
+  }
+  __shared__ double sh[RED_T / 32][KV][2];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < KV; ++i) {
+    double a = warp_sum_d(ar[i]), b = warp_sum_d(ai[i]);
+    if (lane == 0) { sh[wid][i][0] = a; sh[wid][i][1] = b; }
+  }
+  __syncthreads();
+  if (threadIdx.x < KV && i0 + (int)threadIdx.x < ktot) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < RED_T / 32; ++q) { a += sh[q][threadIdx.x][0]; b += sh[q][threadIdx.x][1]; }
+    size_t o = ((size_t)blockIdx.x * ktot + i0 + threadIdx.x) * 2;
+    part[o] = a;
+    part[o + 1] = b;
+  }
+}
+
+// out[i] = sum_b part[(b * width + i) * 2 + {0,1}]  (fixed order)
+__global__ void k_reduce_parts(const double* __restrict__ part, int nblk, int width,
+                               double2* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= width) return;
+  double a = 0.0, b = 0.0;
+  for (int q = 0; q < nblk; ++q) {
+    a += part[((size_t)q * width + i) * 2];
+    b += part[((size_t)q * width + i) * 2 + 1];
+  }
+  out[i] = make_double2(a, b);
+}
+
+// w -= sum_{i<k} h_i V_i  (FP64 accumulation per element); part[bx] = sum |w|^2.
+template <typename WT>
+__global__ void __launch_bounds__(RED_T) k_update(const float2* __restrict__ V, long long ldv, int k,
+                                                  const double2* __restrict__ hc,
+                                                  WT* __restrict__ w, long long n,
+                                                  double* __restrict__ part) {
+  double nn = 0.0;
+  for (long long p = (long long)blockIdx.x * RED_T + threadIdx.x; p < n;
+       p += (long long)gridDim.x * RED_T) {
+    double sr = 0.0, si = 0.0;
+    for (int i = 0; i < k; ++i) {
+      const float2 v = V[(long long)i * ldv + p];
+      const double2 hh = hc[i];
+      sr += hh.x * v.x - hh.y * v.y;
+      si += hh.x * v.y + hh.y * v.x;
+    }
+    const double2 wd = to_d2(w[p]);
+    store_w(w + p, wd.x - sr, wd.y - si);
+    const double2 o = to_d2(w[p]);
+    nn += o.x * o.x + o.y * o.y;
+  }
+  __shared__ double sh[RED_T / 32];
+  nn = warp_sum_d(nn);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int q = 0; q < RED_T / 32; ++q) a += sh[q];
+    part[blockIdx.x] = a;
+  }
+}
+
+__global__ void k_reduce_scalar(const double* __restrict__ part, int nblk, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double a = 0.0;
+    for (int q = 0; q < nblk; ++q) a += part[q];
+    *out = a;
+  }
+}
+
+// Residual partials [nblk][2] -> rr, ff
+__global__ void k_reduce_res(const double* __restrict__ part, int nblk, double* __restrict__ dsc,
+                             double* __restrict__ stat_rr) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < nblk; ++q) { a += part[2 * q]; b += part[2 * q + 1]; }
+    dsc[0] = a;
+    dsc[1] = b;
+    stat_rr[0] = a;
+    stat_rr[1] = b;
+  }
+}
+
+// v0 = r / beta (to complex64), g = (beta, 0, ...)
+__global__ void k_start_cycle(const double2* __restrict__ r, const double* __restrict__ dsc,
+                              float2* __restrict__ v0, long long n, double2* __restrict__ g,
+                              int m) {
+  const double beta = sqrt(dsc[0]);
+  const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) {
+    const double2 v = r[p];
+    v0[p] = make_float2((float)(v.x * inv), (float)(v.y * inv));
+  }
+  if (p <= m) g[p] = make_double2(p == 0 ? beta : 0.0, 0.0);
+}
+
+struct Stat {
+  double res;     // |g_{j+1}|
+  double hn;      // h_{j+1, j}
+  double w0;      // ||A z_j|| before orthogonalisation
+  double rr, ff;  // |f - A u|^2, |f|^2 at the last restart
+};
+
+// Hessenberg column j = dots + dots2, h_{j+1,j} = sqrt(nrm2); previous Givens
+// rotations, new rotation, rhs update.  One thread.
+__global__ void k_givens(int j, int m, const double2* __restrict__ d1, const double2* __restrict__ d2,
+                         const double* __restrict__ dsc, double2* __restrict__ H, double* cs,
+                         double2* sn, double2* g, Stat* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double2* col = H + (size_t)j * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = make_double2(d1[i].x + d2[i].x, d1[i].y + d2[i].y);
+  const double hn = sqrt(dsc[3]);
+  col[j + 1] = make_double2(hn, 0.0);
+  for (int i = 0; i < j; ++i) {
+    const double2 h0 = col[i], h1 = col[i + 1];
+    const double c = cs[i];
+    const double2 s = sn[i];
+    // [c, s; -conj(s), c] applied to (h0, h1)
+    col[i] = make_double2(c * h0.x + s.x * h1.x - s.y * h1.y, c * h0.y + s.x * h1.y + s.y * h1.x);
+    col[i + 1] = make_double2(-(s.x * h0.x + s.y * h0.y) + c * h1.x,
+                              -(s.x * h0.y - s.y * h0.x) + c * h1.y);
+  }
+  const double2 a = col[j], b = col[j + 1];
+  const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
+  const double rho = hypot(aa, bb);
+  double c;
+  double2 s;
+  if (aa == 0.0) {
+    c = 0.0;
+    s = make_double2(1.0, 0.0);
+  } else {
+    c = aa / rho;
+    // s = (a / |a|) conj(b) / rho
+    const double2 ua = make_double2(a.x / aa, a.y / aa);
+    s = make_double2((ua.x * b.x + ua.y * b.y) / rho, (ua.y * b.x - ua.x * b.y) / rho);
+  }
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
+  col[j + 1] = make_double2(0.0, 0.0);
+  const double2 gj = g[j];
+  g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+  g[j] = make_double2(c * gj.x, c * gj.y);
+  st->res = hypot(g[j + 1].x, g[j + 1].y);
+  st->hn = hn;
+  st->w0 = sqrt(d1[j + 1].x);
+}
+
+// v_{j+1} = w / sqrt(nrm2)
+__global__ void k_scale(const double2* __restrict__ w, const double* __restrict__ dsc,
+                        float2* __restrict__ v, long long n) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const double hn = sqrt(dsc[3]);
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  const double2 x = w[p];
+  v[p] = make_float2((float)(x.x * inv), (float)(x.y * inv));
+}
+
+// y = R^{-1} g for the k x k upper triangle of the rotated Hessenberg matrix.
+__global__ void __launch_bounds__(1024) k_backsolve(const double2* __restrict__ H, int m, int k,
+                                                    const double2* __restrict__ g,
+                                                    double2* __restrict__ gw,
+                                                    double2* __restrict__ y) {
+  for (int l = threadIdx.x; l < k; l += blockDim.x) gw[l] = g[l];
+  __syncthreads();
+  __shared__ double2 yi;
+  for (int i = k - 1; i >= 0; --i) {
+    if (threadIdx.x == 0) {
+      const double2 d = H[(size_t)i * (m + 1) + i];
+      const double2 num = gw[i];
+      const double den = d.x * d.x + d.y * d.y;
+      yi = make_double2((num.x * d.x + num.y * d.y) / den, (num.y * d.x - num.x * d.y) / den);
+      y[i] = yi;
+    }
+    __syncthreads();
+    const double2 v = yi;
+    const double2* col = H + (size_t)i * (m + 1);
+    for (int l = threadIdx.x; l < i; l += blockDim.x) {
+      const double2 hc = col[l];
+      gw[l] = make_double2(gw[l].x - (hc.x * v.x - hc.y * v.y), gw[l].y - (hc.x * v.y + hc.y * v.x));
+    }
+    __syncthreads();
+  }
+}
+
+// u += sum_{i<k} y_i Z_i (complex128 accumulate)
+__global__ void k_update_x(const float2* __restrict__ Z, long long ldz, int k,
+                           const double2* __restrict__ y, double2* __restrict__ u, long long n) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double sr = 0.0, si = 0.0;
+  for (int i = 0; i < k; ++i) {
+    const float2 z = Z[(long long)i * ldz + p];
+    const double2 yy = y[i];
+    sr += yy.x * z.x - yy.y * z.y;
+    si += yy.x * z.y + yy.y * z.x;
+  }
+  const double2 o = u[p];
+  u[p] = make_double2(o.x + sr, o.y + si);
+}
+
+// ---------------------------------------------------------------------------
+struct Krylov {
+  mcmg_handle_s* h = nullptr;
+  int m = 0;
+  long long n = 0;
+  int nblk = 0;
+  VWork* vw = nullptr;
+  float2* V = nullptr;
+  float2* Z = nullptr;
+  double2* w = nullptr;     // Arnoldi work vector, FP64
+  double2* r64 = nullptr;
+  double* part = nullptr;
+  double2* d1 = nullptr;
+  double2* d2 = nullptr;
+  double2* H = nullptr;
+  double* cs = nullptr;
+  double2* sn = nullptr;
+  double2* g = nullptr;
+  double2* gw = nullptr;
+  double2* y = nullptr;
+  double* dsc = nullptr;
+  Stat* stat_h = nullptr;   // mapped pinned
+  Stat* stat_d = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaStream_t st = nullptr;
+  DevArena arena;
+  // solve state
+  const double2* f = nullptr;
+  double2* u = nullptr;
+  mcmg_solve_opts o{};
+  enum Phase { IDLE, WAIT_RES, WAIT_STEP, DONE } phase = IDLE;
+  int j = 0, iters = 0, restarts = 0, max_iters = 0;
+  double fnorm = 0.0, rel = 0.0;
+  bool converged = false;
+  mcmg_status final = MCMG_OK;
+  std::chrono::steady_clock::time_point t0;
+  double t_solve = 0.0;
+};
+
+static int red_blocks(long long n) {
+  long long b = (n + RED_T - 1) / RED_T;
+  long long cap = 148 * 4;
+  return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+mcmg_status krylov_create(mcmg_handle_s* h, int m, Krylov** out) {
+  Krylov* k = new Krylov();
+  k->h = h;
+  k->m = m;
+  k->n = h->g0.nodes();
+  k->nblk = red_blocks(k->n);
+  const long long n = k->n;
+  auto A = [&](void** p, size_t b) { return dev_alloc(h, k->arena, p, b); };
+  mcmg_status s = MCMG_OK;
+  if ((s = A((void**)&k->V, sizeof(float2) * (size_t)(m + 1) * n)) ||
+      (s = A((void**)&k->Z, sizeof(float2) * (size_t)m * n)) ||
+      (s = A((void**)&k->w, sizeof(double2) * (size_t)n)) ||
+      (s = A((void**)&k->r64, sizeof(double2) * (size_t)n)) ||
+      (s = A((void**)&k->part, sizeof(double) * 2 * (size_t)k->nblk * (m + 2))) ||
+      (s = A((void**)&k->d1, sizeof(double2) * (m + 2))) ||
+      (s = A((void**)&k->d2, sizeof(double2) * (m + 2))) ||
+      (s = A((void**)&k->H, sizeof(double2) * (size_t)m * (m + 1))) ||
+      (s = A((void**)&k->cs, sizeof(double) * (m + 1))) ||
+      (s = A((void**)&k->sn, sizeof(double2) * (m + 1))) ||
+      (s = A((void**)&k->g, sizeof(double2) * (m + 2))) ||
+      (s = A((void**)&k->gw, sizeof(double2) * (m + 2))) ||
+      (s = A((void**)&k->y, sizeof(double2) * (m + 1))) ||
+      (s = A((void**)&k->dsc, sizeof(double) * 8))) {
+    krylov_destroy(h, k);
+    return s;
+  }
+  if ((s = vwork_create(h, 1, &k->vw)) != MCMG_OK) {
+    krylov_destroy(h, k);
+    return s;
+  }
+  cudaError_t e = cudaHostAlloc((void**)&k->stat_h, sizeof(Stat), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&k->stat_d, k->stat_h, 0);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&k->ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    krylov_destroy(h, k);
+    return cuda_fail(e, "krylov_create");
+  }
+  *out = k;
+  return MCMG_OK;
+}
+
+void krylov_destroy(mcmg_handle_s* h, Krylov* k) {
+  if (!k) return;
+  if (k->vw) vwork_destroy(h, k->vw);
+  arena_free(h, k->arena);
+  if (k->stat_h) cudaFreeHost(k->stat_h);
+  if (k->ev) cudaEventDestroy(k->ev);
+  delete k;
+}
+
+// Enqueue r = f - A u and its norms; the host reads them at WAIT_RES.
+static mcmg_status enqueue_restart(Krylov* k) {
+  mcmg_handle_s* h = k->h;
+  MCMG_TRY(launch_residual64(h->q64, k->f, k->u, k->r64, k->part, k->nblk, h->g0, 1, k->st));
+  k_reduce_res<<<1, 32, 0, k->st>>>(k->part, k->nblk, k->dsc, &k->stat_d->rr);
+  MCMG_CHECK_LAUNCH("reduce_res");
+  MCMG_CUDA(cudaEventRecord(k->ev, k->st));
+  k->phase = Krylov::WAIT_RES;
+  return MCMG_OK;
+}
+
+static mcmg_status multidot(Krylov* k, int nv, bool self, double2* out) {
+  const int ktot = nv + (self ? 1 : 0);
+  dim3 grid((unsigned)k->nblk, (unsigned)((ktot + KV - 1) / KV));
+  k_multidot<double2><<<grid, RED_T, 0, k->st>>>(k->V, k->n, nv, ktot, k->w, k->n, k->part);
+  MCMG_CHECK_LAUNCH("multidot");
+  k_reduce_parts<<<(ktot + 127) / 128, 128, 0, k->st>>>(k->part, k->nblk, ktot, out);
+  MCMG_CHECK_LAUNCH("reduce_parts");
+  return MCMG_OK;
+}
+
+// One Arnoldi step j: z_j = MG(v_j), w = A z_j, CGS2, Givens; event.
+static mcmg_status enqueue_step(Krylov* k) {
+  mcmg_handle_s* h = k->h;
+  const long long n = k->n;
+  const int j = k->j;
+  float2* vj = k->V + (size_t)j * n;
+  float2* zj = k->Z + (size_t)j * n;
+  MCMG_TRY(vcycle_run(h, k->vw, vj, zj, 1, k->st));
+  MCMG_TRY(launch_apply_A_mixed(h->q64, zj, k->w, h->g0, 1, k->st));
+  MCMG_TRY(multidot(k, j + 1, true, k->d1));
+  k_update<double2><<<k->nblk, RED_T, 0, k->st>>>(k->V, n, j + 1, k->d1, k->w, n, k->part);
+  MCMG_CHECK_LAUNCH("update");
+  MCMG_TRY(multidot(k, j + 1, false, k->d2));
+  k_update<double2><<<k->nblk, RED_T, 0, k->st>>>(k->V, n, j + 1, k->d2, k->w, n, k->part);
+  MCMG_CHECK_LAUNCH("update");
+  k_reduce_scalar<<<1, 32, 0, k->st>>>(k->part, k->nblk, k->dsc + 3);
+  MCMG_CHECK_LAUNCH("reduce_scalar");
+  k_givens<<<1, 32, 0, k->st>>>(j, k->m, k->d1, k->d2, k->dsc, k->H, k->cs, k->sn, k->g,
+                                k->stat_d);
+  MCMG_CHECK_LAUNCH("givens");
+  if (j + 1 <= k->m) {
+    k_scale<<<(unsigned)((n + 255) / 256), 256, 0, k->st>>>(k->w, k->dsc, k->V + (size_t)(j + 1) * n, n);
+    MCMG_CHECK_LAUNCH("scale");
+  }
+  MCMG_CUDA(cudaEventRecord(k->ev, k->st));
+  k->phase = Krylov::WAIT_STEP;
+  return MCMG_OK;
+}
+
+static mcmg_status enqueue_finish_cycle(Krylov* k, int kk) {
+  k_backsolve<<<1, 1024, 0, k->st>>>(k->H, k->m, kk, k->g, k->gw, k->y);
+  MCMG_CHECK_LAUNCH("backsolve");
+  k_update_x<<<(unsigned)((k->n + 255) / 256), 256, 0, k->st>>>(k->Z, k->n, kk, k->y, k->u, k->n);
+  MCMG_CHECK_LAUNCH("update_x");
+  k->restarts += 1;
+  return enqueue_restart(k);
+}
+
+mcmg_status krylov_begin(Krylov* k, const double2* f, double2* u, const mcmg_solve_opts& o,
+                         cudaStream_t st) {
+  k->f = f;
+  k->u = u;
+  k->o = o;
+  k->st = st;
+  k->iters = 0;
+  k->restarts = 0;
+  k->j = 0;
+  k->converged = false;
+  k->final = MCMG_OK;
+  k->fnorm = -1.0;
+  k->max_iters = o.max_iters > 0 ? o.max_iters : 20 * (k->h->g0.d == 3 ? k->h->g0.nz : k->h->g0.ny);
+  k->t0 = std::chrono::steady_clock::now();
+  return enqueue_restart(k);
+}
+
+static void finish(Krylov* k, bool conv, mcmg_status s) {
+  k->converged = conv;
+  k->final = s;
+  k->phase = Krylov::DONE;
+  k->t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - k->t0).count();
+}
+
+mcmg_status krylov_advance(Krylov* k, bool blocking, int* done) {
+  *done = 0;
+  if (k->phase == Krylov::DONE) {
+    *done = 1;
+    return MCMG_OK;
+  }
+  if (blocking) {
+    MCMG_CUDA(cudaEventSynchronize(k->ev));
+  } else {
+    cudaError_t e = cudaEventQuery(k->ev);
+    if (e == cudaErrorNotReady) return MCMG_OK;
+    if (e != cudaSuccess) return cuda_fail(e, "krylov event");
+  }
+  Stat st;
+  std::memcpy(&st, (const void*)k->stat_h, sizeof(Stat));
+  if (k->phase == Krylov::WAIT_RES) {
+    if (k->fnorm < 0.0) k->fnorm = std::sqrt(st.ff);
+    const double beta = std::sqrt(st.rr);
+    if (!std::isfinite(beta)) {
+      k->rel = beta;
+      finish(k, false, MCMG_ERR_NUMERIC);
+      *done = 1;
+      return MCMG_OK;
+    }
+    k->rel = k->fnorm > 0.0 ? beta / k->fnorm : 0.0;
+    if (k->fnorm == 0.0 || k->rel <= k->o.tol) {
+      finish(k, true, MCMG_OK);
+      *done = 1;
+      return MCMG_OK;
+    }
+    if (k->iters >= k->max_iters) {
+      finish(k, false, MCMG_ERR_NOT_CONVERGED);
+      *done = 1;
+      return MCMG_OK;
+    }
+    const long long cover = std::max<long long>(k->n, k->m + 1);
+    k_start_cycle<<<(unsigned)((cover + 255) / 256), 256, 0, k->st>>>(k->r64, k->dsc, k->V, k->n,
+                                                                        k->g, k->m);
+    MCMG_CHECK_LAUNCH("start_cycle");
+    k->j = 0;
+    return enqueue_step(k);
+  }
+  // WAIT_STEP
+  k->iters += 1;
+  const double est = st.res / k->fnorm;
+  if (!std::isfinite(est)) {
+    finish(k, false, MCMG_ERR_NUMERIC);
+    *done = 1;
+    return MCMG_OK;
+  }
+  const bool stop = est <= k->o.tol || st.hn <= 1e-14 * st.w0 || k->j + 1 >= k->m ||
+                    k->iters >= k->max_iters;
+  if (stop) return enqueue_finish_cycle(k, k->j + 1);
+  k->j += 1;
+  return enqueue_step(k);
+}
+
+int krylov_m(const Krylov* k) { return k->m; }
+
+void krylov_info(const Krylov* k, mcmg_solve_info* info, mcmg_status* final_status) {
+  if (info) {
+    info->iters = k->iters;
+    info->restarts = k->restarts;
+    info->rel_residual = k->rel;
+    info->t_solve_s = k->t_solve;
+    info->converged = k->converged ? 1 : 0;
+  }
+  if (final_status) *final_status = k->final;
+}
+
+mcmg_status cgs2_once(mcmg_handle_s* h, const float2* V, int kv, long long n, float2* w,
+                      double* h_host, double* norm_host, cudaStream_t st) {
+  DevArena ar;
+  int nblk = red_blocks(n);
+  double* part = nullptr;
+  double2 *d1 = nullptr, *d2 = nullptr;
+  double* dsc = nullptr;
+  mcmg_status s;
+  if ((s = dev_alloc(h, ar, (void**)&part, sizeof(double) * 2 * (size_t)nblk * (kv + 1))) ||
+      (s = dev_alloc(h, ar, (void**)&d1, sizeof(double2) * (kv + 1))) ||
+      (s = dev_alloc(h, ar, (void**)&d2, sizeof(double2) * (kv + 1))) ||
+      (s = dev_alloc(h, ar, (void**)&dsc, sizeof(double) * 2))) {
+    arena_free(h, ar);
+    return s;
+  }
+  auto run = [&]() -> mcmg_status {
+    dim3 grid((unsigned)nblk, (unsigned)((kv + KV - 1) / KV));
+    for (int pass = 0; pass < 2; ++pass) {
+      double2* dd = pass == 0 ? d1 : d2;
+      k_multidot<float2><<<grid, RED_T, 0, st>>>(V, n, kv, kv, w, n, part);
+      MCMG_CHECK_LAUNCH("multidot");
+      k_reduce_parts<<<(kv + 127) / 128, 128, 0, st>>>(part, nblk, kv, dd);
+      MCMG_CHECK_LAUNCH("reduce_parts");
+      k_update<float2><<<nblk, RED_T, 0, st>>>(V, n, kv, dd, w, n, part);
+      MCMG_CHECK_LAUNCH("update");
+    }
+    k_reduce_scalar<<<1, 32, 0, st>>>(part, nblk, dsc);
+    MCMG_CHECK_LAUNCH("reduce_scalar");
+    std::vector<double2> a(kv), b(kv);
+    double nrm2 = 0.0;
+    MCMG_CUDA(cudaMemcpyAsync(a.data(), d1, sizeof(double2) * kv, cudaMemcpyDeviceToHost, st));
+    MCMG_CUDA(cudaMemcpyAsync(b.data(), d2, sizeof(double2) * kv, cudaMemcpyDeviceToHost, st));
+    MCMG_CUDA(cudaMemcpyAsync(&nrm2, dsc, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MCMG_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < kv; ++i) {
+      h_host[2 * i] = a[i].x + b[i].x;
+      h_host[2 * i + 1] = a[i].y + b[i].y;
+    }
+    *norm_host = std::sqrt(nrm2);
+    return MCMG_OK;
+  };
+  s = run();
+  cudaStreamSynchronize(st);
+  arena_free(h, ar);
+  return s;
+}
+
+}  // namespace mcmg

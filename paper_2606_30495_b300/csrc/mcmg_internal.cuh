@@ -1,0 +1,196 @@
+// Internal declarations shared by the McMg CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/mcmg.h"
+
+namespace mcmg {
+
+// ---------------------------------------------------------------- complex ---
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  return make_float2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return make_float2(a.x - b.x, a.y - b.y);
+}
+
+// ------------------------------------------------------- launch counting ---
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ----------------------------------------------------------------- errors ---
+void set_error(const char* fmt, ...);
+mcmg_status cuda_fail(cudaError_t e, const char* what);
+
+#define MCMG_CUDA(call)                                              \
+  do {                                                               \
+    cudaError_t _e = (call);                                         \
+    if (_e != cudaSuccess) return ::mcmg::cuda_fail(_e, #call);      \
+  } while (0)
+
+#define MCMG_CHECK_LAUNCH(what)                                      \
+  do {                                                               \
+    ::mcmg::count_launch();                                          \
+    cudaError_t _e = cudaGetLastError();                             \
+    if (_e != cudaSuccess) return ::mcmg::cuda_fail(_e, what);       \
+  } while (0)
+
+#define MCMG_TRY(expr)                                               \
+  do {                                                               \
+    mcmg_status _s = (expr);                                         \
+    if (_s != MCMG_OK) return _s;                                    \
+  } while (0)
+
+// ------------------------------------------------------------------- grid ---
+struct Grid {
+  int d;            // 2 or 3
+  int nx, ny, nz;   // nz = 1 in 2D
+  __host__ __device__ long long nodes() const { return (long long)nx * ny * nz; }
+  __host__ __device__ Grid coarse() const { return Grid{d, nx / 2, ny / 2, d == 3 ? nz / 2 : 1}; }
+};
+
+// Read-only per-level state: features and weights.  Mixing matrices are
+// stored transposed, M^T[ci][co], so consecutive output channels are
+// contiguous.
+struct Level {
+  Grid g;
+  int C = 0, Cn = 0;          // channels here and on the next coarser level
+  int nu_pre = 0, nu_post = 0;
+  float2* a = nullptr;        // [nodes][C]
+  float2* s = nullptr;        // [nodes][C]
+  float2* Wt = nullptr;       // [T][C][C]
+  float2* KAt = nullptr;      // [C][C]
+  float2* KSt = nullptr;      // [C][C]
+  float2* Wsmt = nullptr;     // [nsteps][C][C]
+  float2* Rt = nullptr;       // [T3][C][Cn]
+  float2* Pt = nullptr;       // [T3][Cn][C]
+};
+
+// Launchers used by the V-cycle (kernels_vcycle.cu), asynchronous on `st`.
+// mode 0: e_out = e_in + S^(step)(r - A e_in); mode 1: e_out = r - A e_in.
+mcmg_status launch_smooth(const Level& L, int step, const float2* r, const float2* e_in,
+                          float2* e_out, int mode, int nrhs, cudaStream_t st);
+mcmg_status launch_restrict(const Level& L, const float2* t, float2* rc, int nrhs,
+                            cudaStream_t st);
+mcmg_status launch_prolong_add(const Level& L, const float2* ec, float2* e, int nrhs,
+                               cudaStream_t st);
+mcmg_status launch_lift(const float2* r, const float2* lift, float2* r1, int C, long long nodes,
+                        int nrhs, cudaStream_t st);
+mcmg_status launch_project(const float2* e1, const float2* proj, float2* e, int C,
+                           long long nodes, int nrhs, cudaStream_t st);
+
+// helmholtz (kernels_helm.cu)
+mcmg_status launch_make_q(const double* c_dev, double omega, int width, double gamma_max,
+                          const Grid& g, float2* q32, double2* q64, cudaStream_t st);
+mcmg_status launch_apply_A32(const float2* q, const float2* x, float2* y, const Grid& g,
+                             int nrhs, cudaStream_t st);
+mcmg_status launch_apply_A64(const double2* q, const double2* x, double2* y, const Grid& g,
+                             int nrhs, cudaStream_t st);
+// complex64 x, FP64 arithmetic, complex128 y
+mcmg_status launch_apply_A_mixed(const double2* q, const float2* x, double2* y, const Grid& g,
+                                 int nrhs, cudaStream_t st);
+mcmg_status launch_residual64(const double2* q, const double2* f, const double2* x, double2* r,
+                              double* part, int nblk, const Grid& g, int nrhs, cudaStream_t st);
+
+// setup (kernels_setup.cu)
+mcmg_status launch_setup_input(const double2* q64, float* m, const Grid& g, cudaStream_t st);
+mcmg_status launch_conv3_gelu(const float* in, int cin, float* out, int cout, const float* w,
+                              const float* b, const Grid& gin, int stride, cudaStream_t st);
+mcmg_status launch_fw_restrict_q(const double2* qf, double2* qc, const Grid& gf, cudaStream_t st);
+mcmg_status launch_assemble_features(const float* net_a, const float* net_s, const double2* ql,
+                                     float2* a, float2* s, int C, const Grid& g, int level,
+                                     double feat_sl, double feat_eps, double beta_re,
+                                     double beta_im, cudaStream_t st);
+
+// Device allocations tracked against a context budget.
+struct DevArena {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+};
+
+}  // namespace mcmg
+
+struct mcmg_handle_s;
+
+namespace mcmg {
+
+// Per-execution V-cycle workspace (one per synchronous user / server request).
+struct VWork {
+  int nrhs = 0;
+  float2* r[MCMG_MAX_LEVELS] = {};
+  float2* e[MCMG_MAX_LEVELS] = {};
+  float2* e2[MCMG_MAX_LEVELS] = {};
+  float2* t[MCMG_MAX_LEVELS] = {};
+  cudaGraphExec_t graph = nullptr;   // the level sequence, captured once
+  float2* e1 = nullptr;              // buffer holding e_1 after the graph
+  unsigned long long graph_kernels = 0;  // kernel nodes in the graph
+  DevArena arena;
+};
+
+mcmg_status vwork_create(mcmg_handle_s* h, int nrhs, VWork** out);
+void vwork_destroy(mcmg_handle_s* h, VWork* w);
+// e = MG(r) on stream st using workspace w.
+mcmg_status vcycle_run(mcmg_handle_s* h, VWork* w, const float2* r, float2* e, int nrhs,
+                       cudaStream_t st);
+
+// Resumable FGMRES(m) for one right-hand side (krylov.cu).
+struct Krylov;
+mcmg_status krylov_create(mcmg_handle_s* h, int m, Krylov** out);
+void krylov_destroy(mcmg_handle_s* h, Krylov* k);
+// Start a solve of A u = f (device c128).  Enqueues work on st.
+mcmg_status krylov_begin(Krylov* k, const double2* f, double2* u, const mcmg_solve_opts& o,
+                         cudaStream_t st);
+// Advance: if the last enqueued work has finished, read its results and
+// enqueue the next stage.  *done = 1 when the solve has finished.
+// blocking = true waits for the enqueued work instead of polling.
+mcmg_status krylov_advance(Krylov* k, bool blocking, int* done);
+void krylov_info(const Krylov* k, mcmg_solve_info* info, mcmg_status* final_status);
+int krylov_m(const Krylov* k);
+// CGS2 on caller buffers (used by mcmg_cgs2).
+mcmg_status cgs2_once(mcmg_handle_s* h, const float2* V, int k, long long n, float2* w,
+                      double* h_host, double* norm_host, cudaStream_t st);
+
+mcmg_status dev_alloc(mcmg_handle_s* h, DevArena& a, void** p, size_t bytes);
+void arena_free(mcmg_handle_s* h, DevArena& a);
+
+}  // namespace mcmg
+
+struct mcmg_ctx_s;
+
+struct mcmg_handle_s {
+  mcmg_ctx_s* ctx = nullptr;
+  int device = 0;
+  int L = 0;
+  int precision = MCMG_FP32;
+  mcmg::Grid g0;
+  float2* q32 = nullptr;        // (kh)^2 (1 - i gamma), c64 [nodes]
+  double2* q64 = nullptr;       // same, c128
+  float2* lift = nullptr;       // [C0]
+  float2* proj = nullptr;       // [C0]
+  mcmg::Level lv[MCMG_MAX_LEVELS];
+  mcmg::DevArena arena;         // features, weights
+  mcmg::VWork* work = nullptr;  // for mcmg_vcycle / mcmg_solve
+  mcmg::Krylov* kry = nullptr;  // for mcmg_solve
+  cudaStream_t stream = nullptr;
+  std::mutex mu;                // serialises synchronous use of work / kry
+};

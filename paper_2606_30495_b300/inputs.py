@@ -269,7 +269,7 @@ def make_weights(dim: int, channels, nu_pre, nu_post, mode: str = "structured",
     wts = dict(dim=dim, levels=L, channels=list(channels), nu_pre=list(nu_pre),
                nu_post=list(nu_post), feat_sl=1.0 if base_on else 0.0,
                feat_eps={"structured": EPS_STRUCTURED, "degenerate": 0.0, "random": 1.0}[mode],
-               sl_shift=(1.0, 1.0))
+               sl_shift=(1.0, -1.0))
     wts["flift_w"], wts["flift_b"] = rconv(2 * channels[0], 2)
     lv = []
     for l in range(L):

@@ -227,15 +227,16 @@ def test_conv3_matches_ndimage_correlate(shape):
 
 
 def test_setup_classical_branch_literal():
-    """Degenerate weights: a_1 = -(1+i) q, s_1 = 1/(4 + a_1), a_2 = full weighting of a_1."""
+    """Degenerate weights: a_1 = -beta q, s_1 = 1/(4 + a_1), a_2 = full weighting of a_1."""
     n = 16
     c = I.grf((n, n), 4.0, 1.0, 3.0, rng(5))
     q = O.wavenumber_coef(c, 30.0, 3, 1.0)
     w = I.make_weights(2, [1, 1, 1], [2, 2, 2], [2, 2, 0], mode="degenerate", seed=0)
     f = O.setup(q, w)
     a1, s1 = f[0][0][..., 0], f[0][1][..., 0]
-    assert np.max(np.abs(a1 + (1 + 1j) * q)) < 1e-15
-    assert np.max(np.abs(s1 - 1 / (4 - (1 + 1j) * q))) < 1e-15
+    beta = complex(*w["sl_shift"])
+    assert np.max(np.abs(a1 + beta * q)) < 1e-15
+    assert np.max(np.abs(s1 - 1 / (4 - beta * q))) < 1e-15
     a2 = f[1][0][..., 0]
     J, K = 3, 5   # interior coarse node (y, x) <-> fine (6, 10)
     fy, fx = 2 * J, 2 * K
@@ -250,10 +251,10 @@ def test_setup_classical_branch_literal():
 # V-cycle
 # --------------------------------------------------------------------------
 
-def _textbook_slmg(q, levels, r):
+def _textbook_slmg(q, levels, r, beta):
     """Classical complex-shifted-Laplacian multigrid V-cycle, written out directly.
 
-    M = -Delta_h - (1 + i) k^2 (Eq. csl_shift) on every level (fine h^2 units,
+    M = -Delta_h - beta k^2 (Eq. csl_shift) on every level (fine h^2 units,
     so the Laplacian part of level l carries 1/4^(l-1)); weighted Jacobi 0.66 on
     diag(M), 2 pre + 2 post steps, 2 steps on the coarsest grid, full-weighting
     restriction, bilinear interpolation, coarse k^2 by full weighting.
@@ -295,10 +296,10 @@ def _textbook_slmg(q, levels, r):
         qs.append(fw(qs[-1]))
 
     def M(l, u):
-        return lap(u) / 4 ** l - (1 + 1j) * qs[l] * u
+        return lap(u) / 4 ** l - beta * qs[l] * u
 
     def jacobi(l, u, f, steps):
-        dg = 4 / 4 ** l - (1 + 1j) * qs[l]
+        dg = 4 / 4 ** l - beta * qs[l]
         for _ in range(steps):
             u = u + 0.66 * (f - M(l, u)) / dg
         return u
@@ -322,8 +323,12 @@ def test_degenerate_mcmg_equals_textbook_shifted_laplacian_mg():
     feats = O.setup(q, w)
     r = I.complex_normal((n, n), rng(7))
     got = O.vcycle(w, feats, r)
-    want = _textbook_slmg(q, 3, r)
+    want = _textbook_slmg(q, 3, r, complex(*w["sl_shift"]))
     assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want))
+    w2 = dict(w, sl_shift=(1.0, 1.0))        # the shift as printed in Eq. csl_shift
+    got2 = O.vcycle(w2, O.setup(q, w2), r)
+    want2 = _textbook_slmg(q, 3, r, 1.0 + 1.0j)
+    assert np.max(np.abs(got2 - want2)) < 1e-13 * np.max(np.abs(want2))
 
 
 def _small_model(mode, seed=0, shape=(8, 8), channels=(2, 3), pre=None, post=None):
