@@ -241,6 +241,23 @@ mcmg_status mcmg_prolong_add(mcmg_handle h, int level, const void* e_coarse_dev,
 mcmg_status mcmg_cgs2(mcmg_handle h, const void* V_dev, int k, size_t n, void* w_dev,
                       double* h_host, double* norm_host);
 
+/* mcmg_cgs2 for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this entry point exists for callers that must not call
+ * cudaMalloc: code running under another framework's fixed memory budget or
+ * allocator, and call sites that cannot afford the device-wide
+ * synchronisation that cudaMalloc / cudaFree can cause.  It allocates nothing:
+ * its scratch (about 0.6 MB) is a static device array that every GPU which
+ * loads this library holds until the process exits.  Same arguments and
+ * results as mcmg_cgs2, with k at most 64 (larger k returns MCMG_ERR_ARG), no
+ * handle, and the caller's stream (NULL = legacy default stream); the call
+ * returns when the results are on the host.  The first call on a device looks
+ * up the array's device address with that device current; make that first
+ * call before any stream capture.  All calls share the one array, so calls
+ * that overlap on the GPU race; nothing carries over from one call to the
+ * next.                                                                      */
+mcmg_status mcmg_cgs2_noalloc(const void* V_dev, int k, size_t n, void* w_dev,
+                              double* h_host, double* norm_host, void* stream);
+
 /* Number of kernel launches the library has issued in this process (a
  * captured graph counts as its kernel nodes).  For launch accounting.        */
 uint64_t mcmg_kernel_launches(void);

@@ -566,4 +566,97 @@ mcmg_status cgs2_once(mcmg_handle_s* h, const float2* V, int kv, long long n, fl
   return s;
 }
 
+// ---------------------------------------------------------------------------
+// CGS2 without any allocation, for callers that cannot allocate device memory.
+//
+// Its scratch (multi-dot partial sums, the two coefficient vectors, the norm)
+// lives in the file-scope array below, which every GPU that loads this
+// library holds until the process exits.  Host code must not pass the array's
+// name to a kernel: on the host that name is only a stand-in, so its device
+// address is looked up once per device with cudaGetSymbolAddress (on the first
+// call made with that device current) and cached.  All calls share the array:
+// calls that overlap on the GPU race, and each call writes every scratch entry
+// it reads before reading it, so nothing depends on an earlier call's contents.
+// ---------------------------------------------------------------------------
+constexpr int NOALLOC_MAX_K = 64;                       // basis vectors per call
+constexpr int NOALLOC_MAX_BLK = 148 * 4;                // = red_blocks() cap
+constexpr size_t NOALLOC_PART = 2ull * NOALLOC_MAX_BLK * NOALLOC_MAX_K;
+constexpr size_t NOALLOC_DOUBLES = NOALLOC_PART + 4ull * NOALLOC_MAX_K + 8;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+// h = d1 + d2 (k entries), written as (re, im) pairs into out.
+__global__ void k_sum_coeffs(const double2* __restrict__ d1, const double2* __restrict__ d2, int k,
+                             double* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < k) {
+    out[2 * i] = d1[i].x + d2[i].x;
+    out[2 * i + 1] = d1[i].y + d2[i].y;
+  }
+}
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[64] = {};                 // per device ordinal
+
+static mcmg_status noalloc_scratch(double** out) {
+  int dev = 0;
+  MCMG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal %d out of range", dev);
+    return MCMG_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return MCMG_OK;
+}
+
 }  // namespace mcmg
+
+mcmg_status mcmg_cgs2_noalloc(const void* V_dev, int k, size_t n, void* w_dev, double* h_host,
+                              double* norm_host, void* stream) {
+  using namespace mcmg;
+  if (!V_dev || !w_dev || !h_host || !norm_host || n < 1) {
+    set_error("NULL pointer or empty vector");
+    return MCMG_ERR_ARG;
+  }
+  if (k < 1 || k > NOALLOC_MAX_K) {
+    set_error("mcmg_cgs2_noalloc takes 1..%d basis vectors, got %d", NOALLOC_MAX_K, k);
+    return MCMG_ERR_ARG;
+  }
+  double* base = nullptr;
+  MCMG_TRY(noalloc_scratch(&base));
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long nn = (long long)n;
+  const int nblk = red_blocks(nn);
+  double* part = base;
+  double2* d1 = (double2*)(base + NOALLOC_PART);
+  double2* d2 = d1 + NOALLOC_MAX_K;
+  double* dsc = base + NOALLOC_DOUBLES - 8;
+  const float2* V = (const float2*)V_dev;
+  float2* w = (float2*)w_dev;
+  dim3 grid((unsigned)nblk, (unsigned)((k + KV - 1) / KV));
+  for (int pass = 0; pass < 2; ++pass) {
+    double2* dd = pass == 0 ? d1 : d2;
+    k_multidot<float2><<<grid, RED_T, 0, st>>>(V, nn, k, k, w, nn, part);
+    MCMG_CHECK_LAUNCH("multidot");
+    k_reduce_parts<<<(k + 127) / 128, 128, 0, st>>>(part, nblk, k, dd);
+    MCMG_CHECK_LAUNCH("reduce_parts");
+    k_update<float2><<<nblk, RED_T, 0, st>>>(V, nn, k, dd, w, nn, part);
+    MCMG_CHECK_LAUNCH("update");
+  }
+  k_reduce_scalar<<<1, 32, 0, st>>>(part, nblk, dsc);
+  MCMG_CHECK_LAUNCH("reduce_scalar");
+  k_sum_coeffs<<<(k + 127) / 128, 128, 0, st>>>(d1, d2, k, part);   // part is free again
+  MCMG_CHECK_LAUNCH("sum_coeffs");
+  double nrm2 = 0.0;
+  MCMG_CUDA(cudaMemcpyAsync(h_host, part, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, st));
+  MCMG_CUDA(cudaMemcpyAsync(&nrm2, dsc, sizeof(double), cudaMemcpyDeviceToHost, st));
+  MCMG_CUDA(cudaStreamSynchronize(st));
+  *norm_host = std::sqrt(nrm2);
+  return MCMG_OK;
+}

@@ -80,6 +80,8 @@ _SIGS = {
     "mcmg_residual_restrict": [_P, C.c_int, _P, _P, _P, C.c_int, _P],
     "mcmg_prolong_add": [_P, C.c_int, _P, _P, C.c_int, _P],
     "mcmg_cgs2": [_P, _P, C.c_int, C.c_size_t, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "mcmg_cgs2_noalloc": [_P, C.c_int, C.c_size_t, _P, C.POINTER(C.c_double),
+                          C.POINTER(C.c_double), _P],
     "mcmg_kernel_launches": [],
     "mcmg_last_error": [],
     "mcmg_version": [],
@@ -184,6 +186,18 @@ def pack_weights(w: dict):
 
 
 # ---------------------------------------------------------------- objects ---
+
+def cgs2_noalloc(V, w, stream=None):
+    """mcmg_cgs2_noalloc: CGS2 of w against the rows of V with no device
+    allocation (scratch in a static device array).  Returns (h, ||w||)."""
+    lib = load()
+    k, n = V.shape[0], V.shape[1]
+    hbuf = np.zeros(2 * k)
+    nrm = C.c_double()
+    _check(lib.mcmg_cgs2_noalloc(ptr(V), k, n, ptr(w), hbuf.ctypes.data_as(C.POINTER(C.c_double)),
+                                 C.byref(nrm), _stream(stream)))
+    return hbuf.view(np.complex128), nrm.value
+
 
 class Context:
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
