@@ -15,12 +15,28 @@
 
 namespace mcmg {
 
-template <int C>
+// Thread (co, g) of a 256-thread block owns output channel co of TN nodes;
+// G = 256 / C node groups, NB = G * TN nodes per block.  TN is chosen per
+// launch: large for big grids (weight reuse), small for coarse grids (enough
+// blocks to cover the SMs).
+template <int C, int TN_>
 struct Tile {
-  static constexpr int G = 256 / C;                               // node groups
-  static constexpr int NB = (2048 / C) < 256 ? (2048 / C) : 256;  // nodes per block
-  static constexpr int TN = NB / G;                               // nodes per thread
+  static constexpr int G = 256 / C;      // node groups
+  static constexpr int TN = TN_;         // nodes per thread
+  static constexpr int NB = G * TN;      // nodes per block
 };
+
+// Largest nodes-per-thread (of 8, 2, 1) that still gives at least two blocks
+// per SM, so coarse levels are not left with a handful of blocks.
+static int pick_tn(long long nodes, int C, int nrhs) {
+  const long long want = 2 * 148;
+  const int G = 256 / C;
+  for (int tn : {8, 2}) {
+    long long blocks = (nodes + (long long)G * tn - 1) / ((long long)G * tn) * nrhs;
+    if (blocks >= want) return tn;
+  }
+  return 1;
+}
 
 struct SmoothParams {
   const float2* r;
@@ -43,9 +59,9 @@ __device__ __forceinline__ void node_xyz(long long n, int nx, int ny, int& x, in
   z = (int)(rest / ny);
 }
 
-template <int C, int D, int MODE>
+template <int C, int D, int MODE, int TN>
 __global__ void __launch_bounds__(256) k_smooth(SmoothParams p) {
-  using T = Tile<C>;
+  using T = Tile<C, TN>;
   extern __shared__ float2 sm[];
   const int co = threadIdx.x % C;
   const int g = threadIdx.x / C;
@@ -169,17 +185,26 @@ __global__ void __launch_bounds__(256) k_smooth(SmoothParams p) {
   }
 }
 
-template <int C, int D>
-static mcmg_status smooth_c(const SmoothParams& p, int mode, int nrhs, cudaStream_t st) {
-  using T = Tile<C>;
+template <int C, int D, int TN>
+static mcmg_status smooth_tn(const SmoothParams& p, int mode, int nrhs, cudaStream_t st) {
+  using T = Tile<C, TN>;
   dim3 grid((unsigned)((p.nodes + T::NB - 1) / T::NB), (unsigned)nrhs);
   size_t smem = mode == 0 ? 2 * (size_t)T::NB * C * sizeof(float2) : 0;
   if (mode == 0)
-    k_smooth<C, D, 0><<<grid, 256, smem, st>>>(p);
+    k_smooth<C, D, 0, TN><<<grid, 256, smem, st>>>(p);
   else
-    k_smooth<C, D, 1><<<grid, 256, smem, st>>>(p);
+    k_smooth<C, D, 1, TN><<<grid, 256, smem, st>>>(p);
   MCMG_CHECK_LAUNCH("smooth");
   return MCMG_OK;
+}
+
+template <int C, int D>
+static mcmg_status smooth_c(const SmoothParams& p, int mode, int nrhs, cudaStream_t st) {
+  switch (pick_tn(p.nodes, C, nrhs)) {
+    case 8: return smooth_tn<C, D, 8>(p, mode, nrhs, st);
+    case 2: return smooth_tn<C, D, 2>(p, mode, nrhs, st);
+    default: return smooth_tn<C, D, 1>(p, mode, nrhs, st);
+  }
 }
 
 template <int D>
@@ -231,9 +256,9 @@ struct TransferParams {
   long long src_nodes, dst_nodes;
 };
 
-template <int CO, int D>
+template <int CO, int D, int TN>
 __global__ void __launch_bounds__(256) k_restrict(TransferParams p) {
-  using T = Tile<CO>;
+  using T = Tile<CO, TN>;
   const int co = threadIdx.x % CO;
   const int g = threadIdx.x / CO;
   const long long NC = p.dst_nodes;
@@ -277,10 +302,13 @@ __global__ void __launch_bounds__(256) k_restrict(TransferParams p) {
 }
 
 // Prolongation-add: e[p][co] += sum over (J, o) with 2J + o = p of
-// sum_ci P[o][co][ci] ec[J][ci]  (transposed strided convolution).
-template <int CO, int D>
+// sum_ci P[o][co][ci] ec[J][ci]  (transposed strided convolution).  Per axis
+// an even fine index has one source (J = p/2, o = 0) and an odd one two
+// (J = (p-1)/2, o = +1 and J = (p+1)/2, o = -1), so each node visits the 2^d
+// combinations of its candidates rather than all 3^d taps.
+template <int CO, int D, int TN>
 __global__ void __launch_bounds__(256) k_prolong_add(TransferParams p) {
-  using T = Tile<CO>;
+  using T = Tile<CO, TN>;
   const int co = threadIdx.x % CO;
   const int g = threadIdx.x / CO;
   const long long NF = p.dst_nodes;
@@ -297,30 +325,30 @@ __global__ void __launch_bounds__(256) k_prolong_add(TransferParams p) {
     node_xyz(c, p.fx, p.fy, px[k], py[k], pz[k]);
     acc[k] = make_float2(0.f, 0.f);
   }
-  constexpr int T3 = D == 3 ? 27 : 9;
-  for (int o = 0; o < T3; ++o) {
-    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = D == 3 ? o / 9 - 1 : 0;
-    long long ci_[T::TN];
-    bool ok[T::TN];
-    bool any = false;
+  constexpr int NCOMB = D == 3 ? 8 : 4;
+  for (int cb = 0; cb < NCOMB; ++cb) {
+    const int bx = cb & 1, by = (cb >> 1) & 1, bz = (cb >> 2) & 1;
 #pragma unroll
     for (int k = 0; k < T::TN; ++k) {
-      int x = px[k] - ox, y = py[k] - oy, z = D == 3 ? pz[k] - oz : 0;
-      bool even = ((x | y | z) & 1) == 0;
-      int X = x >> 1, Y = y >> 1, Z = z >> 1;
-      ok[k] = even && x >= 0 && y >= 0 && z >= 0 && X < p.cx && Y < p.cy && Z < p.cz;
-      ci_[k] = ok[k] ? ((long long)Z * p.cy + Y) * p.cx + X : 0;
-      any |= ok[k];
-    }
-    if (!__syncthreads_or(any)) continue;
-    const float2* w = p.Wt + (size_t)o * p.cin * CO;
-    for (int ci = 0; ci < p.cin; ++ci) {
-      const float2 wv = __ldg(w + ci * CO + co);
-#pragma unroll
-      for (int k = 0; k < T::TN; ++k) {
-        const float2 v = __ldg(ec + ci_[k] * p.cin + ci);
-        if (ok[k]) cfma(acc[k], wv, v);
+      // candidate along each axis: b = 0 -> o = 0 (even) or o = +1 (odd);
+      // b = 1 -> o = -1 (odd only)
+      int oxs = (px[k] & 1) ? (bx ? -1 : 1) : 0;
+      int oys = (py[k] & 1) ? (by ? -1 : 1) : 0;
+      int ozs = D == 3 ? ((pz[k] & 1) ? (bz ? -1 : 1) : 0) : 0;
+      bool valid = !((bx && !(px[k] & 1)) || (by && !(py[k] & 1)) || (D == 3 && bz && !(pz[k] & 1)));
+      int X = (px[k] - oxs) >> 1, Y = (py[k] - oys) >> 1, Z = D == 3 ? (pz[k] - ozs) >> 1 : 0;
+      valid = valid && X >= 0 && X < p.cx && Y >= 0 && Y < p.cy && Z >= 0 && Z < p.cz;
+      if (__syncthreads_or(valid) == 0) continue;
+      const int o = D == 3 ? ((ozs + 1) * 3 + (oys + 1)) * 3 + (oxs + 1) : (oys + 1) * 3 + (oxs + 1);
+      const float2* w = p.Wt + (size_t)o * p.cin * CO;
+      const float2* src = ec + (valid ? (((long long)Z * p.cy + Y) * p.cx + X) * p.cin : 0);
+      float2 a = make_float2(0.f, 0.f);
+      for (int ci = 0; ci < p.cin; ++ci) {
+        const float2 wv = __ldg(w + ci * CO + co);
+        const float2 v = __ldg(src + ci);
+        cfma(a, wv, v);
       }
+      if (valid) acc[k] = cadd(acc[k], a);
     }
   }
 #pragma unroll
@@ -328,16 +356,25 @@ __global__ void __launch_bounds__(256) k_prolong_add(TransferParams p) {
     if (nn[k] < NF) e[nn[k] * CO + co] = cadd(e[nn[k] * CO + co], acc[k]);
 }
 
-template <int CO, int D>
-static mcmg_status transfer_c(const TransferParams& p, bool restrict_, int nrhs, cudaStream_t st) {
-  using T = Tile<CO>;
+template <int CO, int D, int TN>
+static mcmg_status transfer_tn(const TransferParams& p, bool restrict_, int nrhs, cudaStream_t st) {
+  using T = Tile<CO, TN>;
   dim3 grid((unsigned)((p.dst_nodes + T::NB - 1) / T::NB), (unsigned)nrhs);
   if (restrict_)
-    k_restrict<CO, D><<<grid, 256, 0, st>>>(p);
+    k_restrict<CO, D, TN><<<grid, 256, 0, st>>>(p);
   else
-    k_prolong_add<CO, D><<<grid, 256, 0, st>>>(p);
+    k_prolong_add<CO, D, TN><<<grid, 256, 0, st>>>(p);
   MCMG_CHECK_LAUNCH(restrict_ ? "restrict" : "prolong_add");
   return MCMG_OK;
+}
+
+template <int CO, int D>
+static mcmg_status transfer_c(const TransferParams& p, bool restrict_, int nrhs, cudaStream_t st) {
+  switch (pick_tn(p.dst_nodes, CO, nrhs)) {
+    case 8: return transfer_tn<CO, D, 8>(p, restrict_, nrhs, st);
+    case 2: return transfer_tn<CO, D, 2>(p, restrict_, nrhs, st);
+    default: return transfer_tn<CO, D, 1>(p, restrict_, nrhs, st);
+  }
 }
 
 template <int D>

@@ -85,17 +85,32 @@ __global__ void __launch_bounds__(RED_T) k_multidot(const float2* __restrict__ V
   }
 }
 
-// out[i] = sum_b part[(b * width + i) * 2 + {0,1}]  (fixed order)
-__global__ void k_reduce_parts(const double* __restrict__ part, int nblk, int width,
-                               double2* __restrict__ out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= width) return;
+// Block-wide sum of two doubles (fixed order: per-thread strided partials,
+// warp shuffles, then warps in order).  Result valid in thread 0.
+__device__ __forceinline__ double2 block_sum2(double a, double b) {
+  __shared__ double sh[2][RED_T / 32];
+  a = warp_sum_d(a);
+  b = warp_sum_d(b);
+  const int wid = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { sh[0][wid] = a; sh[1][wid] = b; }
+  __syncthreads();
+  double ra = 0.0, rb = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < RED_T / 32; ++q) { ra += sh[0][q]; rb += sh[1][q]; }
+  return make_double2(ra, rb);
+}
+
+// out[i] = sum_b part[(b * width + i) * 2 + {0,1}]; one block per output i.
+__global__ void __launch_bounds__(RED_T) k_reduce_parts(const double* __restrict__ part, int nblk,
+                                                        int width, double2* __restrict__ out) {
+  const int i = blockIdx.x;
   double a = 0.0, b = 0.0;
-  for (int q = 0; q < nblk; ++q) {
+  for (int q = threadIdx.x; q < nblk; q += RED_T) {
     a += part[((size_t)q * width + i) * 2];
     b += part[((size_t)q * width + i) * 2 + 1];
   }
-  out[i] = make_double2(a, b);
+  const double2 r = block_sum2(a, b);
+  if (threadIdx.x == 0) out[i] = r;
 }
 
 // w -= sum_{i<k} h_i V_i  (FP64 accumulation per element); part[bx] = sum |w|^2.
@@ -130,24 +145,26 @@ __global__ void __launch_bounds__(RED_T) k_update(const float2* __restrict__ V, 
   }
 }
 
-__global__ void k_reduce_scalar(const double* __restrict__ part, int nblk, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double a = 0.0;
-    for (int q = 0; q < nblk; ++q) a += part[q];
-    *out = a;
-  }
+__global__ void __launch_bounds__(RED_T) k_reduce_scalar(const double* __restrict__ part, int nblk,
+                                                         double* out) {
+  double a = 0.0;
+  for (int q = threadIdx.x; q < nblk; q += RED_T) a += part[q];
+  const double2 r = block_sum2(a, 0.0);
+  if (threadIdx.x == 0) *out = r.x;
 }
 
 // Residual partials [nblk][2] -> rr, ff
-__global__ void k_reduce_res(const double* __restrict__ part, int nblk, double* __restrict__ dsc,
-                             double* __restrict__ stat_rr) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int q = 0; q < nblk; ++q) { a += part[2 * q]; b += part[2 * q + 1]; }
-    dsc[0] = a;
-    dsc[1] = b;
-    stat_rr[0] = a;
-    stat_rr[1] = b;
+__global__ void __launch_bounds__(RED_T) k_reduce_res(const double* __restrict__ part, int nblk,
+                                                      double* __restrict__ dsc,
+                                                      double* __restrict__ stat_rr) {
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < nblk; q += RED_T) { a += part[2 * q]; b += part[2 * q + 1]; }
+  const double2 r = block_sum2(a, b);
+  if (threadIdx.x == 0) {
+    dsc[0] = r.x;
+    dsc[1] = r.y;
+    stat_rr[0] = r.x;
+    stat_rr[1] = r.y;
   }
 }
 
@@ -310,9 +327,11 @@ struct Krylov {
   double t_solve = 0.0;
 };
 
+// Blocks of the grid-stride reductions: about four elements per thread, at
+// most two blocks per SM.
 static int red_blocks(long long n) {
-  long long b = (n + RED_T - 1) / RED_T;
-  long long cap = 148 * 4;
+  long long b = (n + 4 * RED_T - 1) / (4 * RED_T);
+  long long cap = 148 * 2;
   return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
@@ -370,7 +389,7 @@ void krylov_destroy(mcmg_handle_s* h, Krylov* k) {
 static mcmg_status enqueue_restart(Krylov* k) {
   mcmg_handle_s* h = k->h;
   MCMG_TRY(launch_residual64(h->q64, k->f, k->u, k->r64, k->part, k->nblk, h->g0, 1, k->st));
-  k_reduce_res<<<1, 32, 0, k->st>>>(k->part, k->nblk, k->dsc, &k->stat_d->rr);
+  k_reduce_res<<<1, RED_T, 0, k->st>>>(k->part, k->nblk, k->dsc, &k->stat_d->rr);
   MCMG_CHECK_LAUNCH("reduce_res");
   MCMG_CUDA(cudaEventRecord(k->ev, k->st));
   k->phase = Krylov::WAIT_RES;
@@ -382,7 +401,7 @@ static mcmg_status multidot(Krylov* k, int nv, bool self, double2* out) {
   dim3 grid((unsigned)k->nblk, (unsigned)((ktot + KV - 1) / KV));
   k_multidot<double2><<<grid, RED_T, 0, k->st>>>(k->V, k->n, nv, ktot, k->w, k->n, k->part);
   MCMG_CHECK_LAUNCH("multidot");
-  k_reduce_parts<<<(ktot + 127) / 128, 128, 0, k->st>>>(k->part, k->nblk, ktot, out);
+  k_reduce_parts<<<ktot, RED_T, 0, k->st>>>(k->part, k->nblk, ktot, out);
   MCMG_CHECK_LAUNCH("reduce_parts");
   return MCMG_OK;
 }
@@ -402,7 +421,7 @@ static mcmg_status enqueue_step(Krylov* k) {
   MCMG_TRY(multidot(k, j + 1, false, k->d2));
   k_update<double2><<<k->nblk, RED_T, 0, k->st>>>(k->V, n, j + 1, k->d2, k->w, n, k->part);
   MCMG_CHECK_LAUNCH("update");
-  k_reduce_scalar<<<1, 32, 0, k->st>>>(k->part, k->nblk, k->dsc + 3);
+  k_reduce_scalar<<<1, RED_T, 0, k->st>>>(k->part, k->nblk, k->dsc + 3);
   MCMG_CHECK_LAUNCH("reduce_scalar");
   k_givens<<<1, 32, 0, k->st>>>(j, k->m, k->d1, k->d2, k->dsc, k->H, k->cs, k->sn, k->g,
                                 k->stat_d);
@@ -540,12 +559,12 @@ mcmg_status cgs2_once(mcmg_handle_s* h, const float2* V, int kv, long long n, fl
       double2* dd = pass == 0 ? d1 : d2;
       k_multidot<float2><<<grid, RED_T, 0, st>>>(V, n, kv, kv, w, n, part);
       MCMG_CHECK_LAUNCH("multidot");
-      k_reduce_parts<<<(kv + 127) / 128, 128, 0, st>>>(part, nblk, kv, dd);
+      k_reduce_parts<<<kv, RED_T, 0, st>>>(part, nblk, kv, dd);
       MCMG_CHECK_LAUNCH("reduce_parts");
       k_update<float2><<<nblk, RED_T, 0, st>>>(V, n, kv, dd, w, n, part);
       MCMG_CHECK_LAUNCH("update");
     }
-    k_reduce_scalar<<<1, 32, 0, st>>>(part, nblk, dsc);
+    k_reduce_scalar<<<1, RED_T, 0, st>>>(part, nblk, dsc);
     MCMG_CHECK_LAUNCH("reduce_scalar");
     std::vector<double2> a(kv), b(kv);
     double nrm2 = 0.0;
@@ -579,7 +598,7 @@ mcmg_status cgs2_once(mcmg_handle_s* h, const float2* V, int kv, long long n, fl
 // it reads before reading it, so nothing depends on an earlier call's contents.
 // ---------------------------------------------------------------------------
 constexpr int NOALLOC_MAX_K = 64;                       // basis vectors per call
-constexpr int NOALLOC_MAX_BLK = 148 * 4;                // = red_blocks() cap
+constexpr int NOALLOC_MAX_BLK = 148 * 4;                // >= the red_blocks() cap
 constexpr size_t NOALLOC_PART = 2ull * NOALLOC_MAX_BLK * NOALLOC_MAX_K;
 constexpr size_t NOALLOC_DOUBLES = NOALLOC_PART + 4ull * NOALLOC_MAX_K + 8;
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
@@ -644,12 +663,12 @@ mcmg_status mcmg_cgs2_noalloc(const void* V_dev, int k, size_t n, void* w_dev, d
     double2* dd = pass == 0 ? d1 : d2;
     k_multidot<float2><<<grid, RED_T, 0, st>>>(V, nn, k, k, w, nn, part);
     MCMG_CHECK_LAUNCH("multidot");
-    k_reduce_parts<<<(k + 127) / 128, 128, 0, st>>>(part, nblk, k, dd);
+    k_reduce_parts<<<k, RED_T, 0, st>>>(part, nblk, k, dd);
     MCMG_CHECK_LAUNCH("reduce_parts");
     k_update<float2><<<nblk, RED_T, 0, st>>>(V, nn, k, dd, w, nn, part);
     MCMG_CHECK_LAUNCH("update");
   }
-  k_reduce_scalar<<<1, 32, 0, st>>>(part, nblk, dsc);
+  k_reduce_scalar<<<1, RED_T, 0, st>>>(part, nblk, dsc);
   MCMG_CHECK_LAUNCH("reduce_scalar");
   k_sum_coeffs<<<(k + 127) / 128, 128, 0, st>>>(d1, d2, k, part);   // part is free again
   MCMG_CHECK_LAUNCH("sum_coeffs");
