@@ -203,6 +203,12 @@ mcmg_status mcmg_drain(mcmg_ctx ctx);
 
 /* ---- single steps of the path (used by tests and diagnostics) ------------- */
 
+/* Wait for the device and read the handle's error word: 0 = fine; non-zero
+ * means a bounded wait inside a tensor-core kernel ran out (that kernel
+ * released its resources and skipped its output).  mcmg_solve reports the
+ * same condition as MCMG_ERR_TIMEOUT.                                        */
+mcmg_status mcmg_device_error(mcmg_handle h, int* code);
+
 /* y = h^2 A x (Eq. FDM_stencil with the sponge).  fp64 = 0: x, y dev c64;
  * fp64 = 1: x, y dev c128.  nrhs fields.                                     */
 mcmg_status mcmg_apply_A(mcmg_handle h, const void* x_dev, void* y_dev, int fp64,

@@ -385,6 +385,29 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
     if ((s = dev_alloc(h, h->arena, (void**)&lv.a, sizeof(float2) * lv.g.nodes() * C)) ||
         (s = dev_alloc(h, h->arena, (void**)&lv.s, sizeof(float2) * lv.g.nodes() * C)))
       return cleanup(), s;
+    lv.err = h->err_dev;
+    if (w->precision == MCMG_BF16 && tc_supported(C)) {
+      // BF16 tiles: taps, K_A, K_S, W^(i)
+      const int K2 = 2 * C;
+      const size_t tile = (size_t)K2 * K2;          // bf16 elements per tile
+      const int ntile = T + 2 + ns;
+      std::vector<uint16_t> host(tile * ntile);
+      std::vector<float2> mat((size_t)C * C);
+      auto put = [&](const double* src, int t) {
+        for (size_t i = 0; i < (size_t)C * C; ++i)
+          mat[i] = make_float2((float)src[2 * i], (float)src[2 * i + 1]);
+        pack_tc_tile(mat.data(), C, host.data() + tile * t);
+      };
+      for (int t = 0; t < T; ++t) put(lb[l].W + (size_t)2 * t * C * C, t);
+      put(lb[l].KA, T);
+      put(lb[l].KS, T + 1);
+      for (int i = 0; i < ns; ++i) put(lb[l].Ws + (size_t)2 * i * C * C, T + 2 + i);
+      if ((s = dev_alloc(h, h->arena, (void**)&lv.tcw.tiles, host.size() * sizeof(uint16_t))))
+        return cleanup(), s;
+      MCMG_CUDA(cudaMemcpy(lv.tcw.tiles, host.data(), host.size() * sizeof(uint16_t),
+                           cudaMemcpyHostToDevice));
+      lv.use_tc = true;
+    }
   }
   {
     std::vector<float2> vl(C0), vp(C0);
@@ -466,6 +489,10 @@ mcmg_status mcmg_setup(mcmg_ctx c, const mcmg_medium* m, double omega, const mcm
   h->device = c->device;
   cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaStreamCreate"); }
+  e = cudaHostAlloc((void**)&h->err_host, sizeof(int), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&h->err_dev, h->err_host, 0);
+  if (e != cudaSuccess) { mcmg_destroy(h); return cuda_fail(e, "error word"); }
+  *h->err_host = 0;
   mcmg_status s = setup_impl(c, m, omega, w, h);
   if (s != MCMG_OK) {
     mcmg_destroy(h);
@@ -483,6 +510,7 @@ mcmg_status mcmg_destroy(mcmg_handle h) {
   if (h->work) vwork_destroy(h, h->work);
   arena_free(h, h->arena);
   if (h->stream) cudaStreamDestroy(h->stream);
+  if (h->err_host) cudaFreeHost(h->err_host);
   delete h;
   return MCMG_OK;
 }
@@ -584,6 +612,14 @@ static mcmg_status check_level(mcmg_handle h, int level, bool need_next) {
     set_error("level %d out of range", level);
     return MCMG_ERR_ARG;
   }
+  return MCMG_OK;
+}
+
+mcmg_status mcmg_device_error(mcmg_handle h, int* code) {
+  if (!h || !code) { set_error("NULL argument"); return MCMG_ERR_ARG; }
+  MCMG_CUDA(cudaSetDevice(h->device));
+  MCMG_CUDA(cudaDeviceSynchronize());
+  *code = *(volatile int*)h->err_host;
   return MCMG_OK;
 }
 

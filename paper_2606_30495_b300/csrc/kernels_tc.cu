@@ -1,0 +1,523 @@
+// Fused smoothing step with the channel mixing on the 5th-generation tensor
+// cores (tcgen05, BF16 operands, FP32 accumulation in tensor memory).
+//
+// One CTA owns M = 128 consecutive nodes of a level and all C channels.  In
+// real form a complex C x C matrix is the 2C x 2C block matrix
+// [[Mr, -Mi], [Mi, Mr]] in interleaved (re, im) order, so every channel-mixing
+// convolution of Section 3.2 becomes a dense GEMM with K = N = 2C:
+//
+//   X = sum_tap E_tap W~_tap^T      (neural PDE operator stencil, 2d+1 taps)
+//   Y = E_0 K~_A^T                  (K_A applied to e)
+//   t = r - X - a (.) Y             (FP32, complex product per channel)
+//   Z = T K~_S^T,   z = s (.) Z
+//   U = Z W~_i^T,   e' = e + U
+//
+// E_tap holds e at each node's neighbour along the tap (zero outside the
+// grid).  A operands (E_tap, T, Z) and B operands (weights) live in shared
+// memory in the no-swizzle K-major core-matrix layout: for every 8-element
+// (16-byte) chunk of K, all rows are contiguous at a 16-byte stride, so an
+// 8-row core matrix is 128 contiguous bytes (SBO = 128 B) and consecutive K
+// chunks are one tile-height apart (LBO = rows * 16 B).  The tap loop is a
+// two-stage pipeline: while the MMAs of tap j run, all threads gather tap j+1
+// into the other buffer.  X, Y (then Z, U) occupy 2 * 2C TMEM columns.
+//
+// Every mbarrier wait is bounded: on timeout the CTA records an error code,
+// waits (bounded) for its own MMAs, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "mcmg_internal.cuh"
+
+namespace mcmg {
+
+namespace tc {
+
+constexpr int M = 128;           // nodes per CTA (MMA M)
+constexpr int THREADS = 256;     // 8 warps
+constexpr unsigned SPIN_LIMIT = 1u << 22;   // ~4M polls with a short sleep: well under a second
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;           // version
+  return d;                         // base offset 0, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t make_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_u32(bar)));
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Bounded wait for the phase with parity `parity` (non-blocking polls with a
+// short sleep); returns false when the bound runs out.
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (unsigned it = 0; it < SPIN_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (it > 64) __nanosleep(32);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+}  // namespace tc
+
+struct TcParams {
+  const float2* r;
+  const float2* e_in;     // null: e = 0 (first pre-smoothing step)
+  float2* e_out;
+  const float2* a;
+  const float2* s;
+  const uint4* Wtap;      // [T] tiles, each K2*K2 bf16 in the core-matrix layout
+  const uint4* KA;
+  const uint4* KS;
+  const uint4* Wi;        // W^(i) of this step
+  int nx, ny, nz;
+  long long nodes;
+  int* err;               // error word (mapped host memory), may be null
+};
+
+// Gather an A tile: row i = node n0 + i, value = src field at the neighbour
+// along `tap` (0 = the node itself), as BF16 in the core-matrix layout.
+// Rows outside the grid or whose neighbour is outside are zero.
+template <int K2, int D>
+__device__ __forceinline__ void gather_tile(uint8_t* dst, const float2* __restrict__ src,
+                                            long long n0, const TcParams& p, int tap) {
+  constexpr int CH = K2 / 8;                 // 16-byte chunks per row
+  const long long sxy = (long long)p.nx * p.ny;
+  for (int idx = threadIdx.x; idx < tc::M * CH; idx += tc::THREADS) {
+    const int row = idx % tc::M;
+    const int ch = idx / tc::M;
+    const long long n = n0 + row;
+    uint4 out = make_uint4(0, 0, 0, 0);
+    if (n < p.nodes) {
+      long long nb = n;
+      bool ok = true;
+      if (tap > 0) {
+        const int axis = (tap - 1) >> 1;
+        const int sgn = (tap & 1) ? -1 : 1;
+        int x = (int)(n % p.nx);
+        long long rest = n / p.nx;
+        int y = (int)(rest % p.ny);
+        int z = (int)(rest / p.ny);
+        int c = axis == 0 ? x : (axis == 1 ? y : z);
+        int ext = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
+        long long stride = axis == 0 ? 1 : (axis == 1 ? p.nx : sxy);
+        ok = (c + sgn >= 0) && (c + sgn < ext);
+        nb = n + sgn * stride;
+      }
+      if (ok) {
+        const float4* q = reinterpret_cast<const float4*>(src + nb * (K2 / 2) + ch * 4);
+        const float4 u = __ldg(q), v = __ldg(q + 1);
+        out.x = tc::pack_bf16(u.x, u.y);
+        out.y = tc::pack_bf16(u.z, u.w);
+        out.z = tc::pack_bf16(v.x, v.y);
+        out.w = tc::pack_bf16(v.z, v.w);
+      }
+    }
+    *reinterpret_cast<uint4*>(dst + (size_t)ch * tc::M * 16 + (size_t)row * 16) = out;
+  }
+}
+
+// Copy a weight tile (already in the core-matrix layout) to shared memory.
+template <int K2>
+__device__ __forceinline__ void copy_tile(uint8_t* dst, const uint4* __restrict__ src) {
+  constexpr int N16 = K2 * K2 * 2 / 16;
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  for (int i = threadIdx.x; i < N16; i += tc::THREADS) d[i] = __ldg(src + i);
+}
+
+// MMAs of one GEMM: D[128 x K2] (+)= A[128 x K2] B[K2 x K2]^T, K in steps of 16.
+template <int K2>
+__device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const uint8_t* A, const uint8_t* B,
+                                           bool accumulate) {
+  constexpr uint32_t idesc = tc::make_idesc(tc::M, K2);
+  const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(B);
+  const uint32_t lbo_a = tc::M * 16, lbo_b = K2 * 16;
+#pragma unroll
+  for (int s = 0; s < K2 / 16; ++s) {
+    const uint64_t ad = tc::make_desc(a0 + 2 * s * lbo_a, lbo_a, 128);
+    const uint64_t bd = tc::make_desc(b0 + 2 * s * lbo_b, lbo_b, 128);
+    tc::mma_bf16(d_tmem, ad, bd, idesc, (accumulate || s > 0) ? 1u : 0u);
+  }
+}
+
+template <int K2, int D>
+__global__ void __launch_bounds__(tc::THREADS, 1) k_smooth_tc(TcParams p) {
+  constexpr int C = K2 / 2;
+  constexpr int NT = 2 * D + 1;
+  constexpr uint32_t TM_COLS = (2 * K2 < 32) ? 32 : 2 * K2;   // power of two for K2 >= 16
+  constexpr size_t A_BYTES = (size_t)tc::M * K2 * 2;
+  constexpr size_t B_BYTES = (size_t)K2 * K2 * 2;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* A0 = smem;
+  uint8_t* A1 = A0 + A_BYTES;
+  uint8_t* B0 = A1 + A_BYTES;
+  uint8_t* B1 = B0 + B_BYTES;
+  uint8_t* BK = B1 + B_BYTES;
+  __shared__ uint64_t bars[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int fail_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long N = p.nodes;
+  const size_t off = (size_t)blockIdx.y * (size_t)N * C;
+  const float2* r = p.r + off;
+  const float2* ein = p.e_in ? p.e_in + off : nullptr;
+  float2* eout = p.e_out + off;
+  const long long n0 = (long long)blockIdx.x * tc::M;
+
+  if (threadIdx.x == 0) {
+    tc::bar_init(&bars[0], 1);
+    tc::bar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    fail_sh = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     tc::smem_u32(&tmem_base_sh)),
+                 "r"(TM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const uint32_t tX = tmem, tY = tmem + K2;    // later Z in tX, U in tY
+  uint32_t phase[2] = {0, 0};
+  int commits = 0;                               // MMA batches committed (for the final wait)
+  int last_bar = 0;
+  bool ok = true;
+
+  auto wait_bar = [&](int b) -> bool {
+    bool w = tc::bar_wait(&bars[b], phase[b]);
+    phase[b] ^= 1;
+    return w;
+  };
+
+  // ---------------- phase 1: X = sum_tap E_tap W~_tap^T, Y = E_0 K~_A^T ----------------
+  if (ein) {
+    gather_tile<K2, D>(A0, ein, n0, p, 0);
+    copy_tile<K2>(B0, p.Wtap);
+    copy_tile<K2>(BK, p.KA);
+    tc::fence_async_smem();
+    __syncthreads();
+    for (int j = 0; j < NT && ok; ++j) {
+      const int b = j & 1;
+      if (threadIdx.x == 0) {
+        tc::fence_after();
+        issue_gemm<K2>(tX, b ? A1 : A0, b ? B1 : B0, j > 0);
+        if (j == 0) issue_gemm<K2>(tY, A0, BK, false);
+        tc::mma_commit(&bars[b]);
+      }
+      ++commits;
+      last_bar = b;
+      if (j + 1 < NT) {
+        const int nb = (j + 1) & 1;
+        if (j >= 1 && !wait_bar(nb)) { ok = false; break; }   // buffers of tap j-1 are free
+        gather_tile<K2, D>(nb ? A1 : A0, ein, n0, p, j + 1);
+        copy_tile<K2>(nb ? B1 : B0, p.Wtap + (size_t)(j + 1) * (B_BYTES / 16));
+        tc::fence_async_smem();
+        __syncthreads();
+      }
+    }
+    // wait for every committed batch not yet waited on
+    if (ok) {
+      // taps 0..NT-1 committed on bars[j & 1]; the loop waited on bars for j-1 >= 0 up to
+      // NT-2's predecessor.  Outstanding: the last two commits.
+      if (NT >= 2 && !wait_bar((NT - 2) & 1)) ok = false;
+      if (ok && !wait_bar((NT - 1) & 1)) ok = false;
+    }
+    if (!ok) goto fail;
+    tc::fence_after();
+    // ---- epilogue 1: t = r - X - a (.) Y -> BF16 into A0
+    {
+      const int q = warp & 3, half = warp >> 2;
+      const int row = 32 * q + lane;
+      const long long n = n0 + row;
+      const long long nc = n < N ? n : N - 1;
+      constexpr int HC = K2 / 2;                 // columns per warp half
+      constexpr int STEP = HC < 16 ? HC : 16;
+      for (int c0 = half * HC; c0 < (half + 1) * HC; c0 += STEP) {
+        float x[16], y[16];
+        const uint32_t lanebits = (uint32_t)(32 * q) << 16;
+        if (STEP == 16) {
+          tc::tmem_ld16(tX + lanebits + c0, x);
+          tc::tmem_ld16(tY + lanebits + c0, y);
+        } else {
+          tc::tmem_ld8(tX + lanebits + c0, x);
+          tc::tmem_ld8(tY + lanebits + c0, y);
+        }
+        uint32_t pk[8];
+#pragma unroll
+        for (int k = 0; k < STEP / 2; ++k) {
+          const int ch = c0 / 2 + k;
+          const float2 rv = r[nc * C + ch];
+          const float2 av = p.a[nc * C + ch];
+          const float tr = rv.x - x[2 * k] - (av.x * y[2 * k] - av.y * y[2 * k + 1]);
+          const float ti = rv.y - x[2 * k + 1] - (av.x * y[2 * k + 1] + av.y * y[2 * k]);
+          pk[k] = (n < N) ? tc::pack_bf16(tr, ti) : 0u;
+        }
+#pragma unroll
+        for (int k8 = 0; k8 < STEP / 8; ++k8) {
+          const int chunk = (c0 + 8 * k8) / 8;
+          *reinterpret_cast<uint4*>(A0 + (size_t)chunk * tc::M * 16 + (size_t)row * 16) =
+              make_uint4(pk[4 * k8], pk[4 * k8 + 1], pk[4 * k8 + 2], pk[4 * k8 + 3]);
+        }
+      }
+    }
+  } else {
+    // first pre-smoothing step: t = r
+    gather_tile<K2, D>(A0, r, n0, p, 0);
+  }
+
+  // ---------------- phase 2: Z = T K~_S^T, z = s (.) Z -> BF16 into A1 ----------------
+  copy_tile<K2>(B0, p.KS);
+  tc::fence_before();
+  tc::fence_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc::fence_after();
+    issue_gemm<K2>(tX, A0, B0, false);
+    tc::mma_commit(&bars[0]);
+  }
+  if (!wait_bar(0)) { ok = false; goto fail; }
+  tc::fence_after();
+  {
+    const int q = warp & 3, half = warp >> 2;
+    const int row = 32 * q + lane;
+    const long long n = n0 + row;
+    const long long nc = n < N ? n : N - 1;
+    constexpr int HC = K2 / 2;
+    constexpr int STEP = HC < 16 ? HC : 16;
+    for (int c0 = half * HC; c0 < (half + 1) * HC; c0 += STEP) {
+      float zv[16];
+      const uint32_t lanebits = (uint32_t)(32 * q) << 16;
+      if (STEP == 16) tc::tmem_ld16(tX + lanebits + c0, zv);
+      else tc::tmem_ld8(tX + lanebits + c0, zv);
+      uint32_t pk[8];
+#pragma unroll
+      for (int k = 0; k < STEP / 2; ++k) {
+        const float2 sv = p.s[nc * C + c0 / 2 + k];
+        const float zr = sv.x * zv[2 * k] - sv.y * zv[2 * k + 1];
+        const float zi = sv.x * zv[2 * k + 1] + sv.y * zv[2 * k];
+        pk[k] = (n < N) ? tc::pack_bf16(zr, zi) : 0u;
+      }
+#pragma unroll
+      for (int k8 = 0; k8 < STEP / 8; ++k8) {
+        const int chunk = (c0 + 8 * k8) / 8;
+        *reinterpret_cast<uint4*>(A1 + (size_t)chunk * tc::M * 16 + (size_t)row * 16) =
+            make_uint4(pk[4 * k8], pk[4 * k8 + 1], pk[4 * k8 + 2], pk[4 * k8 + 3]);
+      }
+    }
+  }
+
+  // ---------------- phase 3: U = Z W~_i^T, e' = e + U ----------------
+  copy_tile<K2>(B1, p.Wi);
+  tc::fence_before();
+  tc::fence_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc::fence_after();
+    issue_gemm<K2>(tY, A1, B1, false);
+    tc::mma_commit(&bars[1]);
+  }
+  if (!wait_bar(1)) { ok = false; goto fail; }
+  tc::fence_after();
+  {
+    const int q = warp & 3, half = warp >> 2;
+    const int row = 32 * q + lane;
+    const long long n = n0 + row;
+    constexpr int HC = K2 / 2;
+    constexpr int STEP = HC < 16 ? HC : 16;
+    for (int c0 = half * HC; c0 < (half + 1) * HC; c0 += STEP) {
+      float u[16];
+      const uint32_t lanebits = (uint32_t)(32 * q) << 16;
+      if (STEP == 16) tc::tmem_ld16(tY + lanebits + c0, u);
+      else tc::tmem_ld8(tY + lanebits + c0, u);
+      if (n < N) {
+#pragma unroll
+        for (int k = 0; k < STEP / 2; ++k) {
+          const int ch = c0 / 2 + k;
+          float2 v = make_float2(u[2 * k], u[2 * k + 1]);
+          if (ein) v = cadd(v, ein[n * C + ch]);
+          eout[n * C + ch] = v;
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(TM_COLS));
+  }
+  return;
+
+fail:
+  // a bounded wait ran out: record it, give the MMAs a last bounded chance to
+  // finish, release tensor memory and leave.
+  if (p.err) atomicOr(p.err, 1);
+  tc::bar_wait(&bars[0], phase[0]);
+  tc::bar_wait(&bars[1], phase[1]);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(TM_COLS));
+  }
+  (void)commits;
+  (void)last_bar;
+}
+
+// Dynamic shared memory: two A tiles, three B tiles, alignment slack.  It is
+// at least A + 36 KB, so that an A descriptor read with its two strides
+// exchanged (16 row groups 2 KB apart) would still stay inside the allocation.
+template <int K2, int D>
+static size_t tc_smem_bytes() {
+  const size_t need = 2 * (size_t)tc::M * K2 * 2 + 3 * (size_t)K2 * K2 * 2 + 1024;
+  const size_t guard = (size_t)tc::M * K2 * 2 + 36 * 1024;
+  return need > guard ? need : guard;
+}
+
+template <int K2, int D>
+static mcmg_status tc_launch(const TcParams& p, int nrhs, cudaStream_t st) {
+  const size_t smem = tc_smem_bytes<K2, D>();
+  static bool attr_set = false;   // one attribute call per instantiation
+  if (!attr_set) {
+    MCMG_CUDA(cudaFuncSetAttribute(k_smooth_tc<K2, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+    attr_set = true;
+  }
+  dim3 grid((unsigned)((p.nodes + tc::M - 1) / tc::M), (unsigned)nrhs);
+  k_smooth_tc<K2, D><<<grid, tc::THREADS, smem, st>>>(p);
+  MCMG_CHECK_LAUNCH("smooth_tc");
+  return MCMG_OK;
+}
+
+bool tc_supported(int C) { return C == 8 || C == 16 || C == 32 || C == 64; }
+
+mcmg_status launch_smooth_tc(const Level& L, const TcWeights& W, int step, const float2* r,
+                             const float2* e_in, float2* e_out, int nrhs, int* err,
+                             cudaStream_t st) {
+  TcParams p;
+  p.r = r;
+  p.e_in = e_in;
+  p.e_out = e_out;
+  p.a = L.a;
+  p.s = L.s;
+  const size_t tile16 = (size_t)(2 * L.C) * (2 * L.C) * 2 / 16;
+  p.Wtap = W.tiles;
+  p.KA = W.tiles + (size_t)(2 * L.g.d + 1) * tile16;
+  p.KS = p.KA + tile16;
+  p.Wi = p.KS + tile16 * (1 + step);
+  p.nx = L.g.nx;
+  p.ny = L.g.ny;
+  p.nz = L.g.nz;
+  p.nodes = L.g.nodes();
+  p.err = err;
+  const bool d3 = L.g.d == 3;
+  switch (L.C) {
+    case 8: return d3 ? tc_launch<16, 3>(p, nrhs, st) : tc_launch<16, 2>(p, nrhs, st);
+    case 16: return d3 ? tc_launch<32, 3>(p, nrhs, st) : tc_launch<32, 2>(p, nrhs, st);
+    case 32: return d3 ? tc_launch<64, 3>(p, nrhs, st) : tc_launch<64, 2>(p, nrhs, st);
+    case 64: return d3 ? tc_launch<128, 3>(p, nrhs, st) : tc_launch<128, 2>(p, nrhs, st);
+  }
+  set_error("tensor-core smoothing needs C in {8, 16, 32, 64}, got %d", L.C);
+  return MCMG_ERR_SHAPE;
+}
+
+// Host: a complex C x C matrix M[co][ci] (float2, row-major) -> its real
+// 2C x 2C block form as BF16 in the core-matrix layout of a B operand
+// (row n = output index, K = input index, chunk-major).
+void pack_tc_tile(const float2* Mc, int C, uint16_t* out) {
+  const int K2 = 2 * C;
+  for (int n = 0; n < K2; ++n)
+    for (int k = 0; k < K2; ++k) {
+      const float2 m = Mc[(size_t)(n >> 1) * C + (k >> 1)];
+      float v;
+      if ((n & 1) == 0) v = (k & 1) == 0 ? m.x : -m.y;   // re out: Mr re_in - Mi im_in
+      else v = (k & 1) == 0 ? m.y : m.x;                 // im out: Mi re_in + Mr im_in
+      __nv_bfloat16 b = __float2bfloat16_rn(v);
+      const size_t pos = ((size_t)(k >> 3) * K2 + n) * 8 + (k & 7);
+      out[pos] = *reinterpret_cast<uint16_t*>(&b);
+    }
+}
+
+}  // namespace mcmg

@@ -224,6 +224,8 @@ static mcmg_status smooth_d(const SmoothParams& p, int C, int mode, int nrhs, cu
 
 mcmg_status launch_smooth(const Level& L, int step, const float2* r, const float2* e_in,
                           float2* e_out, int mode, int nrhs, cudaStream_t st) {
+  if (mode == 0 && L.use_tc)
+    return launch_smooth_tc(L, L.tcw, step, r, e_in, e_out, nrhs, L.err, st);
   SmoothParams p;
   p.r = r;
   p.e_in = e_in;

@@ -483,6 +483,12 @@ mcmg_status krylov_advance(Krylov* k, bool blocking, int* done) {
   }
   Stat st;
   std::memcpy(&st, (const void*)k->stat_h, sizeof(Stat));
+  if (k->h->err_host && *(volatile int*)k->h->err_host) {
+    set_error("a bounded wait in a tensor-core kernel ran out (code %d)", *k->h->err_host);
+    finish(k, false, MCMG_ERR_TIMEOUT);
+    *done = 1;
+    return MCMG_OK;
+  }
   if (k->phase == Krylov::WAIT_RES) {
     if (k->fnorm < 0.0) k->fnorm = std::sqrt(st.ff);
     const double beta = std::sqrt(st.rr);

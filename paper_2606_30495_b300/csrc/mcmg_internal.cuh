@@ -69,6 +69,13 @@ struct Grid {
   __host__ __device__ Grid coarse() const { return Grid{d, nx / 2, ny / 2, d == 3 ? nz / 2 : 1}; }
 };
 
+// BF16 weight tiles of one level for the tensor-core smoothing step: the real
+// 2C x 2C block form of every mixing matrix, in the shared-memory core-matrix
+// layout, stored [stencil taps][K_A][K_S][W^(i) per step].
+struct TcWeights {
+  uint4* tiles = nullptr;
+};
+
 // Read-only per-level state: features and weights.  Mixing matrices are
 // stored transposed, M^T[ci][co], so consecutive output channels are
 // contiguous.
@@ -84,7 +91,17 @@ struct Level {
   float2* Wsmt = nullptr;     // [nsteps][C][C]
   float2* Rt = nullptr;       // [T3][C][Cn]
   float2* Pt = nullptr;       // [T3][Cn][C]
+  bool use_tc = false;        // smoothing step on tcgen05 (BF16 mixing)
+  TcWeights tcw;
+  int* err = nullptr;         // device view of the handle's error word
 };
+
+// tensor-core smoothing (kernels_tc.cu)
+bool tc_supported(int C);
+mcmg_status launch_smooth_tc(const Level& L, const TcWeights& W, int step, const float2* r,
+                             const float2* e_in, float2* e_out, int nrhs, int* err,
+                             cudaStream_t st);
+void pack_tc_tile(const float2* Mc, int C, uint16_t* out);
 
 // Launchers used by the V-cycle (kernels_vcycle.cu), asynchronous on `st`.
 // mode 0: e_out = e_in + S^(step)(r - A e_in); mode 1: e_out = r - A e_in.
@@ -193,4 +210,6 @@ struct mcmg_handle_s {
   mcmg::Krylov* kry = nullptr;  // for mcmg_solve
   cudaStream_t stream = nullptr;
   std::mutex mu;                // serialises synchronous use of work / kry
+  int* err_host = nullptr;      // error word, mapped pinned (bounded waits that ran out)
+  int* err_dev = nullptr;
 };

@@ -73,6 +73,7 @@ _SIGS = {
     "mcmg_poll": [_P, C.c_uint64, C.POINTER(SolveInfo)],
     "mcmg_drain": [_P],
     "mcmg_apply_A": [_P, _P, _P, C.c_int, C.c_int, _P],
+    "mcmg_device_error": [_P, C.POINTER(C.c_int)],
     "mcmg_get_feature": [_P, C.c_int, C.c_int, _P],
     "mcmg_lift": [_P, _P, _P, C.c_int, _P],
     "mcmg_project": [_P, _P, _P, C.c_int, _P],
@@ -278,6 +279,11 @@ class Handle:
         if st not in (MCMG_OK, -5):
             _check(st)
         return st, info.as_dict()
+
+    def device_error(self) -> int:
+        v = C.c_int()
+        _check(self.lib.mcmg_device_error(self.h, C.byref(v)))
+        return v.value
 
     def apply_A(self, x, y, fp64=False, nrhs=1, stream=None):
         _check(self.lib.mcmg_apply_A(self.h, ptr(x), ptr(y), int(fp64), nrhs, _stream(stream)))
