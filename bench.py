@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--workload", default="helm2d_n256_grf")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-iters", type=int, default=12)
+    p.add_argument("--n", type=int, default=0,
+                   help="override the grid size (smaller copies of a workload for profiling)")
+    p.add_argument("--max-iters", type=int, default=0)
     return p.parse_args()
 
 
@@ -111,9 +114,9 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def setup_workload(name):
+def setup_workload(name, n=0):
     from paper_2606_30495_b300 import inputs as I
-    wl = I.workload(name)
+    wl = I.workload(name, **({"n": n} if n else {}))
     c = I.medium_for(wl)
     omega = I.omega_for_ppw(c.min(), wl["ppw"], wl["n"])
     w = I.weights_for(wl)
@@ -204,7 +207,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl, c, omega, w = setup_workload(args.workload)
+    wl, c, omega, w = setup_workload(args.workload, args.n)
     iters, src = golden_iters(args.workload)
     if iters is None:
         print(json.dumps({"impl": "reference", "unavailable":
@@ -255,8 +258,8 @@ def main():
     from paper_2606_30495_b300 import inputs as I
     from paper_2606_30495_b300 import mcmg
 
-    wl, c, omega, w = setup_workload(args.workload)
-    sp = dict(restart=wl["restart"], max_iters=MAX_ITERS[args.workload])
+    wl, c, omega, w = setup_workload(args.workload, args.n)
+    sp = dict(restart=wl["restart"], max_iters=args.max_iters or MAX_ITERS[args.workload])
     prec = mcmg.BF16 if wl["precision"] == "bf16" else mcmg.FP32
     ctx = mcmg.Context(local)
     t0 = time.perf_counter()

@@ -216,22 +216,75 @@ __device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const uint8_t* A, co
   }
 }
 
+// Load the 16-byte chunk `ch` of row `row` of a tap's A tile (BF16 of the
+// neighbour's e, zero outside the grid) into a register.
+template <int K2>
+__device__ __forceinline__ uint4 load_chunk(const float2* __restrict__ src, long long n0, int row,
+                                            int ch, const TcParams& p, int tap) {
+  const long long n = n0 + row;
+  uint4 out = make_uint4(0, 0, 0, 0);
+  if (n >= p.nodes) return out;
+  long long nb = n;
+  if (tap > 0) {
+    const int axis = (tap - 1) >> 1;
+    const int sgn = (tap & 1) ? -1 : 1;
+    const int x = (int)(n % p.nx);
+    const long long rest = n / p.nx;
+    const int y = (int)(rest % p.ny);
+    const int z = (int)(rest / p.ny);
+    const int c = axis == 0 ? x : (axis == 1 ? y : z);
+    const int ext = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
+    const long long stride = axis == 0 ? 1 : (axis == 1 ? p.nx : (long long)p.nx * p.ny);
+    if (c + sgn < 0 || c + sgn >= ext) return out;
+    nb = n + sgn * stride;
+  }
+  const float4* q = reinterpret_cast<const float4*>(src + nb * (K2 / 2) + ch * 4);
+  const float4 u = __ldg(q), v = __ldg(q + 1);
+  out.x = tc::pack_bf16(u.x, u.y);
+  out.y = tc::pack_bf16(u.z, u.w);
+  out.z = tc::pack_bf16(v.x, v.y);
+  out.w = tc::pack_bf16(v.z, v.w);
+  return out;
+}
+
+__device__ __forceinline__ void store_chunk(uint8_t* tile, int row, int ch, uint4 v) {
+  *reinterpret_cast<uint4*>(tile + (size_t)ch * tc::M * 16 + (size_t)row * 16) = v;
+}
+
+// Epilogue thread mapping: warp w reads TMEM lanes 32 (w % 4) .. + 31 (one node
+// per lane) and the column half w / 4.
+template <int K2>
+struct Epi {
+  static constexpr int HC = K2 / 2;                  // FP32 columns per half
+  static constexpr int STEP = HC < 16 ? HC : 16;     // columns per TMEM load
+  static constexpr int NCH = HC / 2;                 // complex channels per thread
+};
+
+template <int K2>
+__device__ __forceinline__ void tmem_cols(uint32_t taddr, float* v) {
+  if (Epi<K2>::STEP == 16) tc::tmem_ld16(taddr, v);
+  else tc::tmem_ld8(taddr, v);
+}
+
 template <int K2, int D>
-__global__ void __launch_bounds__(tc::THREADS, 1) k_smooth_tc(TcParams p) {
+__global__ void __launch_bounds__(tc::THREADS) k_smooth_tc(TcParams p) {
   constexpr int C = K2 / 2;
   constexpr int NT = 2 * D + 1;
-  constexpr uint32_t TM_COLS = (2 * K2 < 32) ? 32 : 2 * K2;   // power of two for K2 >= 16
+  constexpr int NA = 2;                      // A tiles (double buffer)
+  constexpr uint32_t TM_COLS = (2 * K2 < 32) ? 32 : 2 * K2;
   constexpr size_t A_BYTES = (size_t)tc::M * K2 * 2;
   constexpr size_t B_BYTES = (size_t)K2 * K2 * 2;
+  constexpr int CH = K2 / 8;                         // 16-byte chunks per row
+  constexpr int PER = tc::M * CH / tc::THREADS;      // chunks per thread per tile (>= 1)
+  static_assert(PER >= 1, "tile smaller than the block");
+  using E = Epi<K2>;
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* A0 = smem;
-  uint8_t* A1 = A0 + A_BYTES;
-  uint8_t* B0 = A1 + A_BYTES;
-  uint8_t* B1 = B0 + B_BYTES;
-  uint8_t* BK = B1 + B_BYTES;
+  uint8_t* Abase = smem;
+  uint8_t* Bbase = smem + NA * A_BYTES;
+  auto Atile = [&](int i) { return Abase + (size_t)i * A_BYTES; };
+  auto Btile = [&](int i) { return Bbase + (size_t)i * B_BYTES; };
   __shared__ uint64_t bars[2];
   __shared__ uint32_t tmem_base_sh;
-  __shared__ int fail_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long N = p.nodes;
@@ -240,12 +293,18 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_smooth_tc(TcParams p) {
   const float2* ein = p.e_in ? p.e_in + off : nullptr;
   float2* eout = p.e_out + off;
   const long long n0 = (long long)blockIdx.x * tc::M;
+  // epilogue mapping
+  const int q4 = warp & 3, half = warp >> 2;
+  const int erow = 32 * q4 + lane;
+  const long long en = n0 + erow;
+  const long long enc = en < N ? en : N - 1;
+  const uint32_t lanebits = (uint32_t)(32 * q4) << 16;
+  const int cbase = half * E::HC;                    // first FP32 column of this thread
 
   if (threadIdx.x == 0) {
     tc::bar_init(&bars[0], 1);
     tc::bar_init(&bars[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    fail_sh = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -257,165 +316,144 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_smooth_tc(TcParams p) {
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_base_sh;
-  const uint32_t tX = tmem, tY = tmem + K2;    // later Z in tX, U in tY
+  const uint32_t tX = tmem, tY = tmem + K2;          // later Z in tX, U in tY
   uint32_t phase[2] = {0, 0};
-  int commits = 0;                               // MMA batches committed (for the final wait)
-  int last_bar = 0;
   bool ok = true;
-
   auto wait_bar = [&](int b) -> bool {
-    bool w = tc::bar_wait(&bars[b], phase[b]);
+    const bool w = tc::bar_wait(&bars[b], phase[b]);
     phase[b] ^= 1;
     return w;
   };
 
   // ---------------- phase 1: X = sum_tap E_tap W~_tap^T, Y = E_0 K~_A^T ----------------
   if (ein) {
-    gather_tile<K2, D>(A0, ein, n0, p, 0);
-    copy_tile<K2>(B0, p.Wtap);
-    copy_tile<K2>(BK, p.KA);
-    tc::fence_async_smem();
-    __syncthreads();
-    for (int j = 0; j < NT && ok; ++j) {
-      const int b = j & 1;
-      if (threadIdx.x == 0) {
-        tc::fence_after();
-        issue_gemm<K2>(tX, b ? A1 : A0, b ? B1 : B0, j > 0);
-        if (j == 0) issue_gemm<K2>(tY, A0, BK, false);
-        tc::mma_commit(&bars[b]);
+    {
+      gather_tile<K2, D>(Atile(0), ein, n0, p, 0);
+      copy_tile<K2>(Btile(0), p.Wtap);
+      copy_tile<K2>(Btile(2), p.KA);
+      tc::fence_async_smem();
+      __syncthreads();
+      for (int j = 0; j < NT && ok; ++j) {
+        const int b = j & 1;
+        if (threadIdx.x == 0) {
+          tc::fence_after();
+          issue_gemm<K2>(tX, Atile(b), Btile(b), j > 0);
+          if (j == 0) issue_gemm<K2>(tY, Atile(0), Btile(2), false);
+          tc::mma_commit(&bars[b]);
+        }
+        if (j + 1 < NT) {
+          const int nb = (j + 1) & 1;
+          if (j >= 1 && !wait_bar(nb)) { ok = false; break; }   // buffers of tap j-1 free
+          gather_tile<K2, D>(Atile(nb), ein, n0, p, j + 1);
+          copy_tile<K2>(Btile(nb), p.Wtap + (size_t)(j + 1) * (B_BYTES / 16));
+          tc::fence_async_smem();
+          __syncthreads();
+        }
       }
-      ++commits;
-      last_bar = b;
-      if (j + 1 < NT) {
-        const int nb = (j + 1) & 1;
-        if (j >= 1 && !wait_bar(nb)) { ok = false; break; }   // buffers of tap j-1 are free
-        gather_tile<K2, D>(nb ? A1 : A0, ein, n0, p, j + 1);
-        copy_tile<K2>(nb ? B1 : B0, p.Wtap + (size_t)(j + 1) * (B_BYTES / 16));
-        tc::fence_async_smem();
-        __syncthreads();
-      }
-    }
-    // wait for every committed batch not yet waited on
-    if (ok) {
-      // taps 0..NT-1 committed on bars[j & 1]; the loop waited on bars for j-1 >= 0 up to
-      // NT-2's predecessor.  Outstanding: the last two commits.
-      if (NT >= 2 && !wait_bar((NT - 2) & 1)) ok = false;
-      if (ok && !wait_bar((NT - 1) & 1)) ok = false;
+      // outstanding: the commits of taps NT-2 and NT-1
+      if (ok) ok = wait_bar((NT - 2) & 1);
+      if (ok) ok = wait_bar((NT - 1) & 1);
     }
     if (!ok) goto fail;
     tc::fence_after();
-    // ---- epilogue 1: t = r - X - a (.) Y -> BF16 into A0
-    {
-      const int q = warp & 3, half = warp >> 2;
-      const int row = 32 * q + lane;
-      const long long n = n0 + row;
-      const long long nc = n < N ? n : N - 1;
-      constexpr int HC = K2 / 2;                 // columns per warp half
-      constexpr int STEP = HC < 16 ? HC : 16;
-      for (int c0 = half * HC; c0 < (half + 1) * HC; c0 += STEP) {
-        float x[16], y[16];
-        const uint32_t lanebits = (uint32_t)(32 * q) << 16;
-        if (STEP == 16) {
-          tc::tmem_ld16(tX + lanebits + c0, x);
-          tc::tmem_ld16(tY + lanebits + c0, y);
-        } else {
-          tc::tmem_ld8(tX + lanebits + c0, x);
-          tc::tmem_ld8(tY + lanebits + c0, y);
-        }
-        uint32_t pk[8];
+    // ---- epilogue 1: t = r - X - a (.) Y -> BF16 into A tile 0
+    for (int c0 = cbase; c0 < cbase + E::HC; c0 += E::STEP) {
+      float x[16], y[16];
+      tmem_cols<K2>(tX + lanebits + c0, x);
+      tmem_cols<K2>(tY + lanebits + c0, y);
+      uint32_t pk[8];
 #pragma unroll
-        for (int k = 0; k < STEP / 2; ++k) {
-          const int ch = c0 / 2 + k;
-          const float2 rv = r[nc * C + ch];
-          const float2 av = p.a[nc * C + ch];
-          const float tr = rv.x - x[2 * k] - (av.x * y[2 * k] - av.y * y[2 * k + 1]);
-          const float ti = rv.y - x[2 * k + 1] - (av.x * y[2 * k + 1] + av.y * y[2 * k]);
-          pk[k] = (n < N) ? tc::pack_bf16(tr, ti) : 0u;
-        }
-#pragma unroll
-        for (int k8 = 0; k8 < STEP / 8; ++k8) {
-          const int chunk = (c0 + 8 * k8) / 8;
-          *reinterpret_cast<uint4*>(A0 + (size_t)chunk * tc::M * 16 + (size_t)row * 16) =
-              make_uint4(pk[4 * k8], pk[4 * k8 + 1], pk[4 * k8 + 2], pk[4 * k8 + 3]);
-        }
+      for (int k = 0; k < E::STEP / 2; ++k) {
+        const int ch = c0 / 2 + k;
+        const float2 rv = r[enc * C + ch];
+        const float2 av = p.a[enc * C + ch];
+        const float tr = rv.x - x[2 * k] - (av.x * y[2 * k] - av.y * y[2 * k + 1]);
+        const float ti = rv.y - x[2 * k + 1] - (av.x * y[2 * k + 1] + av.y * y[2 * k]);
+        pk[k] = (en < N) ? tc::pack_bf16(tr, ti) : 0u;
       }
+#pragma unroll
+      for (int k8 = 0; k8 < E::STEP / 8; ++k8)
+        store_chunk(Atile(0), erow, (c0 + 8 * k8) / 8,
+                    make_uint4(pk[4 * k8], pk[4 * k8 + 1], pk[4 * k8 + 2], pk[4 * k8 + 3]));
     }
   } else {
     // first pre-smoothing step: t = r
-    gather_tile<K2, D>(A0, r, n0, p, 0);
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int idx = threadIdx.x + i * tc::THREADS;
+      store_chunk(Atile(0), idx % tc::M, idx / tc::M, load_chunk<K2>(r, n0, idx % tc::M, idx / tc::M, p, 0));
+    }
   }
 
-  // ---------------- phase 2: Z = T K~_S^T, z = s (.) Z -> BF16 into A1 ----------------
-  copy_tile<K2>(B0, p.KS);
-  tc::fence_before();
-  tc::fence_async_smem();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    tc::fence_after();
-    issue_gemm<K2>(tX, A0, B0, false);
-    tc::mma_commit(&bars[0]);
-  }
-  if (!wait_bar(0)) { ok = false; goto fail; }
-  tc::fence_after();
+  // ---------------- phase 2: Z = T K~_S^T, z = s (.) Z -> BF16 into A tile 1 ----------------
   {
-    const int q = warp & 3, half = warp >> 2;
-    const int row = 32 * q + lane;
-    const long long n = n0 + row;
-    const long long nc = n < N ? n : N - 1;
-    constexpr int HC = K2 / 2;
-    constexpr int STEP = HC < 16 ? HC : 16;
-    for (int c0 = half * HC; c0 < (half + 1) * HC; c0 += STEP) {
+    copy_tile<K2>(Btile(0), p.KS);
+    // operands of the epilogue, fetched while the MMA runs
+    float2 sv[E::NCH <= 8 ? E::NCH : 1];
+    if constexpr (E::NCH <= 8) {
+#pragma unroll
+      for (int k = 0; k < E::NCH; ++k) sv[k] = p.s[enc * C + cbase / 2 + k];
+    }
+    tc::fence_before();
+    tc::fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc::fence_after();
+      issue_gemm<K2>(tX, Atile(0), Btile(0), false);
+      tc::mma_commit(&bars[0]);
+    }
+    if (!wait_bar(0)) { ok = false; goto fail; }
+    tc::fence_after();
+    for (int c0 = cbase; c0 < cbase + E::HC; c0 += E::STEP) {
       float zv[16];
-      const uint32_t lanebits = (uint32_t)(32 * q) << 16;
-      if (STEP == 16) tc::tmem_ld16(tX + lanebits + c0, zv);
-      else tc::tmem_ld8(tX + lanebits + c0, zv);
+      tmem_cols<K2>(tX + lanebits + c0, zv);
       uint32_t pk[8];
 #pragma unroll
-      for (int k = 0; k < STEP / 2; ++k) {
-        const float2 sv = p.s[nc * C + c0 / 2 + k];
-        const float zr = sv.x * zv[2 * k] - sv.y * zv[2 * k + 1];
-        const float zi = sv.x * zv[2 * k + 1] + sv.y * zv[2 * k];
-        pk[k] = (n < N) ? tc::pack_bf16(zr, zi) : 0u;
+      for (int k = 0; k < E::STEP / 2; ++k) {
+        float2 s2;
+        if constexpr (E::NCH <= 8) s2 = sv[k];
+        else s2 = p.s[enc * C + c0 / 2 + k];
+        const float zr = s2.x * zv[2 * k] - s2.y * zv[2 * k + 1];
+        const float zi = s2.x * zv[2 * k + 1] + s2.y * zv[2 * k];
+        pk[k] = (en < N) ? tc::pack_bf16(zr, zi) : 0u;
       }
 #pragma unroll
-      for (int k8 = 0; k8 < STEP / 8; ++k8) {
-        const int chunk = (c0 + 8 * k8) / 8;
-        *reinterpret_cast<uint4*>(A1 + (size_t)chunk * tc::M * 16 + (size_t)row * 16) =
-            make_uint4(pk[4 * k8], pk[4 * k8 + 1], pk[4 * k8 + 2], pk[4 * k8 + 3]);
-      }
+      for (int k8 = 0; k8 < E::STEP / 8; ++k8)
+        store_chunk(Atile(1), erow, (c0 + 8 * k8) / 8,
+                    make_uint4(pk[4 * k8], pk[4 * k8 + 1], pk[4 * k8 + 2], pk[4 * k8 + 3]));
     }
   }
 
   // ---------------- phase 3: U = Z W~_i^T, e' = e + U ----------------
-  copy_tile<K2>(B1, p.Wi);
-  tc::fence_before();
-  tc::fence_async_smem();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    tc::fence_after();
-    issue_gemm<K2>(tY, A1, B1, false);
-    tc::mma_commit(&bars[1]);
-  }
-  if (!wait_bar(1)) { ok = false; goto fail; }
-  tc::fence_after();
   {
-    const int q = warp & 3, half = warp >> 2;
-    const int row = 32 * q + lane;
-    const long long n = n0 + row;
-    constexpr int HC = K2 / 2;
-    constexpr int STEP = HC < 16 ? HC : 16;
-    for (int c0 = half * HC; c0 < (half + 1) * HC; c0 += STEP) {
-      float u[16];
-      const uint32_t lanebits = (uint32_t)(32 * q) << 16;
-      if (STEP == 16) tc::tmem_ld16(tY + lanebits + c0, u);
-      else tc::tmem_ld8(tY + lanebits + c0, u);
-      if (n < N) {
+    copy_tile<K2>(Btile(1), p.Wi);
+    float2 ev[E::NCH <= 8 ? E::NCH : 1];
+    if constexpr (E::NCH <= 8) {
 #pragma unroll
-        for (int k = 0; k < STEP / 2; ++k) {
+      for (int k = 0; k < E::NCH; ++k)
+        ev[k] = ein ? ein[enc * C + cbase / 2 + k] : make_float2(0.f, 0.f);
+    }
+    tc::fence_before();
+    tc::fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc::fence_after();
+      issue_gemm<K2>(tY, Atile(1), Btile(1), false);
+      tc::mma_commit(&bars[1]);
+    }
+    if (!wait_bar(1)) { ok = false; goto fail; }
+    tc::fence_after();
+    for (int c0 = cbase; c0 < cbase + E::HC; c0 += E::STEP) {
+      float u[16];
+      tmem_cols<K2>(tY + lanebits + c0, u);
+      if (en < N) {
+#pragma unroll
+        for (int k = 0; k < E::STEP / 2; ++k) {
           const int ch = c0 / 2 + k;
           float2 v = make_float2(u[2 * k], u[2 * k + 1]);
-          if (ein) v = cadd(v, ein[n * C + ch]);
-          eout[n * C + ch] = v;
+          if constexpr (E::NCH <= 8) v = cadd(v, ev[k]);
+          else if (ein) v = cadd(v, ein[en * C + ch]);
+          eout[en * C + ch] = v;
         }
       }
     }
@@ -442,13 +480,8 @@ fail:
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
                  "r"(TM_COLS));
   }
-  (void)commits;
-  (void)last_bar;
 }
 
-// Dynamic shared memory: two A tiles, three B tiles, alignment slack.  It is
-// at least A + 36 KB, so that an A descriptor read with its two strides
-// exchanged (16 row groups 2 KB apart) would still stay inside the allocation.
 template <int K2, int D>
 static size_t tc_smem_bytes() {
   const size_t need = 2 * (size_t)tc::M * K2 * 2 + 3 * (size_t)K2 * K2 * 2 + 1024;
