@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "solves/s and V-cycles/s to rel. residual 1e-6; p50/p99 solve latency"
 # Iteration cap per workload (the restart length is the workload's FGMRES(m)).
 MAX_ITERS = {"helm2d_n64_homogeneous": 2000, "helm2d_n64_slmg": 2000, "helm2d_n256_grf": 4000,
-             "helm2d_n1024_layers": 8000, "helm3d_n256_grf": 8000}
+             "helm2d_n1024_layers": 20000, "helm3d_n256_grf": 8000}
 FP32_LANES_PER_SM = 128
 NUM_SMS = 148
 
@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--n", type=int, default=0,
                    help="override the grid size (smaller copies of a workload for profiling)")
     p.add_argument("--max-iters", type=int, default=0)
+    p.add_argument("--requests", type=int, default=24,
+                   help="serving_stream: how many requests of the 256-request stream to serve")
+    p.add_argument("--budget-gb", type=float, default=150.0)
     return p.parse_args()
 
 
@@ -238,10 +241,117 @@ def run_reference(args):
     }))
 
 
+def run_serving(args):
+    """Serving stream: requests with their own media and 1-8 point sources.
+
+    Plain form: every right-hand side solved one after another with mcmg_solve
+    on FP32 handles.  Served form: BF16 handles set up at each request's
+    arrival and submitted to the context's server (admission against the HBM
+    budget, every solve on its own stream, stages of all admitted solves
+    overlapping).  Arrivals are Poisson at 1.5x the plain form's request rate.
+    Reports solves/s (right-hand sides per second of makespan), p50/p99 request
+    latency (completion - arrival, setup included) and the speedup."""
+    import numpy as np
+    import torch
+
+    from paper_2606_30495_b300 import build as B
+    B.build()
+    from paper_2606_30495_b300 import inputs as I
+    from paper_2606_30495_b300 import mcmg
+    torch.cuda.set_device(0)
+    base = I.serving_weights()
+    reqs = I.serving_requests(count=256)[: args.requests]
+    data = [I.serving_request_inputs(r, base) for r in reqs]
+    nrhs_total = sum(r["nrhs"] for r in reqs)
+    max_it = args.max_iters or 20000
+    ctx = mcmg.Context(0, hbm_budget_bytes=int(args.budget_gb * 2 ** 30))
+
+    # ---- plain per-request FP32 form (sequential)
+    plain_lat, plain_iters = [], []
+    t0 = time.perf_counter()
+    for r, (c, om, w, f) in zip(reqs, data):
+        ts = time.perf_counter()
+        h = mcmg.Handle(ctx, c, om, 16, 1.0, w, precision=mcmg.FP32)
+        fd = torch.from_numpy(f).cuda()
+        u = torch.zeros_like(fd)
+        st, info = h.solve(fd, u, tol=1e-6, restart_m=30, max_iters=max_it, nrhs=r["nrhs"])
+        torch.cuda.synchronize()
+        plain_lat.append(time.perf_counter() - ts)
+        plain_iters.append(info["iters"])
+        h.close()
+    plain_total = time.perf_counter() - t0
+    plain_rate = nrhs_total / plain_total
+    req_rate = 1.5 * len(reqs) / plain_total
+
+    # ---- served form: Poisson arrivals at req_rate
+    rng = np.random.Generator(np.random.PCG64(11))
+    gaps = rng.exponential(1.0 / req_rate, size=len(reqs))
+    arrive = np.cumsum(gaps) - gaps[0]
+    handles, bufs, tickets, t_arr = [], [], [], []
+    launches0 = mcmg.kernel_launches()
+    t0 = time.perf_counter()
+    for k, (r, (c, om, w, f)) in enumerate(zip(reqs, data)):
+        while time.perf_counter() - t0 < arrive[k]:
+            time.sleep(0.0005)
+        t_arr.append(time.perf_counter() - t0)
+        h = mcmg.Handle(ctx, c, om, 16, 1.0, w, precision=mcmg.BF16)
+        fd = torch.from_numpy(f).cuda()
+        u = torch.zeros_like(fd)
+        torch.cuda.synchronize()
+        tickets.append(ctx.submit(h, fd, u, tol=1e-6, restart_m=30, max_iters=max_it,
+                                  nrhs=r["nrhs"]))
+        handles.append(h)
+        bufs.append((fd, u))
+    done = {}
+    while len(done) < len(tickets):
+        for k, t in enumerate(tickets):
+            if k in done:
+                continue
+            st, info = ctx.poll(t)
+            if st != mcmg.MCMG_PENDING:
+                done[k] = (time.perf_counter() - t0, st, info)
+        time.sleep(0.0005)
+    makespan = max(v[0] for v in done.values())
+    launches = mcmg.kernel_launches() - launches0
+    lat = sorted(done[k][0] - t_arr[k] for k in range(len(reqs)))
+    conv = all(done[k][1] == 0 for k in range(len(reqs)))
+    served_rate = nrhs_total / makespan
+    # true residuals against the FP64 operator (oracle), every right-hand side
+    from oracle import mcmg_oracle as O
+    worst = 0.0
+    for k, (r, (c, om, w, f)) in enumerate(zip(reqs, data)):
+        q = O.wavenumber_coef(c, om, 16, 1.0)
+        un = bufs[k][1].cpu().numpy()
+        for j in range(r["nrhs"]):
+            worst = max(worst, float(np.linalg.norm(f[j] - O.apply_A(q, un[j])) / np.linalg.norm(f[j])))
+    for h in handles:
+        h.close()
+    ctx.close()
+    pct = lambda a, p: a[min(len(a) - 1, int(math.ceil(p * len(a))) - 1)]
+    out = {
+        "metric": METRIC, "value": served_rate, "unit": "solves/s", "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": 1e3 * makespan, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16/f32", "data": "synthetic",
+        "config": {"workload": "serving_stream", "requests": len(reqs), "rhs_total": nrhs_total,
+                   "grids": sorted({r["n"] for r in reqs}), "arrival_rate_hz": req_rate,
+                   "fgmres_restart": 30, "tol": 1e-6},
+        "latency_ms": {"p50": 1e3 * pct(lat, 0.5), "p99": 1e3 * pct(lat, 0.99)},
+        "plain_fp32": {"solves_per_s": plain_rate, "seconds": plain_total,
+                       "latency_ms_p50": 1e3 * sorted(plain_lat)[len(plain_lat) // 2],
+                       "iters": plain_iters},
+        "speedup_vs_plain": served_rate / plain_rate,
+        "served_iters": [done[k][2]["iters"] for k in range(len(reqs))],
+        "converged": conv, "worst_true_rel_residual": worst, "gpu_launches": int(launches),
+    }
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving_stream":
+        return run_serving(args)
     import numpy as np
     import torch
     import torch.distributed as dist

@@ -26,6 +26,7 @@ struct Request {
   std::chrono::steady_clock::time_point t_submit;
   mcmg_status status = MCMG_PENDING;
   mcmg_solve_info info{};
+  std::string err;                   // message of a failure on the server thread
 };
 
 struct mcmg_ctx_s {
@@ -696,27 +697,33 @@ mcmg_status mcmg_cgs2(mcmg_handle h, const void* V, int k, size_t n, void* w, do
 // ------------------------------------------------------------------ server --
 // One worker thread.  Admission: queued requests start in arrival order when
 // their Krylov and V-cycle workspaces fit the context's HBM budget.  Every
-// admitted request runs on its own stream; the worker polls each request's
-// last event and enqueues its next FGMRES stage as soon as it completes, so
-// the stages of different requests overlap on the device.
+// right-hand side of every admitted request runs on its own stream; the worker
+// polls each solve's last event and enqueues its next FGMRES stage as soon as
+// it completes, so the stages of different solves overlap on the device.
 
 static size_t request_bytes(mcmg_handle_s* h, const mcmg_solve_opts& o) {
   const size_t n = (size_t)h->g0.nodes();
   const int m = o.restart_m;
   size_t b = sizeof(float2) * n * (2 * (size_t)m + 2) + sizeof(double2) * n;
   for (int l = 0; l < h->L; ++l) b += 4 * sizeof(float2) * (size_t)h->lv[l].g.nodes() * h->lv[l].C;
-  b += sizeof(double2) * (size_t)m * (m + 1) + (size_t)1 << 20;
+  b += sizeof(double2) * (size_t)m * (m + 1) + ((size_t)1 << 20);
   return b * o.nrhs;
 }
 
 static void release(Request* r) {
   for (auto* k : r->kry) krylov_destroy(r->h, k);
   r->kry.clear();
+  r->done.clear();
   if (r->st) { cudaStreamDestroy(r->st); r->st = nullptr; }
 }
 
 static bool try_admit(mcmg_ctx_s* c, Request* r) {
-  if (c->budget && c->used.load() + r->bytes_needed > c->budget) return false;
+  if (c->budget && c->used.load() + r->bytes_needed > c->budget) {
+    set_error("request needs about %zu bytes; %zu of the %zu-byte budget are in use",
+              r->bytes_needed, c->used.load(), c->budget);
+    r->err = mcmg_last_error();
+    return false;
+  }
   if (cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -726,13 +733,14 @@ static bool try_admit(mcmg_ctx_s* c, Request* r) {
     Krylov* kr = nullptr;
     mcmg_status s = krylov_create(r->h, r->o.restart_m, &kr);
     if (s != MCMG_OK) {
+      r->err = mcmg_last_error();
       release(r);
       cudaGetLastError();
       return false;
     }
     r->kry.push_back(kr);
     r->done.push_back(0);
-    s = krylov_begin(kr, r->f + k * N, r->u + k * N, r->o, r->st);
+    s = krylov_begin(kr, r->f + k * N, r->u + k * N, r->o, krylov_stream(kr));
     if (s != MCMG_OK) {
       r->status = s;
       return true;
@@ -776,7 +784,7 @@ static void server_loop(mcmg_ctx_s* c) {
           if (r->done[k]) continue;
           int d = 0;
           mcmg_status s = krylov_advance(r->kry[k], false, &d);
-          if (s != MCMG_OK) { r->status = s; d = 1; }
+          if (s != MCMG_OK) { r->status = s; r->err = mcmg_last_error(); d = 1; }
           if (d) { r->done[k] = 1; progressed = true; }
           else all = false;
         }
@@ -889,6 +897,7 @@ mcmg_status mcmg_poll(mcmg_ctx c, uint64_t ticket, mcmg_solve_info* info) {
   Request* r = it->second;
   if (info) *info = r->info;
   mcmg_status s = r->status;
+  if (s < 0) set_error("%s", r->err.empty() ? "request failed" : r->err.c_str());
   c->finished.erase(it);
   delete r;
   return s;

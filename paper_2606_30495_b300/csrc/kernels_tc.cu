@@ -33,7 +33,7 @@ namespace tc {
 
 constexpr int M = 128;           // nodes per CTA (MMA M)
 constexpr int THREADS = 256;     // 8 warps
-constexpr unsigned SPIN_LIMIT = 1u << 22;   // ~4M polls with a short sleep: well under a second
+constexpr unsigned SPIN_LIMIT = 1u << 20;   // ~1M polls with a short sleep: about a second at most
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -75,10 +75,12 @@ __device__ __forceinline__ void bar_init(uint64_t* bar, uint32_t count) {
 }
 
 // Bounded wait for the phase with parity `parity` (non-blocking polls with a
-// short sleep); returns false when the bound runs out.
-__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+// short sleep); returns false when the bound runs out, or at once when another
+// CTA has already recorded a failure in the error word.
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, const int* err) {
   const uint32_t a = smem_u32(bar);
   for (unsigned it = 0; it < SPIN_LIMIT; ++it) {
+    if ((it & 1023) == 1023 && err && *(const volatile int*)err) return false;
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -151,56 +153,6 @@ struct TcParams {
   int* err;               // error word (mapped host memory), may be null
 };
 
-// Gather an A tile: row i = node n0 + i, value = src field at the neighbour
-// along `tap` (0 = the node itself), as BF16 in the core-matrix layout.
-// Rows outside the grid or whose neighbour is outside are zero.
-template <int K2, int D>
-__device__ __forceinline__ void gather_tile(uint8_t* dst, const float2* __restrict__ src,
-                                            long long n0, const TcParams& p, int tap) {
-  constexpr int CH = K2 / 8;                 // 16-byte chunks per row
-  const long long sxy = (long long)p.nx * p.ny;
-  for (int idx = threadIdx.x; idx < tc::M * CH; idx += tc::THREADS) {
-    const int row = idx % tc::M;
-    const int ch = idx / tc::M;
-    const long long n = n0 + row;
-    uint4 out = make_uint4(0, 0, 0, 0);
-    if (n < p.nodes) {
-      long long nb = n;
-      bool ok = true;
-      if (tap > 0) {
-        const int axis = (tap - 1) >> 1;
-        const int sgn = (tap & 1) ? -1 : 1;
-        int x = (int)(n % p.nx);
-        long long rest = n / p.nx;
-        int y = (int)(rest % p.ny);
-        int z = (int)(rest / p.ny);
-        int c = axis == 0 ? x : (axis == 1 ? y : z);
-        int ext = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
-        long long stride = axis == 0 ? 1 : (axis == 1 ? p.nx : sxy);
-        ok = (c + sgn >= 0) && (c + sgn < ext);
-        nb = n + sgn * stride;
-      }
-      if (ok) {
-        const float4* q = reinterpret_cast<const float4*>(src + nb * (K2 / 2) + ch * 4);
-        const float4 u = __ldg(q), v = __ldg(q + 1);
-        out.x = tc::pack_bf16(u.x, u.y);
-        out.y = tc::pack_bf16(u.z, u.w);
-        out.z = tc::pack_bf16(v.x, v.y);
-        out.w = tc::pack_bf16(v.z, v.w);
-      }
-    }
-    *reinterpret_cast<uint4*>(dst + (size_t)ch * tc::M * 16 + (size_t)row * 16) = out;
-  }
-}
-
-// Copy a weight tile (already in the core-matrix layout) to shared memory.
-template <int K2>
-__device__ __forceinline__ void copy_tile(uint8_t* dst, const uint4* __restrict__ src) {
-  constexpr int N16 = K2 * K2 * 2 / 16;
-  uint4* d = reinterpret_cast<uint4*>(dst);
-  for (int i = threadIdx.x; i < N16; i += tc::THREADS) d[i] = __ldg(src + i);
-}
-
 // MMAs of one GEMM: D[128 x K2] (+)= A[128 x K2] B[K2 x K2]^T, K in steps of 16.
 template <int K2>
 __device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const uint8_t* A, const uint8_t* B,
@@ -251,6 +203,52 @@ __device__ __forceinline__ void store_chunk(uint8_t* tile, int row, int ch, uint
   *reinterpret_cast<uint4*>(tile + (size_t)ch * tc::M * 16 + (size_t)row * 16) = v;
 }
 
+// Tiles staged through registers: every global load of a tile is issued
+// before any of its shared-memory stores, so the loads of a thread overlap.
+template <int K2>
+struct Stage {
+  static constexpr int PER = tc::M * (K2 / 8) / tc::THREADS;              // A chunks / thread
+  static constexpr int N16 = K2 * K2 * 2 / 16;                            // B uint4 per tile
+  static constexpr int BPER = (N16 + tc::THREADS - 1) / tc::THREADS;      // B uint4 / thread
+};
+
+template <int K2>
+__device__ __forceinline__ void load_a(uint4 (&v)[Stage<K2>::PER], const float2* __restrict__ src,
+                                       long long n0, const TcParams& p, int tap) {
+#pragma unroll
+  for (int i = 0; i < Stage<K2>::PER; ++i) {
+    const int idx = threadIdx.x + i * tc::THREADS;
+    v[i] = load_chunk<K2>(src, n0, idx % tc::M, idx / tc::M, p, tap);
+  }
+}
+
+template <int K2>
+__device__ __forceinline__ void store_a(uint8_t* tile, const uint4 (&v)[Stage<K2>::PER]) {
+#pragma unroll
+  for (int i = 0; i < Stage<K2>::PER; ++i) {
+    const int idx = threadIdx.x + i * tc::THREADS;
+    store_chunk(tile, idx % tc::M, idx / tc::M, v[i]);
+  }
+}
+
+template <int K2>
+__device__ __forceinline__ void load_b(uint4 (&v)[Stage<K2>::BPER], const uint4* __restrict__ src) {
+#pragma unroll
+  for (int i = 0; i < Stage<K2>::BPER; ++i) {
+    const int idx = threadIdx.x + i * tc::THREADS;
+    v[i] = idx < Stage<K2>::N16 ? __ldg(src + idx) : make_uint4(0, 0, 0, 0);
+  }
+}
+
+template <int K2>
+__device__ __forceinline__ void store_b(uint8_t* tile, const uint4 (&v)[Stage<K2>::BPER]) {
+#pragma unroll
+  for (int i = 0; i < Stage<K2>::BPER; ++i) {
+    const int idx = threadIdx.x + i * tc::THREADS;
+    if (idx < Stage<K2>::N16) reinterpret_cast<uint4*>(tile)[idx] = v[i];
+  }
+}
+
 // Epilogue thread mapping: warp w reads TMEM lanes 32 (w % 4) .. + 31 (one node
 // per lane) and the column half w / 4.
 template <int K2>
@@ -267,7 +265,7 @@ __device__ __forceinline__ void tmem_cols(uint32_t taddr, float* v) {
 }
 
 template <int K2, int D>
-__global__ void __launch_bounds__(tc::THREADS) k_smooth_tc(TcParams p) {
+__global__ void __launch_bounds__(tc::THREADS, (K2 >= 64 ? 1 : 4)) k_smooth_tc(TcParams p) {
   constexpr int C = K2 / 2;
   constexpr int NT = 2 * D + 1;
   constexpr int NA = 2;                      // A tiles (double buffer)
@@ -320,7 +318,7 @@ __global__ void __launch_bounds__(tc::THREADS) k_smooth_tc(TcParams p) {
   uint32_t phase[2] = {0, 0};
   bool ok = true;
   auto wait_bar = [&](int b) -> bool {
-    const bool w = tc::bar_wait(&bars[b], phase[b]);
+    const bool w = tc::bar_wait(&bars[b], phase[b], p.err);
     phase[b] ^= 1;
     return w;
   };
@@ -328,9 +326,13 @@ __global__ void __launch_bounds__(tc::THREADS) k_smooth_tc(TcParams p) {
   // ---------------- phase 1: X = sum_tap E_tap W~_tap^T, Y = E_0 K~_A^T ----------------
   if (ein) {
     {
-      gather_tile<K2, D>(Atile(0), ein, n0, p, 0);
-      copy_tile<K2>(Btile(0), p.Wtap);
-      copy_tile<K2>(Btile(2), p.KA);
+      uint4 av[Stage<K2>::PER], bv[Stage<K2>::BPER], kv[Stage<K2>::BPER];
+      load_a<K2>(av, ein, n0, p, 0);
+      load_b<K2>(bv, p.Wtap);
+      load_b<K2>(kv, p.KA);
+      store_a<K2>(Atile(0), av);
+      store_b<K2>(Btile(0), bv);
+      store_b<K2>(Btile(2), kv);
       tc::fence_async_smem();
       __syncthreads();
       for (int j = 0; j < NT && ok; ++j) {
@@ -343,9 +345,12 @@ __global__ void __launch_bounds__(tc::THREADS) k_smooth_tc(TcParams p) {
         }
         if (j + 1 < NT) {
           const int nb = (j + 1) & 1;
+          // fetch tap j+1 while the MMAs of tap j run
+          load_a<K2>(av, ein, n0, p, j + 1);
+          load_b<K2>(bv, p.Wtap + (size_t)(j + 1) * (B_BYTES / 16));
           if (j >= 1 && !wait_bar(nb)) { ok = false; break; }   // buffers of tap j-1 free
-          gather_tile<K2, D>(Atile(nb), ein, n0, p, j + 1);
-          copy_tile<K2>(Btile(nb), p.Wtap + (size_t)(j + 1) * (B_BYTES / 16));
+          store_a<K2>(Atile(nb), av);
+          store_b<K2>(Btile(nb), bv);
           tc::fence_async_smem();
           __syncthreads();
         }
@@ -387,7 +392,11 @@ __global__ void __launch_bounds__(tc::THREADS) k_smooth_tc(TcParams p) {
 
   // ---------------- phase 2: Z = T K~_S^T, z = s (.) Z -> BF16 into A tile 1 ----------------
   {
-    copy_tile<K2>(Btile(0), p.KS);
+    {
+      uint4 bv[Stage<K2>::BPER];
+      load_b<K2>(bv, p.KS);
+      store_b<K2>(Btile(0), bv);
+    }
     // operands of the epilogue, fetched while the MMA runs
     float2 sv[E::NCH <= 8 ? E::NCH : 1];
     if constexpr (E::NCH <= 8) {
@@ -426,7 +435,11 @@ __global__ void __launch_bounds__(tc::THREADS) k_smooth_tc(TcParams p) {
 
   // ---------------- phase 3: U = Z W~_i^T, e' = e + U ----------------
   {
-    copy_tile<K2>(Btile(1), p.Wi);
+    {
+      uint4 bv[Stage<K2>::BPER];
+      load_b<K2>(bv, p.Wi);
+      store_b<K2>(Btile(1), bv);
+    }
     float2 ev[E::NCH <= 8 ? E::NCH : 1];
     if constexpr (E::NCH <= 8) {
 #pragma unroll
@@ -471,8 +484,8 @@ fail:
   // a bounded wait ran out: record it, give the MMAs a last bounded chance to
   // finish, release tensor memory and leave.
   if (p.err) atomicOr(p.err, 1);
-  tc::bar_wait(&bars[0], phase[0]);
-  tc::bar_wait(&bars[1], phase[1]);
+  tc::bar_wait(&bars[0], phase[0], nullptr);
+  tc::bar_wait(&bars[1], phase[1], nullptr);
   tc::fence_before();
   __syncthreads();
   if (warp == 0) {

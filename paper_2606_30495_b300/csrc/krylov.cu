@@ -312,7 +312,8 @@ struct Krylov {
   Stat* stat_h = nullptr;   // mapped pinned
   Stat* stat_d = nullptr;
   cudaEvent_t ev = nullptr;
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;        // stream of the current solve
+  cudaStream_t own = nullptr;       // the solve's private stream (server use)
   DevArena arena;
   // solve state
   const double2* f = nullptr;
@@ -368,6 +369,7 @@ mcmg_status krylov_create(mcmg_handle_s* h, int m, Krylov** out) {
   cudaError_t e = cudaHostAlloc((void**)&k->stat_h, sizeof(Stat), cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&k->stat_d, k->stat_h, 0);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&k->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&k->own, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     krylov_destroy(h, k);
     return cuda_fail(e, "krylov_create");
@@ -382,6 +384,7 @@ void krylov_destroy(mcmg_handle_s* h, Krylov* k) {
   arena_free(h, k->arena);
   if (k->stat_h) cudaFreeHost(k->stat_h);
   if (k->ev) cudaEventDestroy(k->ev);
+  if (k->own) cudaStreamDestroy(k->own);
   delete k;
 }
 
@@ -532,6 +535,7 @@ mcmg_status krylov_advance(Krylov* k, bool blocking, int* done) {
 }
 
 int krylov_m(const Krylov* k) { return k->m; }
+cudaStream_t krylov_stream(const Krylov* k) { return k->own; }
 
 void krylov_info(const Krylov* k, mcmg_solve_info* info, mcmg_status* final_status) {
   if (info) {

@@ -183,6 +183,7 @@ mcmg_status krylov_begin(Krylov* k, const double2* f, double2* u, const mcmg_sol
 mcmg_status krylov_advance(Krylov* k, bool blocking, int* done);
 void krylov_info(const Krylov* k, mcmg_solve_info* info, mcmg_status* final_status);
 int krylov_m(const Krylov* k);
+cudaStream_t krylov_stream(const Krylov* k);   // the solve's private stream
 // CGS2 on caller buffers (used by mcmg_cgs2).
 mcmg_status cgs2_once(mcmg_handle_s* h, const float2* V, int k, long long n, float2* w,
                       double* h_host, double* norm_host, cudaStream_t st);

@@ -330,6 +330,38 @@ def serving_levels(n: int) -> int:
     return min(6, int(round(math.log2(n / 16))) + 1)
 
 
+def prefix_weights(w: dict, L: int) -> dict:
+    """The first L levels of a model: level L-1 becomes the coarsest (its
+    transfers are dropped and it keeps only its pre-smoothing steps)."""
+    lv = [dict(x) for x in w["lvl"][:L]]
+    last = lv[-1]
+    for k in ("R", "P", "fa_w", "fa_b"):
+        last.pop(k, None)
+    last["Wsm"] = last["Wsm"][: w["nu_pre"][L - 1]]
+    out = dict(w)
+    out.update(levels=L, channels=list(w["channels"][:L]), nu_pre=list(w["nu_pre"][:L]),
+               nu_post=list(w["nu_post"][: L - 1]) + [0], lvl=lv)
+    return out
+
+
+def serving_request_inputs(req: dict, base_weights: dict):
+    """Medium, omega, weights and right-hand sides of one serving request:
+    a Gaussian random field (correlation 16 cells, c in [1, 3]), 8 points per
+    wavelength at c = 1, a 16-cell sponge and `nrhs` point sources."""
+    n = req["n"]
+    rng = np.random.Generator(np.random.PCG64(req["medium_seed"]))
+    c = grf((n, n), 16.0, 1.0, 3.0, rng)
+    omega = omega_for_ppw(1.0, 8.0, n)
+    f = random_point_sources((n, n), 16, req["nrhs"], rng)
+    return c, omega, prefix_weights(base_weights, req["levels"]), f
+
+
+def serving_weights(seed: int = 3) -> dict:
+    """The shared 6-level model (8/16/32/64/64/64 channels) requests take prefixes of."""
+    pre, post = nu_schedule(6)
+    return make_weights(2, SERVING_CHANNELS, pre, post, mode="structured", seed=seed)
+
+
 def serving_requests(count=256, sizes=(128, 256, 512, 1024), rate_hz=100.0, seed=3):
     """Seeded request stream: grid size, medium seed, source count and arrival time.
 

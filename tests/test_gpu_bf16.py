@@ -110,3 +110,22 @@ def test_tc_workload_vcycle_256(ctx):
         assert h.device_error() == 0
     finally:
         h.close()
+
+
+def test_tc_residual_restrict(case):
+    """Residual r - A_l(e) and restriction on a BF16 handle (the residual runs
+    on the CUDA cores in FP32)."""
+    m, h = case
+    w = m["w"]
+    for l in range(w["levels"] - 1):
+        C, Cn = w["channels"][l], w["channels"][l + 1]
+        shp = tuple(n >> l for n in m["shape"])
+        cshp = tuple(n >> (l + 1) for n in m["shape"])
+        a, _ = m["feats"][l]
+        lv = w["lvl"][l]
+        r = I.complex_normal((2,) + shp + (C,), rng(30))
+        e = I.complex_normal((2,) + shp + (C,), rng(31))
+        rc = torch.zeros((2,) + cshp + (Cn,), dtype=torch.complex64, device="cuda")
+        h.residual_restrict(l, dev(r), dev(e), rc, nrhs=2)
+        want = np.stack([O.restrict(lv["R"], r[k] - O.op_A(lv, a, e[k])) for k in range(2)])
+        assert relerr(host(rc), want) < TOL_STEP

@@ -1,0 +1,114 @@
+"""The request server (mcmg_submit / mcmg_poll): each result is the same alone
+and in the mix, admission respects the HBM budget, and a request that can
+never fit is refused."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import mcmg_oracle as O
+from paper_2606_30495_b300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _requests():
+    base = I.serving_weights()
+    out = []
+    for i, (n, nrhs) in enumerate([(64, 2), (128, 1), (64, 3), (128, 2)]):
+        req = dict(id=i, n=n, nrhs=nrhs, medium_seed=500 + i, levels=I.serving_levels(max(n, 64)) - 0)
+        req["levels"] = 3 if n == 64 else 4
+        out.append((req,) + I.serving_request_inputs(req, base))
+    return out
+
+
+def _handles(ctx, reqs, precision):
+    from paper_2606_30495_b300 import mcmg
+    return [mcmg.Handle(ctx, c, om, 16, 1.0, w, precision=precision) for (_, c, om, w, _) in reqs]
+
+
+def test_server_results_equal_alone_and_in_the_mix():
+    from paper_2606_30495_b300 import mcmg
+    ctx = mcmg.Context(0)
+    reqs = _requests()
+    hs = _handles(ctx, reqs, mcmg.BF16)
+    try:
+        alone = []
+        for h, (req, c, om, w, f) in zip(hs, reqs):
+            fd = torch.from_numpy(f).cuda()
+            u = torch.zeros_like(fd)
+            st, info = h.solve(fd, u, tol=1e-6, restart_m=30, max_iters=3000, nrhs=req["nrhs"])
+            assert st == 0 and info["converged"], info
+            alone.append(u.cpu().numpy())
+        # in the mix: all submitted at once, overlapping on the device
+        fs = [torch.from_numpy(f).cuda() for (_, _, _, _, f) in reqs]
+        us = [torch.zeros_like(x) for x in fs]
+        tickets = [ctx.submit(h, fd, u, tol=1e-6, restart_m=30, max_iters=3000, nrhs=r[0]["nrhs"])
+                   for h, fd, u, r in zip(hs, fs, us, reqs)]
+        done = {}
+        t0 = time.time()
+        while len(done) < len(tickets) and time.time() - t0 < 120:
+            for t in tickets:
+                if t not in done:
+                    st, info = ctx.poll(t)
+                    if st != mcmg.MCMG_PENDING:
+                        done[t] = (st, info)
+            time.sleep(0.002)
+        assert len(done) == len(tickets)
+        for k, t in enumerate(tickets):
+            st, info = done[t]
+            assert st == 0 and info["converged"]
+            mix = us[k].cpu().numpy()
+            assert np.max(np.abs(mix - alone[k])) <= 1e-12 * np.max(np.abs(alone[k]))
+            req, c, om, w, f = reqs[k]
+            q = O.wavenumber_coef(c, om, 16, 1.0)
+            for j in range(req["nrhs"]):
+                res = np.linalg.norm(f[j] - O.apply_A(q, mix[j])) / np.linalg.norm(f[j])
+                assert res <= 1e-6
+    finally:
+        for h in hs:
+            h.close()
+        ctx.close()
+
+
+def test_admission_under_a_small_budget_and_refusal():
+    from paper_2606_30495_b300 import mcmg
+    reqs = _requests()[:3]
+    probe = mcmg.Context(0)
+    hs = _handles(probe, reqs, mcmg.BF16)
+    held = probe.memory()
+    for h in hs:
+        h.close()
+    probe.close()
+    # room for the handles plus about one request's workspaces at a time
+    slack = 48 * 2 ** 20
+    ctx = mcmg.Context(0, hbm_budget_bytes=held + slack)
+    hs = _handles(ctx, reqs, mcmg.BF16)
+    try:
+        fs = [torch.from_numpy(f).cuda() for (_, _, _, _, f) in reqs]
+        us = [torch.zeros_like(x) for x in fs]
+        tickets = [ctx.submit(h, fd, u, tol=1e-6, restart_m=30, max_iters=3000, nrhs=r[0]["nrhs"])
+                   for h, fd, u, r in zip(hs, fs, us, reqs)]
+        ctx.drain()
+        for t in tickets:
+            try:
+                st, info = ctx.poll(t)
+            except mcmg.McmgError as e:
+                raise AssertionError(f"ticket {t}: {e} (handles hold {held} bytes)")
+            assert st == 0 and info["converged"]
+        assert ctx.memory() <= held + slack
+        # a request far larger than the budget is refused once nothing else runs
+        big = torch.zeros((8, 64, 64), dtype=torch.complex128, device="cuda")
+        big[:, 32, 32] = 1.0
+        t = ctx.submit(hs[0], big, torch.zeros_like(big), tol=1e-6, restart_m=2000, nrhs=8)
+        ctx.drain()
+        with pytest.raises(mcmg.McmgError) as ei:
+            ctx.poll(t)
+        assert ei.value.status == -3
+        with pytest.raises(mcmg.McmgError):
+            ctx.poll(987654)
+    finally:
+        for h in hs:
+            h.close()
+        ctx.close()
