@@ -130,7 +130,9 @@ typedef struct {
 } mcmg_solve_opts;
 
 #define MCMG_SOLVE_STATIONARY 1  /* u <- u + MG(f - A u) instead of FGMRES
-                                    (Eq. mcmg_iteration)                      */
+                                    (Eq. mcmg_iteration); restart_m is
+                                    ignored; mcmg_solve only (the server
+                                    refuses it with MCMG_ERR_ARG)             */
 
 typedef struct {
   int iters;                 /* V-cycle applications (max over the rhs)      */

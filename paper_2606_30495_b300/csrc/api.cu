@@ -546,17 +546,14 @@ mcmg_status mcmg_solve(mcmg_handle h, const void* f, void* u, const mcmg_solve_o
                        mcmg_solve_info* info) {
   if (!h || !f || !u) { set_error("NULL argument"); return MCMG_ERR_ARG; }
   MCMG_TRY(check_opts(o));
-  if (o->flags & MCMG_SOLVE_STATIONARY) {
-    set_error("the stationary iteration is not available in this build");
-    return MCMG_ERR_ARG;
-  }
   std::lock_guard<std::mutex> lk(h->mu);
   MCMG_CUDA(cudaSetDevice(h->device));
-  if (h->kry && krylov_m(h->kry) != o->restart_m) {
+  const int m_need = (o->flags & MCMG_SOLVE_STATIONARY) ? 1 : o->restart_m;
+  if (h->kry && krylov_m(h->kry) != m_need) {
     krylov_destroy(h, h->kry);
     h->kry = nullptr;
   }
-  if (!h->kry) MCMG_TRY(krylov_create(h, o->restart_m, &h->kry));
+  if (!h->kry) MCMG_TRY(krylov_create(h, m_need, &h->kry));
   const long long N = h->g0.nodes();
   mcmg_solve_info agg{};
   agg.converged = 1;
@@ -564,13 +561,18 @@ mcmg_status mcmg_solve(mcmg_handle h, const void* f, void* u, const mcmg_solve_o
   auto t0 = std::chrono::steady_clock::now();
   for (int k = 0; k < o->nrhs; ++k) {
     cudaStream_t st = o->stream ? (cudaStream_t)o->stream : h->stream;
-    MCMG_TRY(krylov_begin(h->kry, (const double2*)f + (size_t)k * N, (double2*)u + (size_t)k * N,
-                          *o, st));
-    int done = 0;
-    while (!done) MCMG_TRY(krylov_advance(h->kry, true, &done));
     mcmg_solve_info one;
     mcmg_status fs;
-    krylov_info(h->kry, &one, &fs);
+    if (o->flags & MCMG_SOLVE_STATIONARY) {
+      MCMG_TRY(stationary_run(h->kry, (const double2*)f + (size_t)k * N,
+                              (double2*)u + (size_t)k * N, *o, st, &one, &fs));
+    } else {
+      MCMG_TRY(krylov_begin(h->kry, (const double2*)f + (size_t)k * N,
+                            (double2*)u + (size_t)k * N, *o, st));
+      int done = 0;
+      while (!done) MCMG_TRY(krylov_advance(h->kry, true, &done));
+      krylov_info(h->kry, &one, &fs);
+    }
     agg.iters = std::max(agg.iters, one.iters);
     agg.restarts = std::max(agg.restarts, one.restarts);
     agg.rel_residual = std::max(agg.rel_residual, one.rel_residual);

@@ -32,7 +32,13 @@ namespace mcmg {
 namespace tc {
 
 constexpr int M = 128;           // nodes per CTA (MMA M)
-constexpr int THREADS = 256;     // 8 warps
+// Threads per CTA: 128 (one per node row) for 2C <= 32, where the step is
+// HBM-bound and more CTAs per SM keep more loads in flight; 256 for larger C,
+// where the epilogue splits each row's columns over two warps.
+template <int K2>
+struct Threads {
+  static constexpr int value = K2 <= 32 ? 128 : 256;
+};
 constexpr unsigned SPIN_LIMIT = 1u << 20;   // ~1M polls with a short sleep: about a second at most
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -207,9 +213,10 @@ __device__ __forceinline__ void store_chunk(uint8_t* tile, int row, int ch, uint
 // before any of its shared-memory stores, so the loads of a thread overlap.
 template <int K2>
 struct Stage {
-  static constexpr int PER = tc::M * (K2 / 8) / tc::THREADS;              // A chunks / thread
-  static constexpr int N16 = K2 * K2 * 2 / 16;                            // B uint4 per tile
-  static constexpr int BPER = (N16 + tc::THREADS - 1) / tc::THREADS;      // B uint4 / thread
+  static constexpr int T = tc::Threads<K2>::value;
+  static constexpr int PER = tc::M * (K2 / 8) / T;              // A chunks / thread
+  static constexpr int N16 = K2 * K2 * 2 / 16;                  // B uint4 per tile
+  static constexpr int BPER = (N16 + T - 1) / T;                // B uint4 / thread
 };
 
 template <int K2>
@@ -217,7 +224,7 @@ __device__ __forceinline__ void load_a(uint4 (&v)[Stage<K2>::PER], const float2*
                                        long long n0, const TcParams& p, int tap) {
 #pragma unroll
   for (int i = 0; i < Stage<K2>::PER; ++i) {
-    const int idx = threadIdx.x + i * tc::THREADS;
+    const int idx = threadIdx.x + i * Stage<K2>::T;
     v[i] = load_chunk<K2>(src, n0, idx % tc::M, idx / tc::M, p, tap);
   }
 }
@@ -226,7 +233,7 @@ template <int K2>
 __device__ __forceinline__ void store_a(uint8_t* tile, const uint4 (&v)[Stage<K2>::PER]) {
 #pragma unroll
   for (int i = 0; i < Stage<K2>::PER; ++i) {
-    const int idx = threadIdx.x + i * tc::THREADS;
+    const int idx = threadIdx.x + i * Stage<K2>::T;
     store_chunk(tile, idx % tc::M, idx / tc::M, v[i]);
   }
 }
@@ -235,7 +242,7 @@ template <int K2>
 __device__ __forceinline__ void load_b(uint4 (&v)[Stage<K2>::BPER], const uint4* __restrict__ src) {
 #pragma unroll
   for (int i = 0; i < Stage<K2>::BPER; ++i) {
-    const int idx = threadIdx.x + i * tc::THREADS;
+    const int idx = threadIdx.x + i * Stage<K2>::T;
     v[i] = idx < Stage<K2>::N16 ? __ldg(src + idx) : make_uint4(0, 0, 0, 0);
   }
 }
@@ -244,7 +251,7 @@ template <int K2>
 __device__ __forceinline__ void store_b(uint8_t* tile, const uint4 (&v)[Stage<K2>::BPER]) {
 #pragma unroll
   for (int i = 0; i < Stage<K2>::BPER; ++i) {
-    const int idx = threadIdx.x + i * tc::THREADS;
+    const int idx = threadIdx.x + i * Stage<K2>::T;
     if (idx < Stage<K2>::N16) reinterpret_cast<uint4*>(tile)[idx] = v[i];
   }
 }
@@ -253,7 +260,8 @@ __device__ __forceinline__ void store_b(uint8_t* tile, const uint4 (&v)[Stage<K2
 // per lane) and the column half w / 4.
 template <int K2>
 struct Epi {
-  static constexpr int HC = K2 / 2;                  // FP32 columns per half
+  static constexpr int GROUPS = tc::Threads<K2>::value / 128;   // warps sharing a lane quarter
+  static constexpr int HC = K2 / GROUPS;             // FP32 columns per thread
   static constexpr int STEP = HC < 16 ? HC : 16;     // columns per TMEM load
   static constexpr int NCH = HC / 2;                 // complex channels per thread
 };
@@ -265,15 +273,14 @@ __device__ __forceinline__ void tmem_cols(uint32_t taddr, float* v) {
 }
 
 template <int K2, int D>
-__global__ void __launch_bounds__(tc::THREADS, (K2 >= 64 ? 1 : 4)) k_smooth_tc(TcParams p) {
+__global__ void __launch_bounds__(tc::Threads<K2>::value, (K2 >= 64 ? 1 : 8)) k_smooth_tc(TcParams p) {
   constexpr int C = K2 / 2;
   constexpr int NT = 2 * D + 1;
   constexpr int NA = 2;                      // A tiles (double buffer)
   constexpr uint32_t TM_COLS = (2 * K2 < 32) ? 32 : 2 * K2;
   constexpr size_t A_BYTES = (size_t)tc::M * K2 * 2;
   constexpr size_t B_BYTES = (size_t)K2 * K2 * 2;
-  constexpr int CH = K2 / 8;                         // 16-byte chunks per row
-  constexpr int PER = tc::M * CH / tc::THREADS;      // chunks per thread per tile (>= 1)
+  constexpr int PER = Stage<K2>::PER;                // chunks per thread per tile (>= 1)
   static_assert(PER >= 1, "tile smaller than the block");
   using E = Epi<K2>;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -385,7 +392,7 @@ __global__ void __launch_bounds__(tc::THREADS, (K2 >= 64 ? 1 : 4)) k_smooth_tc(T
     // first pre-smoothing step: t = r
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-      const int idx = threadIdx.x + i * tc::THREADS;
+      const int idx = threadIdx.x + i * Stage<K2>::T;
       store_chunk(Atile(0), idx % tc::M, idx / tc::M, load_chunk<K2>(r, n0, idx % tc::M, idx / tc::M, p, 0));
     }
   }
@@ -512,7 +519,7 @@ static mcmg_status tc_launch(const TcParams& p, int nrhs, cudaStream_t st) {
     attr_set = true;
   }
   dim3 grid((unsigned)((p.nodes + tc::M - 1) / tc::M), (unsigned)nrhs);
-  k_smooth_tc<K2, D><<<grid, tc::THREADS, smem, st>>>(p);
+  k_smooth_tc<K2, D><<<grid, tc::Threads<K2>::value, smem, st>>>(p);
   MCMG_CHECK_LAUNCH("smooth_tc");
   return MCMG_OK;
 }

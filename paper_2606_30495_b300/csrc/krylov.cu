@@ -245,6 +245,17 @@ __global__ void k_scale(const double2* __restrict__ w, const double* __restrict_
   v[p] = make_float2((float)(x.x * inv), (float)(x.y * inv));
 }
 
+// Stationary step: u += beta * z, beta = ||r|| (the V-cycle ran on r / beta).
+__global__ void k_stationary_update(const float2* __restrict__ z, const double* __restrict__ dsc,
+                                    double2* __restrict__ u, long long n) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const double beta = sqrt(dsc[0]);
+  const float2 zz = z[p];
+  const double2 o = u[p];
+  u[p] = make_double2(o.x + beta * zz.x, o.y + beta * zz.y);
+}
+
 // y = R^{-1} g for the k x k upper triangle of the rotated Hessenberg matrix.
 __global__ void __launch_bounds__(1024) k_backsolve(const double2* __restrict__ H, int m, int k,
                                                     const double2* __restrict__ g,
@@ -546,6 +557,52 @@ void krylov_info(const Krylov* k, mcmg_solve_info* info, mcmg_status* final_stat
     info->converged = k->converged ? 1 : 0;
   }
   if (final_status) *final_status = k->final;
+}
+
+// The stationary McMg iteration (Eq. mcmg_iteration): r = f - A u in FP64,
+// u <- u + MG(r), until ||r|| / ||f|| <= tol or max_iters V-cycles.  The
+// V-cycle runs on r / ||r|| (it is linear) so the complex64 input stays in
+// range.  Synchronous.
+mcmg_status stationary_run(Krylov* k, const double2* f, double2* u, const mcmg_solve_opts& o,
+                           cudaStream_t st, mcmg_solve_info* info, mcmg_status* final_status) {
+  mcmg_handle_s* h = k->h;
+  const long long n = k->n;
+  const int max_iters = o.max_iters > 0 ? o.max_iters : 20 * (h->g0.d == 3 ? h->g0.nz : h->g0.ny);
+  const auto t0 = std::chrono::steady_clock::now();
+  double fnorm = -1.0, rel = 0.0;
+  int it = 0;
+  mcmg_status fs = MCMG_OK;
+  bool conv = false;
+  for (;; ++it) {
+    MCMG_TRY(launch_residual64(h->q64, f, u, k->r64, k->part, k->nblk, h->g0, 1, st));
+    k_reduce_res<<<1, RED_T, 0, st>>>(k->part, k->nblk, k->dsc, &k->stat_d->rr);
+    MCMG_CHECK_LAUNCH("reduce_res");
+    MCMG_CUDA(cudaStreamSynchronize(st));
+    Stat sv;
+    std::memcpy(&sv, (const void*)k->stat_h, sizeof(Stat));
+    if (fnorm < 0.0) fnorm = std::sqrt(sv.ff);
+    rel = fnorm > 0.0 ? std::sqrt(sv.rr) / fnorm : 0.0;
+    if (!std::isfinite(rel)) { fs = MCMG_ERR_NUMERIC; break; }
+    if (rel <= o.tol) { conv = true; break; }
+    if (it >= max_iters) { fs = MCMG_ERR_NOT_CONVERGED; break; }
+    if (h->err_host && *(volatile int*)h->err_host) { fs = MCMG_ERR_TIMEOUT; break; }
+    const long long cover = std::max<long long>(n, k->m + 1);
+    k_start_cycle<<<(unsigned)((cover + 255) / 256), 256, 0, st>>>(k->r64, k->dsc, k->V, n, k->g,
+                                                                   k->m);
+    MCMG_CHECK_LAUNCH("start_cycle");
+    MCMG_TRY(vcycle_run(h, k->vw, k->V, k->Z, 1, st));
+    k_stationary_update<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(k->Z, k->dsc, u, n);
+    MCMG_CHECK_LAUNCH("stationary_update");
+  }
+  if (info) {
+    info->iters = it;
+    info->restarts = 0;
+    info->rel_residual = rel;
+    info->converged = conv ? 1 : 0;
+    info->t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  *final_status = fs;
+  return MCMG_OK;
 }
 
 mcmg_status cgs2_once(mcmg_handle_s* h, const float2* V, int kv, long long n, float2* w,

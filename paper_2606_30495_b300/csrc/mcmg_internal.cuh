@@ -183,6 +183,9 @@ mcmg_status krylov_begin(Krylov* k, const double2* f, double2* u, const mcmg_sol
 mcmg_status krylov_advance(Krylov* k, bool blocking, int* done);
 void krylov_info(const Krylov* k, mcmg_solve_info* info, mcmg_status* final_status);
 int krylov_m(const Krylov* k);
+// The stationary iteration u <- u + MG(f - A u), synchronous, on a Krylov workspace.
+mcmg_status stationary_run(Krylov* k, const double2* f, double2* u, const mcmg_solve_opts& o,
+                           cudaStream_t st, mcmg_solve_info* info, mcmg_status* final_status);
 cudaStream_t krylov_stream(const Krylov* k);   // the solve's private stream
 // CGS2 on caller buffers (used by mcmg_cgs2).
 mcmg_status cgs2_once(mcmg_handle_s* h, const float2* V, int k, long long n, float2* w,

@@ -331,3 +331,28 @@ def test_errors_are_reported(ctx):
             h.smooth(5, 0, x, None, x.clone())
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("name", ["helm2d_n64_homogeneous", "helm2d_n64_slmg"])
+def test_stationary_iteration_matches_oracle(ctx, name):
+    """The stationary McMg iteration (Eq. mcmg_iteration): the true residual
+    after k = 1..6 V-cycles matches the oracle's iterates."""
+    m = workload_model(name)
+    feats = O.setup(m["q"], m["w"])
+    f = I.point_source(m["shape"])
+    _, oinfo = O.stationary_solve(lambda u: O.apply_A(m["q"], u),
+                                  lambda v: O.vcycle(m["w"], feats, v), f, tol=1e-30, max_iters=6)
+    h = handle(ctx, m)
+    try:
+        from paper_2606_30495_b300 import mcmg
+        for k in range(1, 7):
+            u = torch.zeros(m["shape"], dtype=torch.complex128, device="cuda")
+            st, info = h.solve(dev(f, torch.complex128), u, tol=1e-30, restart_m=1, max_iters=k,
+                               flags=mcmg.SOLVE_STATIONARY)
+            assert st == -5 and info["iters"] == k
+            want = oinfo["history"][k]
+            assert abs(info["rel_residual"] - want) <= 1e-4 * want, (k, info, want)
+            res = np.linalg.norm(f - O.apply_A(m["q"], host(u))) / np.linalg.norm(f)
+            assert abs(res - want) <= 1e-4 * want
+    finally:
+        h.close()
