@@ -461,6 +461,21 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
       net_a = net_n;
     }
   }
+  // autotune the CUDA-core smoothing shapes on scratch fields of the largest level
+  {
+    size_t big = 0;
+    for (int l = 0; l < L; ++l)
+      big = std::max(big, (size_t)h->lv[l].g.nodes() * h->lv[l].C);
+    float2 *s0, *s1, *s2;
+    if ((s = dev_alloc(h, tmp, (void**)&s0, sizeof(float2) * big)) ||
+        (s = dev_alloc(h, tmp, (void**)&s1, sizeof(float2) * big)) ||
+        (s = dev_alloc(h, tmp, (void**)&s2, sizeof(float2) * big)))
+      return cleanup(), s;
+    MCMG_CUDA(cudaMemsetAsync(s0, 0, sizeof(float2) * big, st));
+    MCMG_CUDA(cudaMemsetAsync(s1, 0, sizeof(float2) * big, st));
+    for (int l = 0; l < L; ++l)
+      if ((s = autotune_smooth(h->lv[l], s0, s1, s2, st))) return cleanup(), s;
+  }
   cudaError_t e = cudaStreamSynchronize(st);
   cleanup();
   if (e != cudaSuccess) return cuda_fail(e, "setup");

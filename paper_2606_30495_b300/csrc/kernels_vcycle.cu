@@ -15,27 +15,47 @@
 
 namespace mcmg {
 
-// Thread (co, g) of a 256-thread block owns output channel co of TN nodes;
-// G = 256 / C node groups, NB = G * TN nodes per block.  TN is chosen per
-// launch: large for big grids (weight reuse), small for coarse grids (enough
-// blocks to cover the SMs).
-template <int C, int TN_>
+// Thread shapes.  Thread (cg, g) of a 256-thread block owns the CO
+// consecutive output channels cg*CO .. cg*CO + CO - 1 of TN nodes
+// n0 + g + G*k (k < TN), with CG = C / CO channel groups and G = 256 / CG
+// node groups; a block covers NB = G * TN consecutive nodes.  Each weight load
+// (CO complex values, one 32-byte vector load for CO = 4) feeds CO * TN
+// complex FMAs.  The shape is chosen per level and mode by the autotuner at
+// setup (autotune_smooth); pick_shape is the fallback heuristic.
+template <int C, int TN_, int CO_>
 struct Tile {
-  static constexpr int G = 256 / C;      // node groups
-  static constexpr int TN = TN_;         // nodes per thread
-  static constexpr int NB = G * TN;      // nodes per block
+  static constexpr int CO = CO_;
+  static constexpr int CG = C / CO;
+  static constexpr int G = 256 / CG;
+  static constexpr int TN = TN_;
+  static constexpr int NB = G * TN;
 };
 
-// Largest nodes-per-thread (of 8, 2, 1) that still gives at least two blocks
-// per SM, so coarse levels are not left with a handful of blocks.
-static int pick_tn(long long nodes, int C, int nrhs) {
+struct Shape {
+  int tn, co;
+};
+// co = 0 marks the K-split shape (k_smooth_ks).
+static constexpr Shape kShapes[] = {{8, 1}, {2, 1}, {1, 1}, {2, 4}, {1, 4}, {1, 0}};
+static constexpr int kNumShapes = 6;
+
+static bool shape_ok(int s, int C) { return kShapes[s].co == 0 ? C >= 8 : kShapes[s].co <= C; }
+
+// Largest nodes-per-thread (8, 2 or 1, one channel per thread) that still
+// gives at least two blocks per SM.
+static int pick_shape(long long nodes, int C, int nrhs) {
   const long long want = 2 * 148;
   const int G = 256 / C;
-  for (int tn : {8, 2}) {
+  for (int s = 0; s < 2; ++s) {
+    const int tn = kShapes[s].tn;
     long long blocks = (nodes + (long long)G * tn - 1) / ((long long)G * tn) * nrhs;
-    if (blocks >= want) return tn;
+    if (blocks >= want) return s;
   }
-  return 1;
+  return 2;
+}
+
+// Largest nodes-per-thread (8, 2 or 1) for the transfer kernels.
+static int pick_tn(long long nodes, int C, int nrhs) {
+  return kShapes[pick_shape(nodes, C, nrhs)].tn;
 }
 
 struct SmoothParams {
@@ -59,12 +79,40 @@ __device__ __forceinline__ void node_xyz(long long n, int nx, int ny, int& x, in
   z = (int)(rest / ny);
 }
 
-template <int C, int D, int MODE, int TN>
+// CO consecutive complex values (one float2, or two float4 for CO = 4).
+template <int CO>
+__device__ __forceinline__ void ldc(const float2* __restrict__ q, float2 (&v)[CO]) {
+  if constexpr (CO == 1) {
+    v[0] = __ldg(q);
+  } else {
+    static_assert(CO == 4, "CO is 1 or 4");
+    const float4* q4 = reinterpret_cast<const float4*>(q);
+    const float4 a = __ldg(q4), b = __ldg(q4 + 1);
+    v[0] = make_float2(a.x, a.y);
+    v[1] = make_float2(a.z, a.w);
+    v[2] = make_float2(b.x, b.y);
+    v[3] = make_float2(b.z, b.w);
+  }
+}
+
+template <int CO>
+__device__ __forceinline__ void stc(float2* q, const float2 (&v)[CO]) {
+  if constexpr (CO == 1) {
+    q[0] = v[0];
+  } else {
+    float4* q4 = reinterpret_cast<float4*>(q);
+    q4[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    q4[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+  }
+}
+
+template <int C, int D, int MODE, int TN, int CO>
 __global__ void __launch_bounds__(256) k_smooth(SmoothParams p) {
-  using T = Tile<C, TN>;
+  using T = Tile<C, TN, CO>;
   extern __shared__ float2 sm[];
-  const int co = threadIdx.x % C;
-  const int g = threadIdx.x / C;
+  const int cg = threadIdx.x % T::CG;
+  const int g = threadIdx.x / T::CG;
+  const int co0 = cg * CO;
   const long long N = p.nodes;
   const size_t off = (size_t)blockIdx.y * (size_t)N * C;
   const float2* __restrict__ r = p.r + off;
@@ -72,33 +120,40 @@ __global__ void __launch_bounds__(256) k_smooth(SmoothParams p) {
   float2* __restrict__ eout = p.e_out + off;
   const long long n0 = (long long)blockIdx.x * T::NB;
 
-  long long nn[T::TN];
-  long long nc[T::TN];  // clamped (always a valid node)
+  long long nn[TN];
+  long long nc[TN];  // clamped (always a valid node)
 #pragma unroll
-  for (int k = 0; k < T::TN; ++k) {
+  for (int k = 0; k < TN; ++k) {
     nn[k] = n0 + g + (long long)T::G * k;
     nc[k] = nn[k] < N ? nn[k] : N - 1;
   }
 
-  float2 t[T::TN];
+  float2 t[TN][CO];
   if (ein) {
-    float2 acc[T::TN], acca[T::TN];
-    int cx[T::TN], cy[T::TN], cz[T::TN];
+    float2 acc[TN][CO], acca[TN][CO];
+    int cx[TN], cy[TN], cz[TN];
 #pragma unroll
-    for (int k = 0; k < T::TN; ++k) {
+    for (int k = 0; k < TN; ++k) {
       node_xyz(nc[k], p.nx, p.ny, cx[k], cy[k], cz[k]);
-      acc[k] = make_float2(0.f, 0.f);
-      acca[k] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < CO; ++c) {
+        acc[k][c] = make_float2(0.f, 0.f);
+        acca[k][c] = make_float2(0.f, 0.f);
+      }
     }
     // centre tap and K_A share the loads of e at the node itself
     for (int ci = 0; ci < C; ++ci) {
-      const float2 w0 = __ldg(p.Wt + ci * C + co);
-      const float2 wa = __ldg(p.KAt + ci * C + co);
+      float2 w0[CO], wa[CO];
+      ldc<CO>(p.Wt + ci * C + co0, w0);
+      ldc<CO>(p.KAt + ci * C + co0, wa);
 #pragma unroll
-      for (int k = 0; k < T::TN; ++k) {
+      for (int k = 0; k < TN; ++k) {
         const float2 v = __ldg(ein + nc[k] * C + ci);
-        cfma(acc[k], w0, v);
-        cfma(acca[k], wa, v);
+#pragma unroll
+        for (int c = 0; c < CO; ++c) {
+          cfma(acc[k][c], w0[c], v);
+          cfma(acca[k][c], wa[c], v);
+        }
       }
     }
     const long long sxy = (long long)p.nx * p.ny;
@@ -106,10 +161,10 @@ __global__ void __launch_bounds__(256) k_smooth(SmoothParams p) {
     for (int tap = 1; tap <= 2 * D; ++tap) {
       const int axis = (tap - 1) >> 1;
       const int sgn = (tap & 1) ? -1 : 1;
-      long long nb[T::TN];
-      bool ok[T::TN];
+      long long nb[TN];
+      bool ok[TN];
 #pragma unroll
-      for (int k = 0; k < T::TN; ++k) {
+      for (int k = 0; k < TN; ++k) {
         int c = axis == 0 ? cx[k] : (axis == 1 ? cy[k] : cz[k]);
         int ext = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
         long long stride = axis == 0 ? 1 : (axis == 1 ? p.nx : sxy);
@@ -118,114 +173,255 @@ __global__ void __launch_bounds__(256) k_smooth(SmoothParams p) {
       }
       const float2* wt = p.Wt + (size_t)tap * C * C;
       for (int ci = 0; ci < C; ++ci) {
-        const float2 w = __ldg(wt + ci * C + co);
+        float2 w[CO];
+        ldc<CO>(wt + ci * C + co0, w);
 #pragma unroll
-        for (int k = 0; k < T::TN; ++k) {
+        for (int k = 0; k < TN; ++k) {
           const float2 v = __ldg(ein + nb[k] * C + ci);
-          if (ok[k]) cfma(acc[k], w, v);
+          if (ok[k]) {
+#pragma unroll
+            for (int c = 0; c < CO; ++c) cfma(acc[k][c], w[c], v);
+          }
         }
       }
     }
 #pragma unroll
-    for (int k = 0; k < T::TN; ++k) {
-      const float2 rv = r[nc[k] * C + co];
-      const float2 av = p.a[nc[k] * C + co];
-      t[k] = csub(csub(rv, acc[k]), cmul(av, acca[k]));
+    for (int k = 0; k < TN; ++k) {
+      float2 rv[CO], av[CO];
+      ldc<CO>(r + nc[k] * C + co0, rv);
+      ldc<CO>(p.a + nc[k] * C + co0, av);
+#pragma unroll
+      for (int c = 0; c < CO; ++c) t[k][c] = csub(csub(rv[c], acc[k][c]), cmul(av[c], acca[k][c]));
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < T::TN; ++k) t[k] = r[nc[k] * C + co];
+    for (int k = 0; k < TN; ++k) ldc<CO>(r + nc[k] * C + co0, t[k]);
   }
 
   if (MODE == 1) {  // residual only
 #pragma unroll
-    for (int k = 0; k < T::TN; ++k)
-      if (nn[k] < N) eout[nn[k] * C + co] = t[k];
+    for (int k = 0; k < TN; ++k)
+      if (nn[k] < N) stc<CO>(eout + nn[k] * C + co0, t[k]);
     return;
   }
 
   float2* sm_t = sm;
   float2* sm_z = sm + T::NB * C;
 #pragma unroll
-  for (int k = 0; k < T::TN; ++k) sm_t[(g + T::G * k) * C + co] = t[k];
+  for (int k = 0; k < TN; ++k)
+#pragma unroll
+    for (int c = 0; c < CO; ++c) sm_t[(g + T::G * k) * C + co0 + c] = t[k][c];
   __syncthreads();
 
   // z = s (.) (K_S t)
-  float2 z[T::TN];
+  float2 z[TN][CO];
 #pragma unroll
-  for (int k = 0; k < T::TN; ++k) z[k] = make_float2(0.f, 0.f);
+  for (int k = 0; k < TN; ++k)
+#pragma unroll
+    for (int c = 0; c < CO; ++c) z[k][c] = make_float2(0.f, 0.f);
   for (int ci = 0; ci < C; ++ci) {
-    const float2 w = __ldg(p.KSt + ci * C + co);
+    float2 w[CO];
+    ldc<CO>(p.KSt + ci * C + co0, w);
 #pragma unroll
-    for (int k = 0; k < T::TN; ++k) cfma(z[k], w, sm_t[(g + T::G * k) * C + ci]);
+    for (int k = 0; k < TN; ++k) {
+      const float2 v = sm_t[(g + T::G * k) * C + ci];
+#pragma unroll
+      for (int c = 0; c < CO; ++c) cfma(z[k][c], w[c], v);
+    }
   }
 #pragma unroll
-  for (int k = 0; k < T::TN; ++k) {
-    z[k] = cmul(p.s[nc[k] * C + co], z[k]);
-    sm_z[(g + T::G * k) * C + co] = z[k];
+  for (int k = 0; k < TN; ++k) {
+    float2 sv[CO];
+    ldc<CO>(p.s + nc[k] * C + co0, sv);
+#pragma unroll
+    for (int c = 0; c < CO; ++c) {
+      z[k][c] = cmul(sv[c], z[k][c]);
+      sm_z[(g + T::G * k) * C + co0 + c] = z[k][c];
+    }
   }
   __syncthreads();
 
   // e' = e + W^(i) z
-  float2 u[T::TN];
+  float2 u[TN][CO];
 #pragma unroll
-  for (int k = 0; k < T::TN; ++k) u[k] = make_float2(0.f, 0.f);
+  for (int k = 0; k < TN; ++k)
+#pragma unroll
+    for (int c = 0; c < CO; ++c) u[k][c] = make_float2(0.f, 0.f);
   for (int ci = 0; ci < C; ++ci) {
-    const float2 w = __ldg(p.Wst + ci * C + co);
+    float2 w[CO];
+    ldc<CO>(p.Wst + ci * C + co0, w);
 #pragma unroll
-    for (int k = 0; k < T::TN; ++k) cfma(u[k], w, sm_z[(g + T::G * k) * C + ci]);
+    for (int k = 0; k < TN; ++k) {
+      const float2 v = sm_z[(g + T::G * k) * C + ci];
+#pragma unroll
+      for (int c = 0; c < CO; ++c) cfma(u[k][c], w[c], v);
+    }
   }
 #pragma unroll
-  for (int k = 0; k < T::TN; ++k) {
+  for (int k = 0; k < TN; ++k) {
     if (nn[k] < N) {
-      float2 v = u[k];
-      if (ein) v = cadd(v, ein[nn[k] * C + co]);
-      eout[nn[k] * C + co] = v;
+      if (ein) {
+        float2 ev[CO];
+        ldc<CO>(ein + nn[k] * C + co0, ev);
+#pragma unroll
+        for (int c = 0; c < CO; ++c) u[k][c] = cadd(u[k][c], ev[c]);
+      }
+      stc<CO>(eout + nn[k] * C + co0, u[k]);
     }
   }
 }
 
-template <int C, int D, int TN>
-static mcmg_status smooth_tn(const SmoothParams& p, int mode, int nrhs, cudaStream_t st) {
-  using T = Tile<C, TN>;
-  dim3 grid((unsigned)((p.nodes + T::NB - 1) / T::NB), (unsigned)nrhs);
-  size_t smem = mode == 0 ? 2 * (size_t)T::NB * C * sizeof(float2) : 0;
-  if (mode == 0)
-    k_smooth<C, D, 0, TN><<<grid, 256, smem, st>>>(p);
-  else
-    k_smooth<C, D, 1, TN><<<grid, 256, smem, st>>>(p);
-  MCMG_CHECK_LAUNCH("smooth");
-  return MCMG_OK;
+template <int C, int D, int TN, int CO>
+static mcmg_status smooth_shape(const SmoothParams& p, int mode, int nrhs, cudaStream_t st) {
+  if constexpr (CO > C) {
+    set_error("thread shape wider than the channel count");
+    return MCMG_ERR_SHAPE;
+  } else {
+    using T = Tile<C, TN, CO>;
+    dim3 grid((unsigned)((p.nodes + T::NB - 1) / T::NB), (unsigned)nrhs);
+    size_t smem = mode == 0 ? 2 * (size_t)T::NB * C * sizeof(float2) : 0;
+    if (mode == 0)
+      k_smooth<C, D, 0, TN, CO><<<grid, 256, smem, st>>>(p);
+    else
+      k_smooth<C, D, 1, TN, CO><<<grid, 256, smem, st>>>(p);
+    MCMG_CHECK_LAUNCH("smooth");
+    return MCMG_OK;
+  }
+}
+
+
+// K-split shape for coarse levels (few nodes, many channels): four lanes share
+// one (node, output channel) pair and each sums a quarter of the input
+// channels; two warp shuffles combine the partial sums.  A warp holds 8
+// output channels x 4 quarters of one node, a 256-thread block NB = 64 / C * 8
+// nodes' worth of C / 8 warps each.  Four times the threads of the one-output
+// shape, so the latency of the weight and field loads is hidden by other warps.
+template <int C>
+struct KsTile {
+  static constexpr int WPN = C / 8;          // warps per node
+  static constexpr int NB = 8 / WPN;         // nodes per block
+  static constexpr int KQ = C / 4;           // input channels per quarter
+};
+
+__device__ __forceinline__ float2 quad_sum(float2 v) {
+  v.x += __shfl_xor_sync(0xffffffffu, v.x, 8);
+  v.y += __shfl_xor_sync(0xffffffffu, v.y, 8);
+  v.x += __shfl_xor_sync(0xffffffffu, v.x, 16);
+  v.y += __shfl_xor_sync(0xffffffffu, v.y, 16);
+  return v;
+}
+
+template <int C, int D, int MODE>
+__global__ void __launch_bounds__(256) k_smooth_ks(SmoothParams p) {
+  using T = KsTile<C>;
+  __shared__ float2 sm_t[T::NB * C];
+  __shared__ float2 sm_z[T::NB * C];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nl = warp / T::WPN;                       // node within the block
+  const int co = (warp % T::WPN) * 8 + (lane & 7);    // output channel
+  const int q = lane >> 3;                            // input-channel quarter
+  const int ci0 = q * T::KQ;
+  const long long N = p.nodes;
+  const size_t off = (size_t)blockIdx.y * (size_t)N * C;
+  const float2* __restrict__ r = p.r + off;
+  const float2* __restrict__ ein = p.e_in ? p.e_in + off : nullptr;
+  float2* __restrict__ eout = p.e_out + off;
+  const long long n = (long long)blockIdx.x * T::NB + nl;
+  const long long nc = n < N ? n : N - 1;
+
+  float2 t;
+  if (ein) {
+    float2 acc = make_float2(0.f, 0.f), acca = make_float2(0.f, 0.f);
+    int cx, cy, cz;
+    node_xyz(nc, p.nx, p.ny, cx, cy, cz);
+    for (int ci = ci0; ci < ci0 + T::KQ; ++ci) {
+      const float2 v = __ldg(ein + nc * C + ci);
+      cfma(acc, __ldg(p.Wt + ci * C + co), v);
+      cfma(acca, __ldg(p.KAt + ci * C + co), v);
+    }
+    const long long sxy = (long long)p.nx * p.ny;
+#pragma unroll
+    for (int tap = 1; tap <= 2 * D; ++tap) {
+      const int axis = (tap - 1) >> 1;
+      const int sgn = (tap & 1) ? -1 : 1;
+      const int c = axis == 0 ? cx : (axis == 1 ? cy : cz);
+      const int ext = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
+      const long long stride = axis == 0 ? 1 : (axis == 1 ? p.nx : sxy);
+      if (c + sgn < 0 || c + sgn >= ext) continue;
+      const float2* e_nb = ein + (nc + sgn * stride) * C;
+      const float2* wt = p.Wt + (size_t)tap * C * C;
+      for (int ci = ci0; ci < ci0 + T::KQ; ++ci) cfma(acc, __ldg(wt + ci * C + co), __ldg(e_nb + ci));
+    }
+    acc = quad_sum(acc);
+    acca = quad_sum(acca);
+    t = csub(csub(__ldg(r + nc * C + co), acc), cmul(__ldg(p.a + nc * C + co), acca));
+  } else {
+    t = __ldg(r + nc * C + co);
+  }
+  if (MODE == 1) {
+    if (q == 0 && n < N) eout[n * C + co] = t;
+    return;
+  }
+  if (q == 0) sm_t[nl * C + co] = t;
+  __syncthreads();
+  float2 z = make_float2(0.f, 0.f);
+  for (int ci = ci0; ci < ci0 + T::KQ; ++ci) cfma(z, __ldg(p.KSt + ci * C + co), sm_t[nl * C + ci]);
+  z = cmul(__ldg(p.s + nc * C + co), quad_sum(z));
+  if (q == 0) sm_z[nl * C + co] = z;
+  __syncthreads();
+  float2 u = make_float2(0.f, 0.f);
+  for (int ci = ci0; ci < ci0 + T::KQ; ++ci) cfma(u, __ldg(p.Wst + ci * C + co), sm_z[nl * C + ci]);
+  u = quad_sum(u);
+  if (q == 0 && n < N) eout[n * C + co] = ein ? cadd(u, ein[n * C + co]) : u;
 }
 
 template <int C, int D>
-static mcmg_status smooth_c(const SmoothParams& p, int mode, int nrhs, cudaStream_t st) {
-  switch (pick_tn(p.nodes, C, nrhs)) {
-    case 8: return smooth_tn<C, D, 8>(p, mode, nrhs, st);
-    case 2: return smooth_tn<C, D, 2>(p, mode, nrhs, st);
-    default: return smooth_tn<C, D, 1>(p, mode, nrhs, st);
+static mcmg_status smooth_ks(const SmoothParams& p, int mode, int nrhs, cudaStream_t st) {
+  if constexpr (C < 8) {
+    set_error("the K-split shape needs at least 8 channels");
+    return MCMG_ERR_SHAPE;
+  } else {
+    using T = KsTile<C>;
+    dim3 grid((unsigned)((p.nodes + T::NB - 1) / T::NB), (unsigned)nrhs);
+    if (mode == 0)
+      k_smooth_ks<C, D, 0><<<grid, 256, 0, st>>>(p);
+    else
+      k_smooth_ks<C, D, 1><<<grid, 256, 0, st>>>(p);
+    MCMG_CHECK_LAUNCH("smooth_ks");
+    return MCMG_OK;
+  }
+}
+
+template <int C, int D>
+static mcmg_status smooth_c(const SmoothParams& p, int mode, int shape, int nrhs, cudaStream_t st) {
+  switch (shape) {
+    case 0: return smooth_shape<C, D, 8, 1>(p, mode, nrhs, st);
+    case 1: return smooth_shape<C, D, 2, 1>(p, mode, nrhs, st);
+    case 2: return smooth_shape<C, D, 1, 1>(p, mode, nrhs, st);
+    case 3: return smooth_shape<C, D, 2, 4>(p, mode, nrhs, st);
+    case 4: return smooth_shape<C, D, 1, 4>(p, mode, nrhs, st);
+    default: return smooth_ks<C, D>(p, mode, nrhs, st);
   }
 }
 
 template <int D>
-static mcmg_status smooth_d(const SmoothParams& p, int C, int mode, int nrhs, cudaStream_t st) {
+static mcmg_status smooth_d(const SmoothParams& p, int C, int mode, int shape, int nrhs,
+                            cudaStream_t st) {
   switch (C) {
-    case 1: return smooth_c<1, D>(p, mode, nrhs, st);
-    case 2: return smooth_c<2, D>(p, mode, nrhs, st);
-    case 4: return smooth_c<4, D>(p, mode, nrhs, st);
-    case 8: return smooth_c<8, D>(p, mode, nrhs, st);
-    case 16: return smooth_c<16, D>(p, mode, nrhs, st);
-    case 32: return smooth_c<32, D>(p, mode, nrhs, st);
-    case 64: return smooth_c<64, D>(p, mode, nrhs, st);
+    case 1: return smooth_c<1, D>(p, mode, shape, nrhs, st);
+    case 2: return smooth_c<2, D>(p, mode, shape, nrhs, st);
+    case 4: return smooth_c<4, D>(p, mode, shape, nrhs, st);
+    case 8: return smooth_c<8, D>(p, mode, shape, nrhs, st);
+    case 16: return smooth_c<16, D>(p, mode, shape, nrhs, st);
+    case 32: return smooth_c<32, D>(p, mode, shape, nrhs, st);
+    case 64: return smooth_c<64, D>(p, mode, shape, nrhs, st);
   }
   set_error("unsupported channel count %d", C);
   return MCMG_ERR_SHAPE;
 }
 
-mcmg_status launch_smooth(const Level& L, int step, const float2* r, const float2* e_in,
-                          float2* e_out, int mode, int nrhs, cudaStream_t st) {
-  if (mode == 0 && L.use_tc)
-    return launch_smooth_tc(L, L.tcw, step, r, e_in, e_out, nrhs, L.err, st);
+static SmoothParams smooth_params(const Level& L, int step, const float2* r, const float2* e_in,
+                                  float2* e_out, int mode) {
   SmoothParams p;
   p.r = r;
   p.e_in = e_in;
@@ -240,7 +436,61 @@ mcmg_status launch_smooth(const Level& L, int step, const float2* r, const float
   p.ny = L.g.ny;
   p.nz = L.g.nz;
   p.nodes = L.g.nodes();
-  return L.g.d == 3 ? smooth_d<3>(p, L.C, mode, nrhs, st) : smooth_d<2>(p, L.C, mode, nrhs, st);
+  return p;
+}
+
+static mcmg_status smooth_run(const Level& L, const SmoothParams& p, int mode, int shape, int nrhs,
+                              cudaStream_t st) {
+  return L.g.d == 3 ? smooth_d<3>(p, L.C, mode, shape, nrhs, st)
+                    : smooth_d<2>(p, L.C, mode, shape, nrhs, st);
+}
+
+mcmg_status launch_smooth(const Level& L, int step, const float2* r, const float2* e_in,
+                          float2* e_out, int mode, int nrhs, cudaStream_t st) {
+  if (mode == 0 && L.use_tc)
+    return launch_smooth_tc(L, L.tcw, step, r, e_in, e_out, nrhs, L.err, st);
+  const SmoothParams p = smooth_params(L, step, r, e_in, e_out, mode);
+  int shape = L.shape[mode];
+  if (shape < 0 || !shape_ok(shape, L.C)) shape = pick_shape(p.nodes, L.C, nrhs);
+  return smooth_run(L, p, mode, shape, nrhs, st);
+}
+
+// Autotuner: time every valid thread shape of the CUDA-core smoothing kernel
+// on this level (the step with e and the residual mode) with CUDA events on
+// scratch fields, and keep the fastest in L.shape[mode].  Run once per
+// medium at setup, before any V-cycle graph is captured.
+mcmg_status autotune_smooth(Level& L, float2* r, float2* e, float2* out, cudaStream_t st) {
+  cudaEvent_t e0, e1;
+  MCMG_CUDA(cudaEventCreate(&e0));
+  MCMG_CUDA(cudaEventCreate(&e1));
+  mcmg_status status = MCMG_OK;
+  for (int mode = 0; mode < 2 && status == MCMG_OK; ++mode) {
+    if (mode == 0 && L.use_tc) continue;
+    const SmoothParams p = smooth_params(L, 0, r, e, out, mode);
+    float best = 1e30f;
+    int best_s = -1;
+    for (int s = 0; s < kNumShapes; ++s) {
+      if (!shape_ok(s, L.C)) continue;
+      for (int rep = 0; rep < 2; ++rep)
+        if ((status = smooth_run(L, p, mode, s, 1, st)) != MCMG_OK) break;
+      if (status != MCMG_OK) break;
+      cudaEventRecord(e0, st);
+      const int reps = 5;
+      for (int rep = 0; rep < reps; ++rep)
+        if ((status = smooth_run(L, p, mode, s, 1, st)) != MCMG_OK) break;
+      if (status != MCMG_OK) break;
+      cudaEventRecord(e1, st);
+      cudaError_t ce = cudaEventSynchronize(e1);
+      if (ce != cudaSuccess) { status = cuda_fail(ce, "autotune"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; best_s = s; }
+    }
+    L.shape[mode] = best_s;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return status;
 }
 
 // ---------------------------------------------------------------------------
@@ -260,7 +510,7 @@ struct TransferParams {
 
 template <int CO, int D, int TN>
 __global__ void __launch_bounds__(256) k_restrict(TransferParams p) {
-  using T = Tile<CO, TN>;
+  using T = Tile<CO, TN, 1>;
   const int co = threadIdx.x % CO;
   const int g = threadIdx.x / CO;
   const long long NC = p.dst_nodes;
@@ -310,7 +560,7 @@ __global__ void __launch_bounds__(256) k_restrict(TransferParams p) {
 // combinations of its candidates rather than all 3^d taps.
 template <int CO, int D, int TN>
 __global__ void __launch_bounds__(256) k_prolong_add(TransferParams p) {
-  using T = Tile<CO, TN>;
+  using T = Tile<CO, TN, 1>;
   const int co = threadIdx.x % CO;
   const int g = threadIdx.x / CO;
   const long long NF = p.dst_nodes;
@@ -360,7 +610,7 @@ __global__ void __launch_bounds__(256) k_prolong_add(TransferParams p) {
 
 template <int CO, int D, int TN>
 static mcmg_status transfer_tn(const TransferParams& p, bool restrict_, int nrhs, cudaStream_t st) {
-  using T = Tile<CO, TN>;
+  using T = Tile<CO, TN, 1>;
   dim3 grid((unsigned)((p.dst_nodes + T::NB - 1) / T::NB), (unsigned)nrhs);
   if (restrict_)
     k_restrict<CO, D, TN><<<grid, 256, 0, st>>>(p);

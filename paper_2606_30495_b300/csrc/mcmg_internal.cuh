@@ -92,6 +92,7 @@ struct Level {
   float2* Rt = nullptr;       // [T3][C][Cn]
   float2* Pt = nullptr;       // [T3][Cn][C]
   bool use_tc = false;        // smoothing step on tcgen05 (BF16 mixing)
+  int shape[2] = {-1, -1};    // CUDA-core smoothing thread shape per mode (autotuned)
   TcWeights tcw;
   int* err = nullptr;         // device view of the handle's error word
 };
@@ -109,6 +110,9 @@ mcmg_status launch_smooth(const Level& L, int step, const float2* r, const float
                           float2* e_out, int mode, int nrhs, cudaStream_t st);
 mcmg_status launch_restrict(const Level& L, const float2* t, float2* rc, int nrhs,
                             cudaStream_t st);
+// Time the thread shapes of the CUDA-core smoothing kernel on level L and keep
+// the fastest per mode (r, e, out: scratch fields of nodes * C elements).
+mcmg_status autotune_smooth(Level& L, float2* r, float2* e, float2* out, cudaStream_t st);
 mcmg_status launch_prolong_add(const Level& L, const float2* ec, float2* e, int nrhs,
                                cudaStream_t st);
 mcmg_status launch_lift(const float2* r, const float2* lift, float2* r1, int C, long long nodes,
