@@ -19,9 +19,7 @@ struct Request {
   const double2* f = nullptr;
   double2* u = nullptr;
   mcmg_solve_opts o{};
-  std::vector<mcmg::Krylov*> kry;   // one per right-hand side
-  std::vector<int> done;
-  cudaStream_t st = nullptr;
+  mcmg::KrylovBlock* blk = nullptr;  // every right-hand side, V-cycles batched
   size_t bytes_needed = 0;
   std::chrono::steady_clock::time_point t_submit;
   mcmg_status status = MCMG_PENDING;
@@ -116,6 +114,7 @@ mcmg_status vwork_create(mcmg_handle_s* h, int nrhs, VWork** out) {
 void vwork_destroy(mcmg_handle_s* h, VWork* w) {
   if (!w) return;
   if (w->graph) cudaGraphExecDestroy(w->graph);
+  for (auto& kv : w->sub) cudaGraphExecDestroy(kv.second.first);
   arena_free(h, w->arena);
   delete w;
 }
@@ -157,7 +156,9 @@ static mcmg_status enqueue_levels(mcmg_handle_s* h, VWork* w, int nrhs, cudaStre
   return MCMG_OK;
 }
 
-static mcmg_status capture_levels(mcmg_handle_s* h, VWork* w) {
+// Capture the level sequence for `count` fields of workspace w as a graph.
+static mcmg_status capture_levels_n(mcmg_handle_s* h, VWork* w, int count, cudaGraphExec_t* exec,
+                                    unsigned long long* kernels) {
   cudaStream_t cs;
   MCMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
@@ -168,9 +169,9 @@ static mcmg_status capture_levels(mcmg_handle_s* h, VWork* w) {
     return cuda_fail(e, "cudaStreamBeginCapture");
   }
   const unsigned long long before = g_launches.load();
-  mcmg_status s = enqueue_levels(h, w, w->nrhs, cs, &e1);
-  w->graph_kernels = g_launches.load() - before;
-  g_launches.fetch_sub(w->graph_kernels);   // counted when the graph runs
+  mcmg_status s = enqueue_levels(h, w, count, cs, &e1);
+  *kernels = g_launches.load() - before;
+  g_launches.fetch_sub(*kernels);   // counted when the graph runs
   e = cudaStreamEndCapture(cs, &graph);
   cudaStreamDestroy(cs);
   if (s != MCMG_OK) {
@@ -178,10 +179,45 @@ static mcmg_status capture_levels(mcmg_handle_s* h, VWork* w) {
     return s;
   }
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&w->graph, graph, 0);
+  e = cudaGraphInstantiate(exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   w->e1 = e1;
+  return MCMG_OK;
+}
+
+static mcmg_status capture_levels(mcmg_handle_s* h, VWork* w) {
+  return capture_levels_n(h, w, w->nrhs, &w->graph, &w->graph_kernels);
+}
+
+mcmg_status vcycle_run_batch(mcmg_handle_s* h, VWork* w, const float2* const* srcs,
+                             float2* const* dsts, int count, cudaStream_t st) {
+  if (count < 1 || count > w->nrhs) {
+    set_error("batch of %d fields in a workspace of %d", count, w->nrhs);
+    return MCMG_ERR_ARG;
+  }
+  const Level& l0 = h->lv[0];
+  MCMG_TRY(launch_lift_gather(srcs, h->lift, w->r[0], l0.C, l0.g.nodes(), count, st));
+  cudaGraphExec_t exec;
+  unsigned long long kernels;
+  if (count == w->nrhs) {
+    if (!w->graph) MCMG_TRY(capture_levels(h, w));
+    exec = w->graph;
+    kernels = w->graph_kernels;
+  } else {
+    auto it = w->sub.find(count);
+    if (it == w->sub.end()) {
+      cudaGraphExec_t ex;
+      unsigned long long kn;
+      MCMG_TRY(capture_levels_n(h, w, count, &ex, &kn));
+      it = w->sub.emplace(count, std::make_pair(ex, kn)).first;
+    }
+    exec = it->second.first;
+    kernels = it->second.second;
+  }
+  MCMG_CUDA(cudaGraphLaunch(exec, st));
+  count_launch(kernels);
+  MCMG_TRY(launch_project_scatter(w->e1, h->proj, dsts, l0.C, l0.g.nodes(), count, st));
   return MCMG_OK;
 }
 
@@ -523,6 +559,7 @@ mcmg_status mcmg_destroy(mcmg_handle h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->kry) krylov_destroy(h, h->kry);
+  if (h->blk) block_destroy(h, h->blk);
   if (h->work) vwork_destroy(h, h->work);
   arena_free(h, h->arena);
   if (h->stream) cudaStreamDestroy(h->stream);
@@ -564,35 +601,51 @@ mcmg_status mcmg_solve(mcmg_handle h, const void* f, void* u, const mcmg_solve_o
   std::lock_guard<std::mutex> lk(h->mu);
   MCMG_CUDA(cudaSetDevice(h->device));
   const int m_need = (o->flags & MCMG_SOLVE_STATIONARY) ? 1 : o->restart_m;
-  if (h->kry && krylov_m(h->kry) != m_need) {
-    krylov_destroy(h, h->kry);
-    h->kry = nullptr;
+  const bool batched = o->nrhs > 1 && !(o->flags & MCMG_SOLVE_STATIONARY);
+  if (!batched) {
+    if (h->kry && krylov_m(h->kry) != m_need) {
+      krylov_destroy(h, h->kry);
+      h->kry = nullptr;
+    }
+    if (!h->kry) MCMG_TRY(krylov_create(h, m_need, &h->kry));
   }
-  if (!h->kry) MCMG_TRY(krylov_create(h, m_need, &h->kry));
   const long long N = h->g0.nodes();
   mcmg_solve_info agg{};
   agg.converged = 1;
   mcmg_status worst = MCMG_OK;
   auto t0 = std::chrono::steady_clock::now();
-  for (int k = 0; k < o->nrhs; ++k) {
-    cudaStream_t st = o->stream ? (cudaStream_t)o->stream : h->stream;
-    mcmg_solve_info one;
-    mcmg_status fs;
-    if (o->flags & MCMG_SOLVE_STATIONARY) {
-      MCMG_TRY(stationary_run(h->kry, (const double2*)f + (size_t)k * N,
-                              (double2*)u + (size_t)k * N, *o, st, &one, &fs));
-    } else {
-      MCMG_TRY(krylov_begin(h->kry, (const double2*)f + (size_t)k * N,
-                            (double2*)u + (size_t)k * N, *o, st));
-      int done = 0;
-      while (!done) MCMG_TRY(krylov_advance(h->kry, true, &done));
-      krylov_info(h->kry, &one, &fs);
+  if (batched) {
+    // all right-hand sides together: V-cycles batched per round
+    if (h->blk && (block_m(h->blk) != o->restart_m || block_size(h->blk) != o->nrhs)) {
+      block_destroy(h, h->blk);
+      h->blk = nullptr;
     }
-    agg.iters = std::max(agg.iters, one.iters);
-    agg.restarts = std::max(agg.restarts, one.restarts);
-    agg.rel_residual = std::max(agg.rel_residual, one.rel_residual);
-    agg.converged &= one.converged;
-    if (fs != MCMG_OK && worst == MCMG_OK) worst = fs;
+    if (!h->blk) MCMG_TRY(block_create(h, o->restart_m, o->nrhs, &h->blk));
+    MCMG_TRY(block_begin(h->blk, (const double2*)f, (double2*)u, *o));
+    int done = 0;
+    while (!done) MCMG_TRY(block_advance(h->blk, true, &done));
+    block_info(h->blk, &agg, &worst);
+  } else {
+    for (int k = 0; k < o->nrhs; ++k) {
+      cudaStream_t st = o->stream ? (cudaStream_t)o->stream : h->stream;
+      mcmg_solve_info one;
+      mcmg_status fs;
+      if (o->flags & MCMG_SOLVE_STATIONARY) {
+        MCMG_TRY(stationary_run(h->kry, (const double2*)f + (size_t)k * N,
+                                (double2*)u + (size_t)k * N, *o, st, &one, &fs));
+      } else {
+        MCMG_TRY(krylov_begin(h->kry, (const double2*)f + (size_t)k * N,
+                              (double2*)u + (size_t)k * N, *o, st));
+        int done = 0;
+        while (!done) MCMG_TRY(krylov_advance(h->kry, true, &done));
+        krylov_info(h->kry, &one, &fs);
+      }
+      agg.iters = std::max(agg.iters, one.iters);
+      agg.restarts = std::max(agg.restarts, one.restarts);
+      agg.rel_residual = std::max(agg.rel_residual, one.rel_residual);
+      agg.converged &= one.converged;
+      if (fs != MCMG_OK && worst == MCMG_OK) worst = fs;
+    }
   }
   agg.t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = agg;
@@ -713,10 +766,12 @@ mcmg_status mcmg_cgs2(mcmg_handle h, const void* V, int k, size_t n, void* w, do
 
 // ------------------------------------------------------------------ server --
 // One worker thread.  Admission: queued requests start in arrival order when
-// their Krylov and V-cycle workspaces fit the context's HBM budget.  Every
-// right-hand side of every admitted request runs on its own stream; the worker
-// polls each solve's last event and enqueues its next FGMRES stage as soon as
-// it completes, so the stages of different solves overlap on the device.
+// their Krylov and V-cycle workspaces fit the context's HBM budget.  Each
+// admitted request runs as one block solve on its own stream: per round, the
+// V-cycles of all its right-hand sides that need one run as a single batched
+// launch per level.  The worker polls every request's last event and enqueues
+// its next round as soon as it completes, so different requests overlap on the
+// device.
 
 static size_t request_bytes(mcmg_handle_s* h, const mcmg_solve_opts& o) {
   const size_t n = (size_t)h->g0.nodes();
@@ -728,10 +783,10 @@ static size_t request_bytes(mcmg_handle_s* h, const mcmg_solve_opts& o) {
 }
 
 static void release(Request* r) {
-  for (auto* k : r->kry) krylov_destroy(r->h, k);
-  r->kry.clear();
-  r->done.clear();
-  if (r->st) { cudaStreamDestroy(r->st); r->st = nullptr; }
+  if (r->blk) {
+    block_destroy(r->h, r->blk);
+    r->blk = nullptr;
+  }
 }
 
 static bool try_admit(mcmg_ctx_s* c, Request* r) {
@@ -741,27 +796,17 @@ static bool try_admit(mcmg_ctx_s* c, Request* r) {
     r->err = mcmg_last_error();
     return false;
   }
-  if (cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking) != cudaSuccess) {
+  mcmg_status s = block_create(r->h, r->o.restart_m, r->o.nrhs, &r->blk);
+  if (s != MCMG_OK) {
+    r->err = mcmg_last_error();
+    release(r);
     cudaGetLastError();
     return false;
   }
-  const size_t N = (size_t)r->h->g0.nodes();
-  for (int k = 0; k < r->o.nrhs; ++k) {
-    Krylov* kr = nullptr;
-    mcmg_status s = krylov_create(r->h, r->o.restart_m, &kr);
-    if (s != MCMG_OK) {
-      r->err = mcmg_last_error();
-      release(r);
-      cudaGetLastError();
-      return false;
-    }
-    r->kry.push_back(kr);
-    r->done.push_back(0);
-    s = krylov_begin(kr, r->f + k * N, r->u + k * N, r->o, krylov_stream(kr));
-    if (s != MCMG_OK) {
-      r->status = s;
-      return true;
-    }
+  s = block_begin(r->blk, r->f, r->u, r->o);
+  if (s != MCMG_OK) {
+    r->status = s;
+    r->err = mcmg_last_error();
   }
   return true;
 }
@@ -796,33 +841,21 @@ static void server_loop(mcmg_ctx_s* c) {
     for (Request* r : c->active) {
       bool all = r->status != MCMG_PENDING;
       if (!all) {
-        all = true;
-        for (size_t k = 0; k < r->kry.size(); ++k) {
-          if (r->done[k]) continue;
-          int d = 0;
-          mcmg_status s = krylov_advance(r->kry[k], false, &d);
-          if (s != MCMG_OK) { r->status = s; r->err = mcmg_last_error(); d = 1; }
-          if (d) { r->done[k] = 1; progressed = true; }
-          else all = false;
-        }
+        int d = 0;
+        mcmg_status s = block_advance(r->blk, false, &d);
+        if (s != MCMG_OK) { r->status = s; r->err = mcmg_last_error(); d = 1; }
+        if (d) { all = true; progressed = true; }
       }
       if (all) fin.push_back(r);
     }
     for (Request* r : fin) {
       mcmg_solve_info agg{};
-      agg.converged = 1;
       mcmg_status worst = r->status == MCMG_PENDING ? MCMG_OK : r->status;
-      for (auto* k : r->kry) {
-        mcmg_solve_info one;
+      if (r->blk) {
         mcmg_status fs;
-        krylov_info(k, &one, &fs);
-        agg.iters = std::max(agg.iters, one.iters);
-        agg.restarts = std::max(agg.restarts, one.restarts);
-        agg.rel_residual = std::max(agg.rel_residual, one.rel_residual);
-        agg.converged &= one.converged;
+        block_info(r->blk, &agg, &fs);
         if (fs != MCMG_OK && worst == MCMG_OK) worst = fs;
       }
-      if (r->st) cudaStreamSynchronize(r->st);
       agg.t_solve_s =
           std::chrono::duration<double>(std::chrono::steady_clock::now() - r->t_submit).count();
       r->info = agg;

@@ -698,6 +698,41 @@ __global__ void k_project(const float2* __restrict__ e1, const float2* __restric
   e[off + n] = acc;
 }
 
+// Batched forms: field k of the batch reads srcs[k] / writes dsts[k].
+__global__ void k_lift_gather(const float2* const* __restrict__ srcs, const float2* __restrict__ lift,
+                              float2* __restrict__ r1, int C, long long N) {
+  long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= N * C) return;
+  const float2* r = srcs[blockIdx.y];
+  r1[(size_t)blockIdx.y * N * C + id] = cmul(lift[id % C], r[id / C]);
+}
+
+__global__ void k_project_scatter(const float2* __restrict__ e1, const float2* __restrict__ proj,
+                                  float2* const* __restrict__ dsts, int C, long long N) {
+  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const float2* src = e1 + ((size_t)blockIdx.y * N + n) * C;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int c = 0; c < C; ++c) cfma(acc, proj[c], src[c]);
+  dsts[blockIdx.y][n] = acc;
+}
+
+mcmg_status launch_lift_gather(const float2* const* srcs, const float2* lift, float2* r1, int C,
+                               long long nodes, int count, cudaStream_t st) {
+  dim3 grid((unsigned)((nodes * C + 255) / 256), (unsigned)count);
+  k_lift_gather<<<grid, 256, 0, st>>>(srcs, lift, r1, C, nodes);
+  MCMG_CHECK_LAUNCH("lift_gather");
+  return MCMG_OK;
+}
+
+mcmg_status launch_project_scatter(const float2* e1, const float2* proj, float2* const* dsts, int C,
+                                   long long nodes, int count, cudaStream_t st) {
+  dim3 grid((unsigned)((nodes + 255) / 256), (unsigned)count);
+  k_project_scatter<<<grid, 256, 0, st>>>(e1, proj, dsts, C, nodes);
+  MCMG_CHECK_LAUNCH("project_scatter");
+  return MCMG_OK;
+}
+
 mcmg_status launch_lift(const float2* r, const float2* lift, float2* r1, int C, long long nodes,
                         int nrhs, cudaStream_t st) {
   dim3 grid((unsigned)((nodes * C + 255) / 256), (unsigned)nrhs);

@@ -330,7 +330,7 @@ struct Krylov {
   const double2* f = nullptr;
   double2* u = nullptr;
   mcmg_solve_opts o{};
-  enum Phase { IDLE, WAIT_RES, WAIT_STEP, DONE } phase = IDLE;
+  enum Phase { IDLE, WAIT_RES, WAIT_STEP, NEED_STEP, DONE } phase = IDLE;
   int j = 0, iters = 0, restarts = 0, max_iters = 0;
   double fnorm = 0.0, rel = 0.0;
   bool converged = false;
@@ -347,7 +347,7 @@ static int red_blocks(long long n) {
   return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
-mcmg_status krylov_create(mcmg_handle_s* h, int m, Krylov** out) {
+mcmg_status krylov_create(mcmg_handle_s* h, int m, Krylov** out, bool own_vcycle_work) {
   Krylov* k = new Krylov();
   k->h = h;
   k->m = m;
@@ -373,7 +373,7 @@ mcmg_status krylov_create(mcmg_handle_s* h, int m, Krylov** out) {
     krylov_destroy(h, k);
     return s;
   }
-  if ((s = vwork_create(h, 1, &k->vw)) != MCMG_OK) {
+  if (own_vcycle_work && (s = vwork_create(h, 1, &k->vw)) != MCMG_OK) {
     krylov_destroy(h, k);
     return s;
   }
@@ -420,14 +420,13 @@ static mcmg_status multidot(Krylov* k, int nv, bool self, double2* out) {
   return MCMG_OK;
 }
 
-// One Arnoldi step j: z_j = MG(v_j), w = A z_j, CGS2, Givens; event.
-static mcmg_status enqueue_step(Krylov* k) {
+// The Arnoldi part of step j once z_j = MG(v_j) is in Z: w = A z_j, CGS2,
+// Givens, v_{j+1}.  No event.
+static mcmg_status enqueue_arnoldi(Krylov* k) {
   mcmg_handle_s* h = k->h;
   const long long n = k->n;
   const int j = k->j;
-  float2* vj = k->V + (size_t)j * n;
   float2* zj = k->Z + (size_t)j * n;
-  MCMG_TRY(vcycle_run(h, k->vw, vj, zj, 1, k->st));
   MCMG_TRY(launch_apply_A_mixed(h->q64, zj, k->w, h->g0, 1, k->st));
   MCMG_TRY(multidot(k, j + 1, true, k->d1));
   k_update<double2><<<k->nblk, RED_T, 0, k->st>>>(k->V, n, j + 1, k->d1, k->w, n, k->part);
@@ -444,8 +443,16 @@ static mcmg_status enqueue_step(Krylov* k) {
     k_scale<<<(unsigned)((n + 255) / 256), 256, 0, k->st>>>(k->w, k->dsc, k->V + (size_t)(j + 1) * n, n);
     MCMG_CHECK_LAUNCH("scale");
   }
-  MCMG_CUDA(cudaEventRecord(k->ev, k->st));
   k->phase = Krylov::WAIT_STEP;
+  return MCMG_OK;
+}
+
+// One Arnoldi step j: z_j = MG(v_j), then the Arnoldi part; event.
+static mcmg_status enqueue_step(Krylov* k) {
+  const long long n = k->n;
+  MCMG_TRY(vcycle_run(k->h, k->vw, k->V + (size_t)k->j * n, k->Z + (size_t)k->j * n, 1, k->st));
+  MCMG_TRY(enqueue_arnoldi(k));
+  MCMG_CUDA(cudaEventRecord(k->ev, k->st));
   return MCMG_OK;
 }
 
@@ -603,6 +610,184 @@ mcmg_status stationary_run(Krylov* k, const double2* f, double2* u, const mcmg_s
   }
   *final_status = fs;
   return MCMG_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Block of right-hand sides of one medium.
+// ---------------------------------------------------------------------------
+struct KrylovBlock {
+  mcmg_handle_s* h = nullptr;
+  int nb = 0, m = 0;
+  std::vector<Krylov*> ks;
+  VWork* vw = nullptr;              // nb fields
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  float2** ptr_h = nullptr;          // pinned: [0, nb) sources, [nb, 2nb) destinations
+  float2** ptr_d = nullptr;
+  DevArena arena;
+  std::chrono::steady_clock::time_point t0;
+  double t_solve = 0.0;
+};
+
+int block_size(const KrylovBlock* b) { return b->nb; }
+int block_m(const KrylovBlock* b) { return b->m; }
+
+mcmg_status block_create(mcmg_handle_s* h, int m, int nb, KrylovBlock** out) {
+  KrylovBlock* b = new KrylovBlock();
+  b->h = h;
+  b->nb = nb;
+  b->m = m;
+  mcmg_status s = MCMG_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&b->ptr_h, sizeof(float2*) * 2 * nb, cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    block_destroy(h, b);
+    return cuda_fail(e, "block_create");
+  }
+  if ((s = dev_alloc(h, b->arena, (void**)&b->ptr_d, sizeof(float2*) * 2 * nb)) ||
+      (s = vwork_create(h, nb, &b->vw))) {
+    block_destroy(h, b);
+    return s;
+  }
+  for (int k = 0; k < nb; ++k) {
+    Krylov* kr = nullptr;
+    if ((s = krylov_create(h, m, &kr, false)) != MCMG_OK) {
+      block_destroy(h, b);
+      return s;
+    }
+    b->ks.push_back(kr);
+  }
+  *out = b;
+  return MCMG_OK;
+}
+
+void block_destroy(mcmg_handle_s* h, KrylovBlock* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  for (Krylov* k : b->ks) krylov_destroy(h, k);
+  if (b->vw) vwork_destroy(h, b->vw);
+  arena_free(h, b->arena);
+  if (b->ptr_h) cudaFreeHost(b->ptr_h);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->st) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+mcmg_status block_begin(KrylovBlock* b, const double2* f, double2* u, const mcmg_solve_opts& o) {
+  const size_t N = (size_t)b->h->g0.nodes();
+  b->t0 = std::chrono::steady_clock::now();
+  for (int k = 0; k < b->nb; ++k)
+    MCMG_TRY(krylov_begin(b->ks[k], f + k * N, u + k * N, o, b->st));
+  MCMG_CUDA(cudaEventRecord(b->ev, b->st));
+  return MCMG_OK;
+}
+
+// Read one member's results of the last round and decide its next stage.
+static mcmg_status member_process(Krylov* k) {
+  Stat st;
+  std::memcpy(&st, (const void*)k->stat_h, sizeof(Stat));
+  if (k->h->err_host && *(volatile int*)k->h->err_host) {
+    set_error("a bounded wait in a tensor-core kernel ran out (code %d)", *k->h->err_host);
+    finish(k, false, MCMG_ERR_TIMEOUT);
+    return MCMG_OK;
+  }
+  if (k->phase == Krylov::WAIT_RES) {
+    if (k->fnorm < 0.0) k->fnorm = std::sqrt(st.ff);
+    const double beta = std::sqrt(st.rr);
+    if (!std::isfinite(beta)) {
+      k->rel = beta;
+      finish(k, false, MCMG_ERR_NUMERIC);
+      return MCMG_OK;
+    }
+    k->rel = k->fnorm > 0.0 ? beta / k->fnorm : 0.0;
+    if (k->fnorm == 0.0 || k->rel <= k->o.tol) {
+      finish(k, true, MCMG_OK);
+      return MCMG_OK;
+    }
+    if (k->iters >= k->max_iters) {
+      finish(k, false, MCMG_ERR_NOT_CONVERGED);
+      return MCMG_OK;
+    }
+    const long long cover = std::max<long long>(k->n, k->m + 1);
+    k_start_cycle<<<(unsigned)((cover + 255) / 256), 256, 0, k->st>>>(k->r64, k->dsc, k->V, k->n,
+                                                                        k->g, k->m);
+    MCMG_CHECK_LAUNCH("start_cycle");
+    k->j = 0;
+    k->phase = Krylov::NEED_STEP;
+    return MCMG_OK;
+  }
+  if (k->phase == Krylov::WAIT_STEP) {
+    k->iters += 1;
+    const double est = st.res / k->fnorm;
+    if (!std::isfinite(est)) {
+      finish(k, false, MCMG_ERR_NUMERIC);
+      return MCMG_OK;
+    }
+    const bool stop = est <= k->o.tol || st.hn <= 1e-14 * st.w0 || k->j + 1 >= k->m ||
+                      k->iters >= k->max_iters;
+    if (stop) return enqueue_finish_cycle(k, k->j + 1);   // -> WAIT_RES
+    k->j += 1;
+    k->phase = Krylov::NEED_STEP;
+  }
+  return MCMG_OK;
+}
+
+mcmg_status block_advance(KrylovBlock* b, bool blocking, int* done) {
+  *done = 0;
+  if (blocking) {
+    MCMG_CUDA(cudaEventSynchronize(b->ev));
+  } else {
+    cudaError_t e = cudaEventQuery(b->ev);
+    if (e == cudaErrorNotReady) return MCMG_OK;
+    if (e != cudaSuccess) return cuda_fail(e, "block event");
+  }
+  for (Krylov* k : b->ks)
+    if (k->phase == Krylov::WAIT_RES || k->phase == Krylov::WAIT_STEP) MCMG_TRY(member_process(k));
+  // batch the V-cycles of every member that needs one
+  int count = 0;
+  for (Krylov* k : b->ks)
+    if (k->phase == Krylov::NEED_STEP) {
+      b->ptr_h[count] = k->V + (size_t)k->j * k->n;
+      b->ptr_h[b->nb + count] = k->Z + (size_t)k->j * k->n;
+      ++count;
+    }
+  if (count > 0) {
+    MCMG_CUDA(cudaMemcpyAsync(b->ptr_d, b->ptr_h, sizeof(float2*) * count, cudaMemcpyHostToDevice,
+                              b->st));
+    MCMG_CUDA(cudaMemcpyAsync(b->ptr_d + b->nb, b->ptr_h + b->nb, sizeof(float2*) * count,
+                              cudaMemcpyHostToDevice, b->st));
+    MCMG_TRY(vcycle_run_batch(b->h, b->vw, b->ptr_d, b->ptr_d + b->nb, count, b->st));
+    for (Krylov* k : b->ks)
+      if (k->phase == Krylov::NEED_STEP) MCMG_TRY(enqueue_arnoldi(k));
+  }
+  bool all = true;
+  for (Krylov* k : b->ks) all = all && k->phase == Krylov::DONE;
+  if (all) {
+    MCMG_CUDA(cudaStreamSynchronize(b->st));
+    b->t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - b->t0).count();
+    *done = 1;
+    return MCMG_OK;
+  }
+  MCMG_CUDA(cudaEventRecord(b->ev, b->st));
+  return MCMG_OK;
+}
+
+void block_info(const KrylovBlock* b, mcmg_solve_info* info, mcmg_status* final_status) {
+  mcmg_solve_info agg{};
+  agg.converged = 1;
+  mcmg_status worst = MCMG_OK;
+  for (const Krylov* k : b->ks) {
+    agg.iters = std::max(agg.iters, k->iters);
+    agg.restarts = std::max(agg.restarts, k->restarts);
+    agg.rel_residual = std::max(agg.rel_residual, k->rel);
+    agg.converged &= k->converged ? 1 : 0;
+    if (k->final != MCMG_OK && worst == MCMG_OK) worst = k->final;
+  }
+  agg.t_solve_s = b->t_solve;
+  if (info) *info = agg;
+  if (final_status) *final_status = worst;
 }
 
 mcmg_status cgs2_once(mcmg_handle_s* h, const float2* V, int kv, long long n, float2* w,

@@ -119,6 +119,10 @@ mcmg_status launch_lift(const float2* r, const float2* lift, float2* r1, int C, 
                         int nrhs, cudaStream_t st);
 mcmg_status launch_project(const float2* e1, const float2* proj, float2* e, int C,
                            long long nodes, int nrhs, cudaStream_t st);
+mcmg_status launch_lift_gather(const float2* const* srcs, const float2* lift, float2* r1, int C,
+                               long long nodes, int count, cudaStream_t st);
+mcmg_status launch_project_scatter(const float2* e1, const float2* proj, float2* const* dsts, int C,
+                                   long long nodes, int count, cudaStream_t st);
 
 // helmholtz (kernels_helm.cu)
 mcmg_status launch_make_q(const double* c_dev, double omega, int width, double gamma_max,
@@ -162,9 +166,11 @@ struct VWork {
   float2* e[MCMG_MAX_LEVELS] = {};
   float2* e2[MCMG_MAX_LEVELS] = {};
   float2* t[MCMG_MAX_LEVELS] = {};
-  cudaGraphExec_t graph = nullptr;   // the level sequence, captured once
+  cudaGraphExec_t graph = nullptr;   // the level sequence for nrhs fields, captured once
   float2* e1 = nullptr;              // buffer holding e_1 after the graph
   unsigned long long graph_kernels = 0;  // kernel nodes in the graph
+  // graphs of the level sequence for fewer fields (batched solves), by count
+  std::map<int, std::pair<cudaGraphExec_t, unsigned long long>> sub;
   DevArena arena;
 };
 
@@ -173,10 +179,14 @@ void vwork_destroy(mcmg_handle_s* h, VWork* w);
 // e = MG(r) on stream st using workspace w.
 mcmg_status vcycle_run(mcmg_handle_s* h, VWork* w, const float2* r, float2* e, int nrhs,
                        cudaStream_t st);
+// Batched V-cycle over `count` <= w->nrhs fields: field k reads srcs[k] and
+// writes dsts[k] (device arrays of device pointers).
+mcmg_status vcycle_run_batch(mcmg_handle_s* h, VWork* w, const float2* const* srcs,
+                             float2* const* dsts, int count, cudaStream_t st);
 
 // Resumable FGMRES(m) for one right-hand side (krylov.cu).
 struct Krylov;
-mcmg_status krylov_create(mcmg_handle_s* h, int m, Krylov** out);
+mcmg_status krylov_create(mcmg_handle_s* h, int m, Krylov** out, bool own_vcycle_work = true);
 void krylov_destroy(mcmg_handle_s* h, Krylov* k);
 // Start a solve of A u = f (device c128).  Enqueues work on st.
 mcmg_status krylov_begin(Krylov* k, const double2* f, double2* u, const mcmg_solve_opts& o,
@@ -191,6 +201,18 @@ int krylov_m(const Krylov* k);
 mcmg_status stationary_run(Krylov* k, const double2* f, double2* u, const mcmg_solve_opts& o,
                            cudaStream_t st, mcmg_solve_info* info, mcmg_status* final_status);
 cudaStream_t krylov_stream(const Krylov* k);   // the solve's private stream
+// FGMRES(m) for several right-hand sides of one medium: every round batches
+// the V-cycles of all members that need one into a single launch per level;
+// Arnoldi, restarts and convergence stay per member.
+struct KrylovBlock;
+mcmg_status block_create(mcmg_handle_s* h, int m, int nb, KrylovBlock** out);
+void block_destroy(mcmg_handle_s* h, KrylovBlock* b);
+mcmg_status block_begin(KrylovBlock* b, const double2* f, double2* u, const mcmg_solve_opts& o);
+// As krylov_advance, for the whole block (one round per call).
+mcmg_status block_advance(KrylovBlock* b, bool blocking, int* done);
+void block_info(const KrylovBlock* b, mcmg_solve_info* info, mcmg_status* final_status);
+int block_size(const KrylovBlock* b);
+int block_m(const KrylovBlock* b);
 // CGS2 on caller buffers (used by mcmg_cgs2).
 mcmg_status cgs2_once(mcmg_handle_s* h, const float2* V, int k, long long n, float2* w,
                       double* h_host, double* norm_host, cudaStream_t st);
@@ -215,7 +237,8 @@ struct mcmg_handle_s {
   mcmg::Level lv[MCMG_MAX_LEVELS];
   mcmg::DevArena arena;         // features, weights
   mcmg::VWork* work = nullptr;  // for mcmg_vcycle / mcmg_solve
-  mcmg::Krylov* kry = nullptr;  // for mcmg_solve
+  mcmg::Krylov* kry = nullptr;  // for mcmg_solve, one right-hand side
+  mcmg::KrylovBlock* blk = nullptr;  // for mcmg_solve, several right-hand sides
   cudaStream_t stream = nullptr;
   std::mutex mu;                // serialises synchronous use of work / kry
   int* err_host = nullptr;      // error word, mapped pinned (bounded waits that ran out)
