@@ -553,65 +553,77 @@ __global__ void __launch_bounds__(256) k_restrict(TransferParams p) {
     if (nn[k] < NC) rc[nn[k] * CO + co] = acc[k];
 }
 
-// Prolongation-add: e[p][co] += sum over (J, o) with 2J + o = p of
-// sum_ci P[o][co][ci] ec[J][ci]  (transposed strided convolution).  Per axis
-// an even fine index has one source (J = p/2, o = 0) and an odd one two
-// (J = (p-1)/2, o = +1 and J = (p+1)/2, o = -1), so each node visits the 2^d
-// combinations of its candidates rather than all 3^d taps.
+// Prolongation-add, coarse-node form: the transposed strided convolution
+// x[2J + o] += P[o] e_c[J] is regrouped by coarse node.  For tap o, write
+// b_a = (o_a != 0) and c_a = (o_a == -1) per axis; then fine node 2J + b(o)
+// receives P[o] e_c[J + c(o)].  A thread owning coarse node J therefore
+// computes its 2^d fine nodes 2J + {0,1}^d (the grid is even, so all exist)
+// with every tap used exactly once and no divergent control flow; e_c outside
+// the coarse grid is zero.
 template <int CO, int D, int TN>
 __global__ void __launch_bounds__(256) k_prolong_add(TransferParams p) {
   using T = Tile<CO, TN, 1>;
+  constexpr int NB2 = D == 3 ? 8 : 4;
+  constexpr int T3 = D == 3 ? 27 : 9;
   const int co = threadIdx.x % CO;
   const int g = threadIdx.x / CO;
-  const long long NF = p.dst_nodes;
-  const float2* __restrict__ ec = p.src + (size_t)blockIdx.y * p.src_nodes * p.cin;
-  float2* __restrict__ e = p.dst + (size_t)blockIdx.y * NF * CO;
+  const long long NC = p.src_nodes;
+  const float2* __restrict__ ec = p.src + (size_t)blockIdx.y * NC * p.cin;
+  float2* __restrict__ e = p.dst + (size_t)blockIdx.y * p.dst_nodes * CO;
   const long long n0 = (long long)blockIdx.x * T::NB;
-  long long nn[T::TN];
-  int px[T::TN], py[T::TN], pz[T::TN];
-  float2 acc[T::TN];
+  long long nn[TN];
+  int jx[TN], jy[TN], jz[TN];
+  float2 acc[TN][NB2];
 #pragma unroll
-  for (int k = 0; k < T::TN; ++k) {
+  for (int k = 0; k < TN; ++k) {
     nn[k] = n0 + g + (long long)T::G * k;
-    long long c = nn[k] < NF ? nn[k] : NF - 1;
-    node_xyz(c, p.fx, p.fy, px[k], py[k], pz[k]);
-    acc[k] = make_float2(0.f, 0.f);
-  }
-  constexpr int NCOMB = D == 3 ? 8 : 4;
-  for (int cb = 0; cb < NCOMB; ++cb) {
-    const int bx = cb & 1, by = (cb >> 1) & 1, bz = (cb >> 2) & 1;
+    const long long c = nn[k] < NC ? nn[k] : NC - 1;
+    node_xyz(c, p.cx, p.cy, jx[k], jy[k], jz[k]);
 #pragma unroll
-    for (int k = 0; k < T::TN; ++k) {
-      // candidate along each axis: b = 0 -> o = 0 (even) or o = +1 (odd);
-      // b = 1 -> o = -1 (odd only)
-      int oxs = (px[k] & 1) ? (bx ? -1 : 1) : 0;
-      int oys = (py[k] & 1) ? (by ? -1 : 1) : 0;
-      int ozs = D == 3 ? ((pz[k] & 1) ? (bz ? -1 : 1) : 0) : 0;
-      bool valid = !((bx && !(px[k] & 1)) || (by && !(py[k] & 1)) || (D == 3 && bz && !(pz[k] & 1)));
-      int X = (px[k] - oxs) >> 1, Y = (py[k] - oys) >> 1, Z = D == 3 ? (pz[k] - ozs) >> 1 : 0;
-      valid = valid && X >= 0 && X < p.cx && Y >= 0 && Y < p.cy && Z >= 0 && Z < p.cz;
-      if (__syncthreads_or(valid) == 0) continue;
-      const int o = D == 3 ? ((ozs + 1) * 3 + (oys + 1)) * 3 + (oxs + 1) : (oys + 1) * 3 + (oxs + 1);
-      const float2* w = p.Wt + (size_t)o * p.cin * CO;
-      const float2* src = ec + (valid ? (((long long)Z * p.cy + Y) * p.cx + X) * p.cin : 0);
-      float2 a = make_float2(0.f, 0.f);
-      for (int ci = 0; ci < p.cin; ++ci) {
-        const float2 wv = __ldg(w + ci * CO + co);
-        const float2 v = __ldg(src + ci);
-        cfma(a, wv, v);
+    for (int b = 0; b < NB2; ++b) acc[k][b] = make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int o = 0; o < T3; ++o) {
+    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = D == 3 ? o / 9 - 1 : 0;
+    const int b = (ox != 0) | ((oy != 0) << 1) | ((oz != 0) << 2);
+    const int cx = ox == -1, cy = oy == -1, cz = oz == -1;
+    long long src[TN];
+    bool ok[TN];
+#pragma unroll
+    for (int k = 0; k < TN; ++k) {
+      const int X = jx[k] + cx, Y = jy[k] + cy, Z = jz[k] + cz;
+      ok[k] = X < p.cx && Y < p.cy && (D == 3 ? Z < p.cz : true);
+      src[k] = ok[k] ? (((long long)Z * p.cy + Y) * p.cx + X) * p.cin : 0;
+    }
+    const float2* w = p.Wt + (size_t)o * p.cin * CO;
+    for (int ci = 0; ci < p.cin; ++ci) {
+      const float2 wv = __ldg(w + ci * CO + co);
+#pragma unroll
+      for (int k = 0; k < TN; ++k) {
+        const float2 v = __ldg(ec + src[k] + ci);
+        if (ok[k]) cfma(acc[k][b], wv, v);
       }
-      if (valid) acc[k] = cadd(acc[k], a);
     }
   }
 #pragma unroll
-  for (int k = 0; k < T::TN; ++k)
-    if (nn[k] < NF) e[nn[k] * CO + co] = cadd(e[nn[k] * CO + co], acc[k]);
+  for (int k = 0; k < TN; ++k) {
+    if (nn[k] >= NC) continue;
+#pragma unroll
+    for (int b = 0; b < NB2; ++b) {
+      const long long fx = 2 * jx[k] + (b & 1), fy = 2 * jy[k] + ((b >> 1) & 1),
+                      fz = D == 3 ? 2 * jz[k] + ((b >> 2) & 1) : 0;
+      const long long fi = ((fz * p.fy + fy) * p.fx + fx) * CO + co;
+      e[fi] = cadd(e[fi], acc[k][b]);
+    }
+  }
 }
 
 template <int CO, int D, int TN>
 static mcmg_status transfer_tn(const TransferParams& p, bool restrict_, int nrhs, cudaStream_t st) {
   using T = Tile<CO, TN, 1>;
-  dim3 grid((unsigned)((p.dst_nodes + T::NB - 1) / T::NB), (unsigned)nrhs);
+  // restriction: one thread per coarse output; prolongation: per coarse source
+  const long long units = restrict_ ? p.dst_nodes : p.src_nodes;
+  dim3 grid((unsigned)((units + T::NB - 1) / T::NB), (unsigned)nrhs);
   if (restrict_)
     k_restrict<CO, D, TN><<<grid, 256, 0, st>>>(p);
   else
@@ -622,7 +634,7 @@ static mcmg_status transfer_tn(const TransferParams& p, bool restrict_, int nrhs
 
 template <int CO, int D>
 static mcmg_status transfer_c(const TransferParams& p, bool restrict_, int nrhs, cudaStream_t st) {
-  switch (pick_tn(p.dst_nodes, CO, nrhs)) {
+  switch (pick_tn(restrict_ ? p.dst_nodes : p.src_nodes, CO, nrhs)) {
     case 8: return transfer_tn<CO, D, 8>(p, restrict_, nrhs, st);
     case 2: return transfer_tn<CO, D, 2>(p, restrict_, nrhs, st);
     default: return transfer_tn<CO, D, 1>(p, restrict_, nrhs, st);
