@@ -126,6 +126,13 @@ def setup_workload(name, n=0):
     return wl, c, omega, w
 
 
+def smooth_bytes(C, first):
+    """Algorithmic bytes per node of one smoothing launch (complex64): read e,
+    r, a, s and write e (40 C); the first pre-step (e = 0) reads r, s, writes e
+    (24 C)."""
+    return (24 if first else 40) * C
+
+
 def smooth_flops(C, d, first):
     """Algorithmic real flops per node of one smoothing launch: complex MACs
     (8 flops each) of the stencil, K_A, K_S and W^(i); the first pre-step
@@ -137,7 +144,7 @@ def time_smoothing(h, wl, torch, stream, reps=20):
     """CUDA-event time of every smoothing launch class of one V-cycle, through
     the C ABI on `stream`.  Returns (total flops, total seconds, launches, detail)."""
     d = wl["dim"]
-    total_f, total_t, launches = 0.0, 0.0, 0
+    total_f, total_b, total_t, launches = 0.0, 0.0, 0.0, 0
     detail = []
     for l in range(wl["levels"]):
         C = wl["channels"][l]
@@ -163,12 +170,14 @@ def time_smoothing(h, wl, torch, stream, reps=20):
             e1.synchronize()
             per = e0.elapsed_time(e1) / 1e3 / reps
             fl = smooth_flops(C, d, first) * nodes
+            by = smooth_bytes(C, first) * nodes
             total_f += fl * count
+            total_b += by * count
             total_t += per * count
             launches += count
             detail.append(dict(level=l, C=C, first=first, count=count, us=per * 1e6,
-                               tflops=fl / per / 1e12))
-    return total_f, total_t, launches, detail
+                               tflops=fl / per / 1e12, gbs=by / per / 1e9))
+    return total_f, total_b, total_t, launches, detail
 
 
 def oracle_rate(wl, c, omega, w, iters_full, sample_iters):
@@ -451,11 +460,23 @@ def main():
     vc_s = v0.elapsed_time(v1) / 1e3 / nv
 
     # dominant kernel: the fused smoothing step (all launch classes of one V-cycle)
-    fl, tsec, nl, detail = time_smoothing(h, wl, torch, stream)
+    fl, by, tsec, nl, detail = time_smoothing(h, wl, torch, stream)
     pk, pk_src = peaks()
     sm_mhz = pk.get("sm_max_mhz", 2032.0)
     alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    achieved = fl / tsec / 1e12
+    if prec == mcmg.FP32:
+        # FP32 channel mixing on the CUDA cores: FFMA-bound (1.6 C flop/B)
+        roof = {"bound": "alu", "kernel": "k_smooth (fused smoothing step, FP32 FFMA)",
+                "achieved": fl / tsec / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
+    else:
+        # BF16 channel mixing on the tensor cores: the step streams e, r, a, s
+        roof = {"bound": "hbm", "kernel": "k_smooth_tc (fused smoothing step, tcgen05 BF16)",
+                "achieved": by / tsec / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "peak_source": f"measured copy bandwidth ({pk_src})"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["detail"] = detail
 
     # end to end through the C ABI with host buffers (copies inside the call)
     f_pin = torch.from_numpy(f_host).pin_memory()
@@ -499,11 +520,7 @@ def main():
         "converged": conv,
         "latency_ms": {"p50": 1e3 * p50, "p99": 1e3 * p99},
         "setup_s": t_setup,
-        "roofline": {"bound": "alu", "kernel": "k_smooth (fused smoothing step, FP32 FFMA)",
-                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved / alu_peak, "traffic": None,
-                     "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
-                     "detail": detail},
+        "roofline": roof,
         "gpu_launches": int(launches),
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 16 * n * 2,

@@ -39,7 +39,7 @@ template <int K2>
 struct Threads {
   static constexpr int value = K2 <= 32 ? 128 : 256;
 };
-constexpr unsigned SPIN_LIMIT = 1u << 20;   // ~1M polls with a short sleep: about a second at most
+constexpr unsigned SPIN_LIMIT = 1u << 20;   // try_waits of at most ~1 us each: about a second
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -80,22 +80,22 @@ __device__ __forceinline__ void bar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// Bounded wait for the phase with parity `parity` (non-blocking polls with a
-// short sleep); returns false when the bound runs out, or at once when another
-// CTA has already recorded a failure in the error word.
+// Bounded wait for the phase with parity `parity`: each try_wait suspends the
+// thread until the phase completes or about 1 us passes, so the loop ends
+// within about a second; it returns false when the bound runs out, or at once
+// when another CTA has already recorded a failure in the error word.
 __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, const int* err) {
   const uint32_t a = smem_u32(bar);
   for (unsigned it = 0; it < SPIN_LIMIT; ++it) {
-    if ((it & 1023) == 1023 && err && *(const volatile int*)err) return false;
+    if ((it & 255) == 255 && err && *(const volatile int*)err) return false;
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.b32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(1000u)
         : "memory");
     if (ok) return true;
-    if (it > 64) __nanosleep(32);
   }
   return false;
 }
@@ -333,15 +333,31 @@ __global__ void __launch_bounds__(tc::Threads<K2>::value, (K2 >= 64 ? 1 : 8)) k_
   // ---------------- phase 1: X = sum_tap E_tap W~_tap^T, Y = E_0 K~_A^T ----------------
   if (ein) {
     {
-      uint4 av[Stage<K2>::PER], bv[Stage<K2>::BPER], kv[Stage<K2>::BPER];
-      load_a<K2>(av, ein, n0, p, 0);
+      // tap t's gather lives in register stage t & 1 from the iteration
+      // before it is stored: the global loads of tap j+2 are issued before the
+      // wait for the MMAs of tap j-1 and the stores of tap j+1
+      uint4 av0[Stage<K2>::PER], av1[Stage<K2>::PER], bv[Stage<K2>::BPER], kv[Stage<K2>::BPER];
+      load_a<K2>(av0, ein, n0, p, 0);
+      load_a<K2>(av1, ein, n0, p, 1);
       load_b<K2>(bv, p.Wtap);
       load_b<K2>(kv, p.KA);
-      store_a<K2>(Atile(0), av);
+      store_a<K2>(Atile(0), av0);
       store_b<K2>(Btile(0), bv);
       store_b<K2>(Btile(2), kv);
       tc::fence_async_smem();
       __syncthreads();
+      auto advance = [&](uint4 (&cur)[Stage<K2>::PER], uint4 (&nxt)[Stage<K2>::PER],
+                         int j) -> bool {
+        const int nb = (j + 1) & 1;
+        if (j + 2 < NT) load_a<K2>(nxt, ein, n0, p, j + 2);
+        load_b<K2>(bv, p.Wtap + (size_t)(j + 1) * (B_BYTES / 16));
+        if (j >= 1 && !wait_bar(nb)) return false;   // buffers of tap j-1 free
+        store_a<K2>(Atile(nb), cur);
+        store_b<K2>(Btile(nb), bv);
+        tc::fence_async_smem();
+        __syncthreads();
+        return true;
+      };
       for (int j = 0; j < NT && ok; ++j) {
         const int b = j & 1;
         if (threadIdx.x == 0) {
@@ -350,17 +366,7 @@ __global__ void __launch_bounds__(tc::Threads<K2>::value, (K2 >= 64 ? 1 : 8)) k_
           if (j == 0) issue_gemm<K2>(tY, Atile(0), Btile(2), false);
           tc::mma_commit(&bars[b]);
         }
-        if (j + 1 < NT) {
-          const int nb = (j + 1) & 1;
-          // fetch tap j+1 while the MMAs of tap j run
-          load_a<K2>(av, ein, n0, p, j + 1);
-          load_b<K2>(bv, p.Wtap + (size_t)(j + 1) * (B_BYTES / 16));
-          if (j >= 1 && !wait_bar(nb)) { ok = false; break; }   // buffers of tap j-1 free
-          store_a<K2>(Atile(nb), av);
-          store_b<K2>(Btile(nb), bv);
-          tc::fence_async_smem();
-          __syncthreads();
-        }
+        if (j + 1 < NT) ok = (j & 1) ? advance(av0, av1, j) : advance(av1, av0, j);
       }
       // outstanding: the commits of taps NT-2 and NT-1
       if (ok) ok = wait_bar((NT - 2) & 1);
