@@ -339,11 +339,12 @@ struct Krylov {
   double t_solve = 0.0;
 };
 
-// Blocks of the grid-stride reductions: about four elements per thread, at
-// most two blocks per SM.
+// Blocks of the grid-stride reductions: about one element per thread, at
+// most four blocks per SM (the update and multi-dot loops over the basis are
+// serial per element, so parallelism over elements hides their latency).
 static int red_blocks(long long n) {
-  long long b = (n + 4 * RED_T - 1) / (4 * RED_T);
-  long long cap = 148 * 2;
+  long long b = (n + RED_T - 1) / RED_T;
+  long long cap = 148 * 4;
   return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
