@@ -176,7 +176,8 @@ def time_smoothing(h, wl, torch, stream, reps=20):
             total_t += per * count
             launches += count
             detail.append(dict(level=l, C=C, first=first, count=count, us=per * 1e6,
-                               tflops=fl / per / 1e12, gbs=by / per / 1e9))
+                               tflops=fl / per / 1e12, gbs=by / per / 1e9,
+                               shape=h.kernel_shape(l, 0)))
     return total_f, total_b, total_t, launches, detail
 
 

@@ -266,6 +266,26 @@ mcmg_status mcmg_cgs2(mcmg_handle h, const void* V_dev, int k, size_t n, void* w
 mcmg_status mcmg_cgs2_noalloc(const void* V_dev, int k, size_t n, void* w_dev,
                               double* h_host, double* norm_host, void* stream);
 
+/* Kernel shapes of the CUDA-core V-cycle operations (tuning and test access;
+ * the paper has no counterpart).  op: 0 smoothing step, 1 residual
+ * r - A_l(e), 2 restriction R_l, 3 prolongation P_l (ops 2 and 3 exist for
+ * level < levels-1).  Each has several interchangeable kernels and thread
+ * shapes with the same results up to FP32 rounding order; setup times them
+ * on every level and keeps the fastest.
+ *   mcmg_kernel_shape_count: number of shapes of op (indices 0 .. count-1),
+ *                            0 for an unknown op.
+ *   mcmg_get_kernel_shape:   the shape `level` uses for op (*shape).
+ *   mcmg_set_kernel_shape:   use `shape` from now on, or -1 for setup's
+ *                            choice; MCMG_ERR_SHAPE (nothing changed) if the
+ *                            shape cannot run on this level's channels.
+ * A change applies to later calls; captured V-cycle graphs are re-captured
+ * at their next use.  Call only while no solve or request on this handle is
+ * in flight.  Op 0 on a level that runs on the tensor cores (BF16 handles,
+ * C_l >= 8) is not affected.                                                  */
+int mcmg_kernel_shape_count(int op);
+mcmg_status mcmg_get_kernel_shape(mcmg_handle h, int level, int op, int* shape);
+mcmg_status mcmg_set_kernel_shape(mcmg_handle h, int level, int op, int shape);
+
 /* Number of kernel launches the library has issued in this process (a
  * captured graph counts as its kernel nodes).  For launch accounting.        */
 uint64_t mcmg_kernel_launches(void);

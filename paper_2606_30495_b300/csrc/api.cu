@@ -186,6 +186,16 @@ static mcmg_status capture_levels_n(mcmg_handle_s* h, VWork* w, int count, cudaG
   return MCMG_OK;
 }
 
+// Drop graphs captured before a smoothing shape was overridden.
+static void refresh_graphs(mcmg_handle_s* h, VWork* w) {
+  if (w->shape_gen == h->shape_gen) return;
+  if (w->graph) cudaGraphExecDestroy(w->graph);
+  w->graph = nullptr;
+  for (auto& kv : w->sub) cudaGraphExecDestroy(kv.second.first);
+  w->sub.clear();
+  w->shape_gen = h->shape_gen;
+}
+
 static mcmg_status capture_levels(mcmg_handle_s* h, VWork* w) {
   return capture_levels_n(h, w, w->nrhs, &w->graph, &w->graph_kernels);
 }
@@ -197,6 +207,7 @@ mcmg_status vcycle_run_batch(mcmg_handle_s* h, VWork* w, const float2* const* sr
     return MCMG_ERR_ARG;
   }
   const Level& l0 = h->lv[0];
+  refresh_graphs(h, w);
   MCMG_TRY(launch_lift_gather(srcs, h->lift, w->r[0], l0.C, l0.g.nodes(), count, st));
   cudaGraphExec_t exec;
   unsigned long long kernels;
@@ -228,6 +239,7 @@ mcmg_status vcycle_run(mcmg_handle_s* h, VWork* w, const float2* r, float2* e, i
     return MCMG_ERR_ARG;
   }
   const Level& l0 = h->lv[0];
+  refresh_graphs(h, w);
   MCMG_TRY(launch_lift(r, h->lift, w->r[0], l0.C, l0.g.nodes(), nrhs, st));
   if (!w->graph) MCMG_TRY(capture_levels(h, w));
   MCMG_CUDA(cudaGraphLaunch(w->graph, st));
@@ -509,8 +521,10 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
       return cleanup(), s;
     MCMG_CUDA(cudaMemsetAsync(s0, 0, sizeof(float2) * big, st));
     MCMG_CUDA(cudaMemsetAsync(s1, 0, sizeof(float2) * big, st));
-    for (int l = 0; l < L; ++l)
+    for (int l = 0; l < L; ++l) {
       if ((s = autotune_smooth(h->lv[l], s0, s1, s2, st))) return cleanup(), s;
+      if (l < L - 1 && (s = autotune_transfer(h->lv[l], s0, s1, st))) return cleanup(), s;
+    }
   }
   cudaError_t e = cudaStreamSynchronize(st);
   cleanup();
@@ -682,6 +696,35 @@ static mcmg_status check_level(mcmg_handle h, int level, bool need_next) {
   if (!h || level < 0 || level >= h->L || (need_next && level >= h->L - 1)) {
     set_error("level %d out of range", level);
     return MCMG_ERR_ARG;
+  }
+  return MCMG_OK;
+}
+
+int mcmg_kernel_shape_count(int op) { return op < 0 || op > 3 ? 0 : kernel_shape_count(op); }
+
+mcmg_status mcmg_get_kernel_shape(mcmg_handle h, int level, int op, int* shape) {
+  MCMG_TRY(check_level(h, level, op >= 2));
+  if (!shape || op < 0 || op > 3) { set_error("bad argument"); return MCMG_ERR_ARG; }
+  *shape = h->lv[level].shape[op];
+  return MCMG_OK;
+}
+
+mcmg_status mcmg_set_kernel_shape(mcmg_handle h, int level, int op, int shape) {
+  MCMG_TRY(check_level(h, level, op >= 2));
+  if (op < 0 || op > 3 || shape < -1 || shape >= kernel_shape_count(op)) {
+    set_error("bad argument");
+    return MCMG_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(h->mu);
+  Level& lv = h->lv[level];
+  if (shape >= 0 && !kernel_shape_valid(lv, op, shape)) {
+    set_error("shape %d cannot run operation %d on level %d", shape, op, level);
+    return MCMG_ERR_SHAPE;
+  }
+  const int want = shape < 0 ? lv.tuned[op] : shape;
+  if (want != lv.shape[op]) {
+    lv.shape[op] = want;
+    ++h->shape_gen;
   }
   return MCMG_OK;
 }

@@ -1,0 +1,226 @@
+// Register-tiled restriction and prolongation (the inter-grid transfers of
+// Section 3.2 / Algorithm 2): kernels, launch, dispatch over channel pairs.
+#include "vcycle_kernels.cuh"
+
+namespace mcmg {
+
+// rc[J][co] = sum_o sum_ci R[o][co][ci] t[2J + o][ci]   (CI fine, CO coarse channels)
+template <int CI, int CO, int D, int TN, int CV, int KQ>
+__global__ void __launch_bounds__(256) k_restrict_rt(TransferParams p) {
+  using T = XTile<CI, CO, TN, CV, KQ>;
+  constexpr int NB = T::NB, KS = T::KS, T3 = D == 3 ? 27 : 9, CI2 = CI / 2;
+  extern __shared__ float4 sm4[];
+  float2* E = reinterpret_cast<float2*>(sm4);   // [T3][NB][CI]
+  float2* red = E + T3 * NB * CI;               // [KS][NB][CO]
+  const int tid = threadIdx.x;
+  const int cg = tid % T::CG;
+  const int ng = (tid / T::CG) % T::NG;
+  const int kg = tid / (T::CG * T::NG);
+  const int co0 = cg * CV, j0 = ng * TN, ci0 = kg * KQ;
+  const long long NC = p.dst_nodes;
+  const float2* __restrict__ t = p.src + (size_t)blockIdx.y * p.src_nodes * CI;
+  float2* __restrict__ rc = p.dst + (size_t)blockIdx.y * NC * CO;
+  const long long n0 = (long long)blockIdx.x * NB;
+  for (int idx = tid; idx < T3 * NB * CI2; idx += 256) {
+    const int c2 = idx % CI2;
+    const int j = (idx / CI2) % NB;
+    const int o = idx / (CI2 * NB);
+    const long long n = n0 + j;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (n < NC) {
+      int jx, jy, jz;
+      node_xyz(n, p.cx, p.cy, jx, jy, jz);
+      const int x = 2 * jx + o % 3 - 1, y = 2 * jy + (o / 3) % 3 - 1;
+      const int z = D == 3 ? 2 * jz + o / 9 - 1 : 0;
+      if (x >= 0 && x < p.fx && y >= 0 && y < p.fy && z >= 0 && z < p.fz)
+        v = __ldg(reinterpret_cast<const float4*>(t + (((long long)z * p.fy + y) * p.fx + x) * CI) + c2);
+    }
+    sm4[(o * NB + j) * CI2 + c2] = v;
+  }
+  __syncthreads();
+  float2 acc[TN][CV];
+#pragma unroll
+  for (int k = 0; k < TN; ++k)
+#pragma unroll
+    for (int c = 0; c < CV; ++c) acc[k][c] = make_float2(0.f, 0.f);
+#pragma unroll 3
+  for (int o = 0; o < T3; ++o) {
+    const float2* __restrict__ wt = p.Wt + (size_t)o * CI * CO;
+    const float2* X = E + o * NB * CI;
+#pragma unroll
+    for (int i = 0; i < KQ; ++i) {
+      float2 w[CV];
+      ldc<CV>(wt + (ci0 + i) * CO + co0, w);
+#pragma unroll
+      for (int k = 0; k < TN; ++k) {
+        const float2 v = X[(j0 + k) * CI + ci0 + i];
+#pragma unroll
+        for (int c = 0; c < CV; ++c) cfma(acc[k][c], w[c], v);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < TN; ++k) stc<CV>(red + (kg * NB + j0 + k) * CO + co0, acc[k]);
+  __syncthreads();
+  for (int idx = tid; idx < NB * CO; idx += 256) {
+    const long long n = n0 + idx / CO;
+    if (n < NC) {
+      float2 v = red[idx];
+#pragma unroll
+      for (int q = 1; q < KS; ++q) v = cadd(v, red[q * NB * CO + idx]);
+      rc[n0 * CO + idx] = v;
+    }
+  }
+}
+
+// e[2J + b] += sum over taps o with b(o) = b of P[o] e_c[J + c(o)]
+// (coarse-node form of the transposed convolution, as k_prolong_add; CI
+// coarse, CO fine channels).  The block stages e_c at J + {0,1}^d.
+template <int CI, int CO, int D, int TN, int CV, int KQ>
+__global__ void __launch_bounds__(256) k_prolong_rt(TransferParams p) {
+  using T = XTile<CI, CO, TN, CV, KQ>;
+  constexpr int NB = T::NB, KS = T::KS, T3 = D == 3 ? 27 : 9, NP = D == 3 ? 8 : 4;
+  constexpr int CI2 = CI / 2;
+  extern __shared__ float4 sm4[];
+  float2* E = reinterpret_cast<float2*>(sm4);   // [NP][NB][CI]
+  float2* red = E + NP * NB * CI;               // [KS][NB][NP][CO]
+  const int tid = threadIdx.x;
+  const int cg = tid % T::CG;
+  const int ng = (tid / T::CG) % T::NG;
+  const int kg = tid / (T::CG * T::NG);
+  const int co0 = cg * CV, j0 = ng * TN, ci0 = kg * KQ;
+  const long long NC = p.src_nodes;
+  const float2* __restrict__ ec = p.src + (size_t)blockIdx.y * NC * CI;
+  float2* __restrict__ e = p.dst + (size_t)blockIdx.y * p.dst_nodes * CO;
+  const long long n0 = (long long)blockIdx.x * NB;
+  for (int idx = tid; idx < NP * NB * CI2; idx += 256) {
+    const int c2 = idx % CI2;
+    const int j = (idx / CI2) % NB;
+    const int c = idx / (CI2 * NB);
+    const long long n = n0 + j;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (n < NC) {
+      int jx, jy, jz;
+      node_xyz(n, p.cx, p.cy, jx, jy, jz);
+      const int X = jx + (c & 1), Y = jy + ((c >> 1) & 1), Z = jz + ((c >> 2) & 1);
+      if (X < p.cx && Y < p.cy && (D == 3 ? Z < p.cz : true))
+        v = __ldg(reinterpret_cast<const float4*>(ec + (((long long)(D == 3 ? Z : 0) * p.cy + Y) * p.cx + X) * CI) + c2);
+    }
+    sm4[(c * NB + j) * CI2 + c2] = v;
+  }
+  __syncthreads();
+  float2 acc[NP][TN][CV];
+#pragma unroll
+  for (int b = 0; b < NP; ++b)
+#pragma unroll
+    for (int k = 0; k < TN; ++k)
+#pragma unroll
+      for (int c = 0; c < CV; ++c) acc[b][k][c] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int o = 0; o < T3; ++o) {
+    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = D == 3 ? o / 9 - 1 : 0;
+    const int b = (ox != 0) | ((oy != 0) << 1) | ((oz != 0) << 2);
+    const int c = (ox == -1) | ((oy == -1) << 1) | ((oz == -1) << 2);
+    const float2* __restrict__ wt = p.Wt + (size_t)o * CI * CO;
+    const float2* X = E + c * NB * CI;
+#pragma unroll
+    for (int i = 0; i < KQ; ++i) {
+      float2 w[CV];
+      ldc<CV>(wt + (ci0 + i) * CO + co0, w);
+#pragma unroll
+      for (int k = 0; k < TN; ++k) {
+        const float2 v = X[(j0 + k) * CI + ci0 + i];
+#pragma unroll
+        for (int cc = 0; cc < CV; ++cc) cfma(acc[b][k][cc], w[cc], v);
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NP; ++b)
+#pragma unroll
+    for (int k = 0; k < TN; ++k) stc<CV>(red + ((kg * NB + j0 + k) * NP + b) * CO + co0, acc[b][k]);
+  __syncthreads();
+  for (int idx = tid; idx < NB * NP * CO; idx += 256) {
+    const int co = idx % CO;
+    const int b = (idx / CO) % NP;
+    const long long n = n0 + idx / (CO * NP);
+    if (n < NC) {
+      float2 v = red[idx];
+#pragma unroll
+      for (int q = 1; q < KS; ++q) v = cadd(v, red[q * NB * NP * CO + idx]);
+      int jx, jy, jz;
+      node_xyz(n, p.cx, p.cy, jx, jy, jz);
+      const long long fx = 2 * jx + (b & 1), fy = 2 * jy + ((b >> 1) & 1),
+                      fz = D == 3 ? 2 * jz + ((b >> 2) & 1) : 0;
+      const long long fi = ((fz * p.fy + fy) * p.fx + fx) * CO + co;
+      e[fi] = cadd(e[fi], v);
+    }
+  }
+}
+
+template <int CI, int CO, int D, int TN, int CV, int KQ>
+static mcmg_status transfer_rt(const TransferParams& p, bool restrict_, int nrhs, cudaStream_t st) {
+  using T = XTile<CI, CO, TN, CV, KQ>;
+  constexpr int T3 = D == 3 ? 27 : 9, NP = D == 3 ? 8 : 4;
+  constexpr size_t smem_r = (size_t)(T3 * T::NB * CI + T::KS * T::NB * CO) * sizeof(float2);
+  constexpr size_t smem_p = (size_t)(NP * T::NB * CI + T::KS * T::NB * NP * CO) * sizeof(float2);
+  if constexpr (!T::valid) {
+    set_error("register-tiled transfer shape does not fit %d -> %d channels", CI, CO);
+    return MCMG_ERR_SHAPE;
+  } else {
+    if ((restrict_ ? smem_r : smem_p) > kMaxSmem) {
+      set_error("register-tiled transfer shape needs too much shared memory");
+      return MCMG_ERR_SHAPE;
+    }
+    const long long units = restrict_ ? p.dst_nodes : p.src_nodes;
+    dim3 grid((unsigned)((units + T::NB - 1) / T::NB), (unsigned)nrhs);
+    if (restrict_) {
+      auto k = k_restrict_rt<CI, CO, D, TN, CV, KQ>;
+      if (smem_r > 48 * 1024) MCMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
+      k<<<grid, 256, smem_r, st>>>(p);
+    } else {
+      auto k = k_prolong_rt<CI, CO, D, TN, CV, KQ>;
+      if (smem_p > 48 * 1024) MCMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
+      k<<<grid, 256, smem_p, st>>>(p);
+    }
+    MCMG_CHECK_LAUNCH(restrict_ ? "restrict_rt" : "prolong_rt");
+    return MCMG_OK;
+  }
+}
+
+template <int CI, int CO, int D>
+static mcmg_status transfer_rt_shape(const TransferParams& p, bool r, int tn, int cv, int kq,
+                                     int nrhs, cudaStream_t st) {
+  if (cv == 4) {
+    if (tn == 1 && kq == 4) return transfer_rt<CI, CO, D, 1, 4, 4>(p, r, nrhs, st);
+    if (tn == 2 && kq == 4) return transfer_rt<CI, CO, D, 2, 4, 4>(p, r, nrhs, st);
+    if (tn == 1 && kq == 8) return transfer_rt<CI, CO, D, 1, 4, 8>(p, r, nrhs, st);
+    if (tn == 2 && kq == 8) return transfer_rt<CI, CO, D, 2, 4, 8>(p, r, nrhs, st);
+    if (tn == 1 && kq == 2) return transfer_rt<CI, CO, D, 1, 4, 2>(p, r, nrhs, st);
+  }
+  set_error("register-tiled transfer shape (%d, %d, %d) is not built", tn, cv, kq);
+  return MCMG_ERR_SHAPE;
+}
+
+template <int D>
+static mcmg_status transfer_rt_d(const TransferParams& p, int Cf, int Cc, bool r, int tn, int cv,
+                                 int kq, int nrhs, cudaStream_t st) {
+#define MCMG_XT_PAIR(F, Cq)                                                                 \
+  if (Cf == F && Cc == Cq)                                                                  \
+    return r ? transfer_rt_shape<F, Cq, D>(p, true, tn, cv, kq, nrhs, st)                        \
+             : transfer_rt_shape<Cq, F, D>(p, false, tn, cv, kq, nrhs, st);
+  MCMG_XT_PAIR(4, 4) MCMG_XT_PAIR(4, 8) MCMG_XT_PAIR(8, 8) MCMG_XT_PAIR(8, 16)
+  MCMG_XT_PAIR(16, 16) MCMG_XT_PAIR(16, 32) MCMG_XT_PAIR(32, 32) MCMG_XT_PAIR(32, 64)
+  MCMG_XT_PAIR(64, 64)
+#undef MCMG_XT_PAIR
+  set_error("no register-tiled transfer for %d -> %d channels", Cf, Cc);
+  return MCMG_ERR_SHAPE;
+}
+
+mcmg_status transfer_rt_launch(const TransferParams& p, int Cf, int Cc, int D, bool restrict_,
+                               int tn, int cv, int kq, int nrhs, cudaStream_t st) {
+  return D == 3 ? transfer_rt_d<3>(p, Cf, Cc, restrict_, tn, cv, kq, nrhs, st)
+                : transfer_rt_d<2>(p, Cf, Cc, restrict_, tn, cv, kq, nrhs, st);
+}
+
+}  // namespace mcmg

@@ -11,7 +11,7 @@
 // output channel co of TN nodes, so each weight load feeds TN complex FMAs.
 // t and z go through shared memory because K_S and W^(i) mix all channels of
 // a node.
-#include "mcmg_internal.cuh"
+#include "vcycle_kernels.cuh"
 
 namespace mcmg {
 
@@ -22,23 +22,35 @@ namespace mcmg {
 // (CO complex values, one 32-byte vector load for CO = 4) feeds CO * TN
 // complex FMAs.  The shape is chosen per level and mode by the autotuner at
 // setup (autotune_smooth); pick_shape is the fallback heuristic.
-template <int C, int TN_, int CO_>
-struct Tile {
-  static constexpr int CO = CO_;
-  static constexpr int CG = C / CO;
-  static constexpr int G = 256 / CG;
-  static constexpr int TN = TN_;
-  static constexpr int NB = G * TN;
-};
-
 struct Shape {
-  int tn, co;
+  int kind;    // 0: k_smooth (Tile), 1: k_smooth_ks (KsTile), 2: k_smooth_rt (RtTile)
+  int tn, co;  // nodes and output channels per thread
+  int kq;      // input channels per K-group (k_smooth_rt)
 };
-// co = 0 marks the K-split shape (k_smooth_ks).
-static constexpr Shape kShapes[] = {{8, 1}, {2, 1}, {1, 1}, {2, 4}, {1, 4}, {1, 0}};
-static constexpr int kNumShapes = 6;
+static constexpr Shape kShapes[] = {{0, 8, 1, 0}, {0, 2, 1, 0}, {0, 1, 1, 0}, {0, 2, 4, 0},
+                                    {0, 1, 4, 0}, {1, 1, 1, 0}, {2, 8, 4, 4}, {2, 4, 4, 4},
+                                    {2, 8, 4, 2}, {2, 4, 4, 2}, {2, 8, 4, 8}, {2, 4, 4, 8}};
+static constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-static bool shape_ok(int s, int C) { return kShapes[s].co == 0 ? C >= 8 : kShapes[s].co <= C; }
+// Shared memory of k_smooth_rt: the staged fields of the 2D+1 taps (reused
+// for t and z) and two sets of KS partial tiles (K_A and the rest).
+static size_t rt_smem(int C, int D, int tn, int co, int kq) {
+  if (co > C || C % co || kq > C || C % kq) return 0;
+  const int cg = C / co, ks = C / kq;
+  if (cg * ks > 256 || 256 % (cg * ks)) return 0;
+  const size_t nb = (size_t)(256 / (cg * ks)) * tn;
+  return (size_t)(2 * D + 1 + 2 * ks) * nb * C * sizeof(float2);
+}
+
+static bool shape_ok(int s, int C, int D) {
+  const Shape& k = kShapes[s];
+  if (k.kind == 1) return C >= 8;
+  if (k.kind == 2) {
+    const size_t b = rt_smem(C, D, k.tn, k.co, k.kq);
+    return b > 0 && b <= kMaxSmem;
+  }
+  return k.co <= C;
+}
 
 // Largest nodes-per-thread (8, 2 or 1, one channel per thread) that still
 // gives at least two blocks per SM.
@@ -56,54 +68,6 @@ static int pick_shape(long long nodes, int C, int nrhs) {
 // Largest nodes-per-thread (8, 2 or 1) for the transfer kernels.
 static int pick_tn(long long nodes, int C, int nrhs) {
   return kShapes[pick_shape(nodes, C, nrhs)].tn;
-}
-
-struct SmoothParams {
-  const float2* r;
-  const float2* e_in;   // null: e = 0 (first pre-smoothing step)
-  float2* e_out;
-  const float2* a;
-  const float2* s;
-  const float2* Wt;     // [T][C][C]
-  const float2* KAt;
-  const float2* KSt;
-  const float2* Wst;    // W^(i) for this step, [C][C]
-  int nx, ny, nz;
-  long long nodes;
-};
-
-__device__ __forceinline__ void node_xyz(long long n, int nx, int ny, int& x, int& y, int& z) {
-  x = (int)(n % nx);
-  long long rest = n / nx;
-  y = (int)(rest % ny);
-  z = (int)(rest / ny);
-}
-
-// CO consecutive complex values (one float2, or two float4 for CO = 4).
-template <int CO>
-__device__ __forceinline__ void ldc(const float2* __restrict__ q, float2 (&v)[CO]) {
-  if constexpr (CO == 1) {
-    v[0] = __ldg(q);
-  } else {
-    static_assert(CO == 4, "CO is 1 or 4");
-    const float4* q4 = reinterpret_cast<const float4*>(q);
-    const float4 a = __ldg(q4), b = __ldg(q4 + 1);
-    v[0] = make_float2(a.x, a.y);
-    v[1] = make_float2(a.z, a.w);
-    v[2] = make_float2(b.x, b.y);
-    v[3] = make_float2(b.z, b.w);
-  }
-}
-
-template <int CO>
-__device__ __forceinline__ void stc(float2* q, const float2 (&v)[CO]) {
-  if constexpr (CO == 1) {
-    q[0] = v[0];
-  } else {
-    float4* q4 = reinterpret_cast<float4*>(q);
-    q4[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-    q4[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
-  }
 }
 
 template <int C, int D, int MODE, int TN, int CO>
@@ -400,7 +364,10 @@ static mcmg_status smooth_c(const SmoothParams& p, int mode, int shape, int nrhs
     case 2: return smooth_shape<C, D, 1, 1>(p, mode, nrhs, st);
     case 3: return smooth_shape<C, D, 2, 4>(p, mode, nrhs, st);
     case 4: return smooth_shape<C, D, 1, 4>(p, mode, nrhs, st);
-    default: return smooth_ks<C, D>(p, mode, nrhs, st);
+    case 5: return smooth_ks<C, D>(p, mode, nrhs, st);
+    default:
+      return smooth_rt_launch(p, C, D, mode, kShapes[shape].tn, kShapes[shape].co,
+                              kShapes[shape].kq, nrhs, st);
   }
 }
 
@@ -451,14 +418,16 @@ mcmg_status launch_smooth(const Level& L, int step, const float2* r, const float
     return launch_smooth_tc(L, L.tcw, step, r, e_in, e_out, nrhs, L.err, st);
   const SmoothParams p = smooth_params(L, step, r, e_in, e_out, mode);
   int shape = L.shape[mode];
-  if (shape < 0 || !shape_ok(shape, L.C)) shape = pick_shape(p.nodes, L.C, nrhs);
+  if (shape < 0 || !shape_ok(shape, L.C, L.g.d)) shape = pick_shape(p.nodes, L.C, nrhs);
   return smooth_run(L, p, mode, shape, nrhs, st);
 }
 
 // Autotuner: time every valid thread shape of the CUDA-core smoothing kernel
 // on this level (the step with e and the residual mode) with CUDA events on
-// scratch fields, and keep the fastest in L.shape[mode].  Run once per
-// medium at setup, before any V-cycle graph is captured.
+// scratch fields, and keep the fastest in L.shape[mode].  Two passes over the
+// shapes, keeping each shape's better time, so a clock still ramping up at
+// the first pass does not decide.  Run once per medium at setup, before any
+// V-cycle graph is captured.
 mcmg_status autotune_smooth(Level& L, float2* r, float2* e, float2* out, cudaStream_t st) {
   cudaEvent_t e0, e1;
   MCMG_CUDA(cudaEventCreate(&e0));
@@ -467,26 +436,32 @@ mcmg_status autotune_smooth(Level& L, float2* r, float2* e, float2* out, cudaStr
   for (int mode = 0; mode < 2 && status == MCMG_OK; ++mode) {
     if (mode == 0 && L.use_tc) continue;
     const SmoothParams p = smooth_params(L, 0, r, e, out, mode);
-    float best = 1e30f;
-    int best_s = -1;
-    for (int s = 0; s < kNumShapes; ++s) {
-      if (!shape_ok(s, L.C)) continue;
-      for (int rep = 0; rep < 2; ++rep)
-        if ((status = smooth_run(L, p, mode, s, 1, st)) != MCMG_OK) break;
-      if (status != MCMG_OK) break;
-      cudaEventRecord(e0, st);
-      const int reps = 5;
-      for (int rep = 0; rep < reps; ++rep)
-        if ((status = smooth_run(L, p, mode, s, 1, st)) != MCMG_OK) break;
-      if (status != MCMG_OK) break;
-      cudaEventRecord(e1, st);
-      cudaError_t ce = cudaEventSynchronize(e1);
-      if (ce != cudaSuccess) { status = cuda_fail(ce, "autotune"); break; }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; best_s = s; }
+    float best_ms[kNumShapes];
+    for (int s = 0; s < kNumShapes; ++s) best_ms[s] = 1e30f;
+    for (int pass = 0; pass < 2 && status == MCMG_OK; ++pass) {
+      for (int s = 0; s < kNumShapes; ++s) {
+        if (!shape_ok(s, L.C, L.g.d)) continue;
+        for (int rep = 0; rep < 2; ++rep)
+          if ((status = smooth_run(L, p, mode, s, 1, st)) != MCMG_OK) break;
+        if (status != MCMG_OK) break;
+        cudaEventRecord(e0, st);
+        const int reps = 5;
+        for (int rep = 0; rep < reps; ++rep)
+          if ((status = smooth_run(L, p, mode, s, 1, st)) != MCMG_OK) break;
+        if (status != MCMG_OK) break;
+        cudaEventRecord(e1, st);
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) { status = cuda_fail(ce, "autotune"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms[s]) best_ms[s] = ms;
+      }
     }
+    int best_s = -1;
+    for (int s = 0; s < kNumShapes; ++s)
+      if (best_ms[s] < 1e29f && (best_s < 0 || best_ms[s] < best_ms[best_s])) best_s = s;
     L.shape[mode] = best_s;
+    L.tuned[mode] = best_s;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -498,16 +473,6 @@ mcmg_status autotune_smooth(Level& L, float2* r, float2* e, float2* out, cudaStr
 // (multi-channel strided convolution, stride 2, zero padding).  Thread (co, g)
 // owns output channel co of TN coarse nodes.
 // ---------------------------------------------------------------------------
-struct TransferParams {
-  const float2* src;
-  float2* dst;
-  const float2* Wt;    // [T3][cin][CO]
-  int cin;
-  int fx, fy, fz;      // fine grid
-  int cx, cy, cz;      // coarse grid
-  long long src_nodes, dst_nodes;
-};
-
 template <int CO, int D, int TN>
 __global__ void __launch_bounds__(256) k_restrict(TransferParams p) {
   using T = Tile<CO, TN, 1>;
@@ -618,6 +583,36 @@ __global__ void __launch_bounds__(256) k_prolong_add(TransferParams p) {
   }
 }
 
+// Register-tiled transfers.  Same scheme as k_smooth_rt: thread
+// (kg, ng, cg) holds a TN x CV output tile and sums the KQ input channels
+// kg*KQ .. +KQ-1 over every tap; the block stages the source values its
+// nodes read ([offset][node][CI], zero outside the grid) and adds the KS
+// partial tiles through shared memory.  A weight load feeds TN nodes.
+// Transfer shapes: 0 is the one-channel-per-thread kernel above.
+struct TShape {
+  int tn, cv, kq;
+};
+static constexpr TShape kTShapes[] = {{0, 0, 0}, {1, 4, 4}, {2, 4, 4}, {1, 4, 8}, {2, 4, 8}, {1, 4, 2}};
+static constexpr int kNumTShapes = sizeof(kTShapes) / sizeof(kTShapes[0]);
+
+// Register-tiled transfers are built for channel pairs (fine, coarse) with
+// the coarse count equal to or twice the fine one; other pairs use shape 0.
+static bool xt_pair(int Cf, int Cc) {
+  return (Cf == 4 || Cf == 8 || Cf == 16 || Cf == 32 || Cf == 64) && (Cc == Cf || Cc == 2 * Cf) &&
+         Cc <= 64;
+}
+
+// Shared memory of a register-tiled transfer (0: shape cannot run).
+static size_t xt_smem(bool restrict_, int CI, int CO, int D, int tn, int cv, int kq) {
+  if (cv > CO || CO % cv || kq > CI || CI % kq || CI % 2) return 0;
+  const int cg = CO / cv, ks = CI / kq;
+  if (cg * ks > 256 || 256 % (cg * ks)) return 0;
+  const size_t nb = (size_t)(256 / (cg * ks)) * tn;
+  const size_t T3 = D == 3 ? 27 : 9, NP = D == 3 ? 8 : 4;
+  const size_t f2 = restrict_ ? T3 * nb * CI + ks * nb * CO : NP * nb * CI + ks * nb * NP * CO;
+  return f2 * sizeof(float2);
+}
+
 template <int CO, int D, int TN>
 static mcmg_status transfer_tn(const TransferParams& p, bool restrict_, int nrhs, cudaStream_t st) {
   using T = Tile<CO, TN, 1>;
@@ -656,36 +651,101 @@ static mcmg_status transfer_d(const TransferParams& p, int CO, bool r, int nrhs,
   return MCMG_ERR_SHAPE;
 }
 
-mcmg_status launch_restrict(const Level& L, const float2* t, float2* rc, int nrhs,
-                            cudaStream_t st) {
+static TransferParams transfer_params(const Level& L, bool restrict_, const float2* src,
+                                      float2* dst) {
   Grid gc = L.g.coarse();
   TransferParams p;
-  p.src = t;
-  p.dst = rc;
-  p.Wt = L.Rt;
-  p.cin = L.C;
+  p.src = src;
+  p.dst = dst;
+  p.Wt = restrict_ ? L.Rt : L.Pt;
+  p.cin = restrict_ ? L.C : L.Cn;
   p.fx = L.g.nx; p.fy = L.g.ny; p.fz = L.g.nz;
   p.cx = gc.nx; p.cy = gc.ny; p.cz = gc.nz;
-  p.src_nodes = L.g.nodes();
-  p.dst_nodes = gc.nodes();
-  return L.g.d == 3 ? transfer_d<3>(p, L.Cn, true, nrhs, st)
-                    : transfer_d<2>(p, L.Cn, true, nrhs, st);
+  p.src_nodes = restrict_ ? L.g.nodes() : gc.nodes();
+  p.dst_nodes = restrict_ ? gc.nodes() : L.g.nodes();
+  return p;
+}
+
+static bool xshape_ok(int s, const Level& L, bool restrict_) {
+  if (s == 0) return true;
+  if (!xt_pair(L.C, L.Cn)) return false;
+  const TShape& k = kTShapes[s];
+  const int CI = restrict_ ? L.C : L.Cn, CO = restrict_ ? L.Cn : L.C;
+  const size_t b = xt_smem(restrict_, CI, CO, L.g.d, k.tn, k.cv, k.kq);
+  return b > 0 && b <= kMaxSmem;
+}
+
+static mcmg_status transfer_run(const Level& L, const TransferParams& p, bool restrict_, int shape,
+                                int nrhs, cudaStream_t st) {
+  if (shape > 0)
+    return transfer_rt_launch(p, L.C, L.Cn, L.g.d, restrict_, kTShapes[shape].tn,
+                              kTShapes[shape].cv, kTShapes[shape].kq, nrhs, st);
+  const int CO = restrict_ ? L.Cn : L.C;
+  return L.g.d == 3 ? transfer_d<3>(p, CO, restrict_, nrhs, st)
+                    : transfer_d<2>(p, CO, restrict_, nrhs, st);
+}
+
+mcmg_status launch_restrict(const Level& L, const float2* t, float2* rc, int nrhs,
+                            cudaStream_t st) {
+  int shape = L.shape[2];
+  if (shape < 0 || !xshape_ok(shape, L, true)) shape = 0;
+  return transfer_run(L, transfer_params(L, true, t, rc), true, shape, nrhs, st);
 }
 
 mcmg_status launch_prolong_add(const Level& L, const float2* ec, float2* e, int nrhs,
                                cudaStream_t st) {
-  Grid gc = L.g.coarse();
-  TransferParams p;
-  p.src = ec;
-  p.dst = e;
-  p.Wt = L.Pt;
-  p.cin = L.Cn;
-  p.fx = L.g.nx; p.fy = L.g.ny; p.fz = L.g.nz;
-  p.cx = gc.nx; p.cy = gc.ny; p.cz = gc.nz;
-  p.src_nodes = gc.nodes();
-  p.dst_nodes = L.g.nodes();
-  return L.g.d == 3 ? transfer_d<3>(p, L.C, false, nrhs, st)
-                    : transfer_d<2>(p, L.C, false, nrhs, st);
+  int shape = L.shape[3];
+  if (shape < 0 || !xshape_ok(shape, L, false)) shape = 0;
+  return transfer_run(L, transfer_params(L, false, ec, e), false, shape, nrhs, st);
+}
+
+// Autotuner for the transfers of level L (L.shape[2] restriction, [3]
+// prolongation): two timed passes over the valid shapes, as for smoothing.
+// fine, coarse: scratch fields of at least nodes_l * C_l and
+// nodes_{l+1} * C_{l+1} elements.
+mcmg_status autotune_transfer(Level& L, float2* fine, float2* coarse, cudaStream_t st) {
+  cudaEvent_t e0, e1;
+  MCMG_CUDA(cudaEventCreate(&e0));
+  MCMG_CUDA(cudaEventCreate(&e1));
+  mcmg_status status = MCMG_OK;
+  for (int op = 2; op < 4 && status == MCMG_OK; ++op) {
+    const bool r = op == 2;
+    const TransferParams p = transfer_params(L, r, r ? fine : coarse, r ? coarse : fine);
+    float best_ms[kNumTShapes];
+    for (int s = 0; s < kNumTShapes; ++s) best_ms[s] = 1e30f;
+    for (int pass = 0; pass < 2 && status == MCMG_OK; ++pass) {
+      for (int s = 0; s < kNumTShapes; ++s) {
+        if (!xshape_ok(s, L, r)) continue;
+        for (int rep = 0; rep < 2; ++rep)
+          if ((status = transfer_run(L, p, r, s, 1, st)) != MCMG_OK) break;
+        if (status != MCMG_OK) break;
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 5; ++rep)
+          if ((status = transfer_run(L, p, r, s, 1, st)) != MCMG_OK) break;
+        if (status != MCMG_OK) break;
+        cudaEventRecord(e1, st);
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) { status = cuda_fail(ce, "autotune"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms[s]) best_ms[s] = ms;
+      }
+    }
+    int best_s = 0;
+    for (int s = 0; s < kNumTShapes; ++s)
+      if (best_ms[s] < best_ms[best_s]) best_s = s;
+    L.shape[op] = best_s;
+    L.tuned[op] = best_s;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return status;
+}
+
+int kernel_shape_count(int op) { return op < 2 ? kNumShapes : kNumTShapes; }
+bool kernel_shape_valid(const Level& L, int op, int shape) {
+  if (shape < 0 || shape >= kernel_shape_count(op)) return false;
+  return op < 2 ? shape_ok(shape, L.C, L.g.d) : xshape_ok(shape, L, op == 2);
 }
 
 // ---------------------------------------------------------------------------

@@ -320,9 +320,10 @@ struct Krylov {
   double2* gw = nullptr;
   double2* y = nullptr;
   double* dsc = nullptr;
-  Stat* stat_h = nullptr;   // mapped pinned
+  Stat* stat_h = nullptr;   // mapped pinned: [0, m) per Arnoldi step, [m + 1] restart
   Stat* stat_d = nullptr;
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev = nullptr;         // restart residual ready
+  cudaEvent_t evs[2] = {};          // Arnoldi step j ready: evs[j & 1]
   cudaStream_t st = nullptr;        // stream of the current solve
   cudaStream_t own = nullptr;       // the solve's private stream (server use)
   DevArena arena;
@@ -332,6 +333,7 @@ struct Krylov {
   mcmg_solve_opts o{};
   enum Phase { IDLE, WAIT_RES, WAIT_STEP, NEED_STEP, DONE } phase = IDLE;
   int j = 0, iters = 0, restarts = 0, max_iters = 0;
+  int enq = 0;                      // Arnoldi steps enqueued in this cycle (j <= enq - 1 <= j + 1)
   double fnorm = 0.0, rel = 0.0;
   bool converged = false;
   mcmg_status final = MCMG_OK;
@@ -378,9 +380,11 @@ mcmg_status krylov_create(mcmg_handle_s* h, int m, Krylov** out, bool own_vcycle
     krylov_destroy(h, k);
     return s;
   }
-  cudaError_t e = cudaHostAlloc((void**)&k->stat_h, sizeof(Stat), cudaHostAllocMapped);
+  cudaError_t e = cudaHostAlloc((void**)&k->stat_h, sizeof(Stat) * (m + 2), cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&k->stat_d, k->stat_h, 0);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&k->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&k->evs[0], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&k->evs[1], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&k->own, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     krylov_destroy(h, k);
@@ -396,6 +400,8 @@ void krylov_destroy(mcmg_handle_s* h, Krylov* k) {
   arena_free(h, k->arena);
   if (k->stat_h) cudaFreeHost(k->stat_h);
   if (k->ev) cudaEventDestroy(k->ev);
+  for (cudaEvent_t e : k->evs)
+    if (e) cudaEventDestroy(e);
   if (k->own) cudaStreamDestroy(k->own);
   delete k;
 }
@@ -404,7 +410,7 @@ void krylov_destroy(mcmg_handle_s* h, Krylov* k) {
 static mcmg_status enqueue_restart(Krylov* k) {
   mcmg_handle_s* h = k->h;
   MCMG_TRY(launch_residual64(h->q64, k->f, k->u, k->r64, k->part, k->nblk, h->g0, 1, k->st));
-  k_reduce_res<<<1, RED_T, 0, k->st>>>(k->part, k->nblk, k->dsc, &k->stat_d->rr);
+  k_reduce_res<<<1, RED_T, 0, k->st>>>(k->part, k->nblk, k->dsc, &k->stat_d[k->m + 1].rr);
   MCMG_CHECK_LAUNCH("reduce_res");
   MCMG_CUDA(cudaEventRecord(k->ev, k->st));
   k->phase = Krylov::WAIT_RES;
@@ -423,10 +429,9 @@ static mcmg_status multidot(Krylov* k, int nv, bool self, double2* out) {
 
 // The Arnoldi part of step j once z_j = MG(v_j) is in Z: w = A z_j, CGS2,
 // Givens, v_{j+1}.  No event.
-static mcmg_status enqueue_arnoldi(Krylov* k) {
+static mcmg_status enqueue_arnoldi(Krylov* k, int j) {
   mcmg_handle_s* h = k->h;
   const long long n = k->n;
-  const int j = k->j;
   float2* zj = k->Z + (size_t)j * n;
   MCMG_TRY(launch_apply_A_mixed(h->q64, zj, k->w, h->g0, 1, k->st));
   MCMG_TRY(multidot(k, j + 1, true, k->d1));
@@ -438,7 +443,7 @@ static mcmg_status enqueue_arnoldi(Krylov* k) {
   k_reduce_scalar<<<1, RED_T, 0, k->st>>>(k->part, k->nblk, k->dsc + 3);
   MCMG_CHECK_LAUNCH("reduce_scalar");
   k_givens<<<1, 32, 0, k->st>>>(j, k->m, k->d1, k->d2, k->dsc, k->H, k->cs, k->sn, k->g,
-                                k->stat_d);
+                                k->stat_d + j);
   MCMG_CHECK_LAUNCH("givens");
   if (j + 1 <= k->m) {
     k_scale<<<(unsigned)((n + 255) / 256), 256, 0, k->st>>>(k->w, k->dsc, k->V + (size_t)(j + 1) * n, n);
@@ -448,13 +453,24 @@ static mcmg_status enqueue_arnoldi(Krylov* k) {
   return MCMG_OK;
 }
 
-// One Arnoldi step j: z_j = MG(v_j), then the Arnoldi part; event.
-static mcmg_status enqueue_step(Krylov* k) {
+// One Arnoldi step j: z_j = MG(v_j), then the Arnoldi part; event evs[j & 1].
+static mcmg_status enqueue_step(Krylov* k, int j) {
   const long long n = k->n;
-  MCMG_TRY(vcycle_run(k->h, k->vw, k->V + (size_t)k->j * n, k->Z + (size_t)k->j * n, 1, k->st));
-  MCMG_TRY(enqueue_arnoldi(k));
-  MCMG_CUDA(cudaEventRecord(k->ev, k->st));
+  MCMG_TRY(vcycle_run(k->h, k->vw, k->V + (size_t)j * n, k->Z + (size_t)j * n, 1, k->st));
+  MCMG_TRY(enqueue_arnoldi(k, j));
+  MCMG_CUDA(cudaEventRecord(k->evs[j & 1], k->st));
+  k->enq = j + 1;
   return MCMG_OK;
+}
+
+// Step j + 1 may be enqueued before the host has read step j's residual
+// estimate: it only reads v_{j+1} and the rotations, all produced on the
+// device in stream order, and if step j ends the cycle its writes (z_{j+1},
+// column j+1 of H, g_{j+1}, g_{j+2}, v_{j+2}) are never read (the back
+// substitution and update use columns 0..j).  So the device never waits for
+// the host between steps; a cycle that stops early wastes one step.
+static bool may_run_ahead(const Krylov* k, int step) {
+  return step < k->m && k->iters + (step - k->j) + 1 <= k->max_iters;
 }
 
 static mcmg_status enqueue_finish_cycle(Krylov* k, int kk) {
@@ -496,15 +512,14 @@ mcmg_status krylov_advance(Krylov* k, bool blocking, int* done) {
     *done = 1;
     return MCMG_OK;
   }
+  cudaEvent_t ev = k->phase == Krylov::WAIT_RES ? k->ev : k->evs[k->j & 1];
   if (blocking) {
-    MCMG_CUDA(cudaEventSynchronize(k->ev));
+    MCMG_CUDA(cudaEventSynchronize(ev));
   } else {
-    cudaError_t e = cudaEventQuery(k->ev);
+    cudaError_t e = cudaEventQuery(ev);
     if (e == cudaErrorNotReady) return MCMG_OK;
     if (e != cudaSuccess) return cuda_fail(e, "krylov event");
   }
-  Stat st;
-  std::memcpy(&st, (const void*)k->stat_h, sizeof(Stat));
   if (k->h->err_host && *(volatile int*)k->h->err_host) {
     set_error("a bounded wait in a tensor-core kernel ran out (code %d)", *k->h->err_host);
     finish(k, false, MCMG_ERR_TIMEOUT);
@@ -512,6 +527,8 @@ mcmg_status krylov_advance(Krylov* k, bool blocking, int* done) {
     return MCMG_OK;
   }
   if (k->phase == Krylov::WAIT_RES) {
+    Stat st;
+    std::memcpy(&st, (const void*)(k->stat_h + k->m + 1), sizeof(Stat));
     if (k->fnorm < 0.0) k->fnorm = std::sqrt(st.ff);
     const double beta = std::sqrt(st.rr);
     if (!std::isfinite(beta)) {
@@ -536,9 +553,14 @@ mcmg_status krylov_advance(Krylov* k, bool blocking, int* done) {
                                                                         k->g, k->m);
     MCMG_CHECK_LAUNCH("start_cycle");
     k->j = 0;
-    return enqueue_step(k);
+    k->phase = Krylov::WAIT_STEP;
+    MCMG_TRY(enqueue_step(k, 0));
+    if (may_run_ahead(k, 1)) MCMG_TRY(enqueue_step(k, 1));
+    return MCMG_OK;
   }
-  // WAIT_STEP
+  // WAIT_STEP: step j has finished (step j + 1 may be queued behind it)
+  Stat st;
+  std::memcpy(&st, (const void*)(k->stat_h + k->j), sizeof(Stat));
   k->iters += 1;
   const double est = st.res / k->fnorm;
   if (!std::isfinite(est)) {
@@ -550,7 +572,9 @@ mcmg_status krylov_advance(Krylov* k, bool blocking, int* done) {
                     k->iters >= k->max_iters;
   if (stop) return enqueue_finish_cycle(k, k->j + 1);
   k->j += 1;
-  return enqueue_step(k);
+  if (k->enq <= k->j) MCMG_TRY(enqueue_step(k, k->j));
+  if (k->enq == k->j + 1 && may_run_ahead(k, k->j + 1)) MCMG_TRY(enqueue_step(k, k->j + 1));
+  return MCMG_OK;
 }
 
 int krylov_m(const Krylov* k) { return k->m; }
@@ -583,11 +607,11 @@ mcmg_status stationary_run(Krylov* k, const double2* f, double2* u, const mcmg_s
   bool conv = false;
   for (;; ++it) {
     MCMG_TRY(launch_residual64(h->q64, f, u, k->r64, k->part, k->nblk, h->g0, 1, st));
-    k_reduce_res<<<1, RED_T, 0, st>>>(k->part, k->nblk, k->dsc, &k->stat_d->rr);
+    k_reduce_res<<<1, RED_T, 0, st>>>(k->part, k->nblk, k->dsc, &k->stat_d[k->m + 1].rr);
     MCMG_CHECK_LAUNCH("reduce_res");
     MCMG_CUDA(cudaStreamSynchronize(st));
     Stat sv;
-    std::memcpy(&sv, (const void*)k->stat_h, sizeof(Stat));
+    std::memcpy(&sv, (const void*)(k->stat_h + k->m + 1), sizeof(Stat));
     if (fnorm < 0.0) fnorm = std::sqrt(sv.ff);
     rel = fnorm > 0.0 ? std::sqrt(sv.rr) / fnorm : 0.0;
     if (!std::isfinite(rel)) { fs = MCMG_ERR_NUMERIC; break; }
@@ -688,7 +712,8 @@ mcmg_status block_begin(KrylovBlock* b, const double2* f, double2* u, const mcmg
 // Read one member's results of the last round and decide its next stage.
 static mcmg_status member_process(Krylov* k) {
   Stat st;
-  std::memcpy(&st, (const void*)k->stat_h, sizeof(Stat));
+  const int slot = k->phase == Krylov::WAIT_RES ? k->m + 1 : k->j;
+  std::memcpy(&st, (const void*)(k->stat_h + slot), sizeof(Stat));
   if (k->h->err_host && *(volatile int*)k->h->err_host) {
     set_error("a bounded wait in a tensor-core kernel ran out (code %d)", *k->h->err_host);
     finish(k, false, MCMG_ERR_TIMEOUT);
@@ -761,7 +786,7 @@ mcmg_status block_advance(KrylovBlock* b, bool blocking, int* done) {
                               cudaMemcpyHostToDevice, b->st));
     MCMG_TRY(vcycle_run_batch(b->h, b->vw, b->ptr_d, b->ptr_d + b->nb, count, b->st));
     for (Krylov* k : b->ks)
-      if (k->phase == Krylov::NEED_STEP) MCMG_TRY(enqueue_arnoldi(k));
+      if (k->phase == Krylov::NEED_STEP) MCMG_TRY(enqueue_arnoldi(k, k->j));
   }
   bool all = true;
   for (Krylov* k : b->ks) all = all && k->phase == Krylov::DONE;

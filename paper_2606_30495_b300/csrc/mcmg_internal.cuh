@@ -92,7 +92,10 @@ struct Level {
   float2* Rt = nullptr;       // [T3][C][Cn]
   float2* Pt = nullptr;       // [T3][Cn][C]
   bool use_tc = false;        // smoothing step on tcgen05 (BF16 mixing)
-  int shape[2] = {-1, -1};    // CUDA-core smoothing thread shape per mode (autotuned)
+  // CUDA-core kernel shape per operation in use (0 smoothing step, 1 residual,
+  // 2 restriction, 3 prolongation) and the autotuner's choice
+  int shape[4] = {-1, -1, -1, -1};
+  int tuned[4] = {-1, -1, -1, -1};
   TcWeights tcw;
   int* err = nullptr;         // device view of the handle's error word
 };
@@ -113,6 +116,12 @@ mcmg_status launch_restrict(const Level& L, const float2* t, float2* rc, int nrh
 // Time the thread shapes of the CUDA-core smoothing kernel on level L and keep
 // the fastest per mode (r, e, out: scratch fields of nodes * C elements).
 mcmg_status autotune_smooth(Level& L, float2* r, float2* e, float2* out, cudaStream_t st);
+// Transfer shapes of level L (fine, coarse: scratch fields), timed at setup.
+mcmg_status autotune_transfer(Level& L, float2* fine, float2* coarse, cudaStream_t st);
+// Number of kernel shapes of an operation (0 smoothing step, 1 residual,
+// 2 restriction, 3 prolongation), and whether one can run on level L.
+int kernel_shape_count(int op);
+bool kernel_shape_valid(const Level& L, int op, int shape);
 mcmg_status launch_prolong_add(const Level& L, const float2* ec, float2* e, int nrhs,
                                cudaStream_t st);
 mcmg_status launch_lift(const float2* r, const float2* lift, float2* r1, int C, long long nodes,
@@ -171,6 +180,7 @@ struct VWork {
   unsigned long long graph_kernels = 0;  // kernel nodes in the graph
   // graphs of the level sequence for fewer fields (batched solves), by count
   std::map<int, std::pair<cudaGraphExec_t, unsigned long long>> sub;
+  unsigned shape_gen = 0;            // handle's shape generation the graphs were captured at
   DevArena arena;
 };
 
@@ -243,4 +253,5 @@ struct mcmg_handle_s {
   std::mutex mu;                // serialises synchronous use of work / kry
   int* err_host = nullptr;      // error word, mapped pinned (bounded waits that ran out)
   int* err_dev = nullptr;
+  unsigned shape_gen = 0;       // bumped when a smoothing shape is overridden
 };

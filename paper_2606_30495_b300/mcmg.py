@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libmcmg.so")
 
 MAX_LEVELS = 8
 MCMG_OK, MCMG_PENDING = 0, 1
+MCMG_ERR_SHAPE = -2
 STATUS = {0: "OK", 1: "PENDING", -1: "ERR_ARG", -2: "ERR_SHAPE", -3: "ERR_OOM", -4: "ERR_CUDA",
           -5: "ERR_NOT_CONVERGED", -6: "ERR_TIMEOUT", -7: "ERR_NUMERIC", -8: "ERR_BUSY"}
 FP32, BF16 = 0, 1
@@ -83,6 +84,9 @@ _SIGS = {
     "mcmg_cgs2": [_P, _P, C.c_int, C.c_size_t, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "mcmg_cgs2_noalloc": [_P, C.c_int, C.c_size_t, _P, C.POINTER(C.c_double),
                           C.POINTER(C.c_double), _P],
+    "mcmg_kernel_shape_count": [C.c_int],
+    "mcmg_get_kernel_shape": [_P, C.c_int, C.c_int, C.POINTER(C.c_int)],
+    "mcmg_set_kernel_shape": [_P, C.c_int, C.c_int, C.c_int],
     "mcmg_kernel_launches": [],
     "mcmg_last_error": [],
     "mcmg_version": [],
@@ -135,6 +139,14 @@ def ptr(t) -> int:
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return t.data_ptr()
+
+
+# operations with interchangeable kernel shapes
+OP_SMOOTH, OP_RESIDUAL, OP_RESTRICT, OP_PROLONG = 0, 1, 2, 3
+
+
+def kernel_shape_count(op: int) -> int:
+    return int(load().mcmg_kernel_shape_count(op))
 
 
 def kernel_launches() -> int:
@@ -279,6 +291,20 @@ class Handle:
         if st not in (MCMG_OK, -5):
             _check(st)
         return st, info.as_dict()
+
+    def kernel_shape(self, level, op=0) -> int:
+        v = C.c_int()
+        _check(self.lib.mcmg_get_kernel_shape(self.h, level, op, C.byref(v)))
+        return v.value
+
+    def set_kernel_shape(self, level, op, shape) -> bool:
+        """Use CUDA-core shape `shape` for operation op (-1: setup's choice).
+        False when the shape cannot run on this level's channels."""
+        st = self.lib.mcmg_set_kernel_shape(self.h, level, op, shape)
+        if st == MCMG_ERR_SHAPE:
+            return False
+        _check(st)
+        return True
 
     def device_error(self) -> int:
         v = C.c_int()

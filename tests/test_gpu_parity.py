@@ -147,6 +147,88 @@ def test_residual_restrict_and_prolong(case):
         assert relerr(host(ef), want) < TOL32
 
 
+def test_every_kernel_shape(case):
+    """Every CUDA-core kernel and thread shape of the four V-cycle operations
+    against the oracle: the smoothing step (with e and with e = 0), the
+    residual, the restriction and the prolongation.  Setup's autotuner picks
+    among them by timing, so each must be exact on its own; grids here leave
+    ragged last blocks for every shape."""
+    from paper_2606_30495_b300 import mcmg
+    m, h = case
+    w = m["w"]
+    L = w["levels"]
+    ran = {op: set() for op in range(4)}
+    try:
+        for l in range(L):
+            C = w["channels"][l]
+            shp = tuple(n >> l for n in m["shape"]) + (C,)
+            a, s = m["feats"][l]
+            lv = w["lvl"][l]
+            step = w["nu_pre"][l] + w["nu_post"][l] - 1
+            r = I.complex_normal((2,) + shp, rng(50))
+            e_in = I.complex_normal((2,) + shp, rng(51))
+            want = np.stack([e_in[k] + O.op_S(lv, s, step, r[k] - O.op_A(lv, a, e_in[k]))
+                             for k in range(2)])
+            want0 = np.stack([O.op_S(lv, s, 0, r[k]) for k in range(2)])
+            for sh in range(mcmg.kernel_shape_count(mcmg.OP_SMOOTH)):
+                if not h.set_kernel_shape(l, mcmg.OP_SMOOTH, sh):
+                    continue
+                ran[0].add(sh)
+                out = torch.zeros(r.shape, dtype=torch.complex64, device="cuda")
+                h.smooth(l, step, dev(r), dev(e_in), out, nrhs=2)
+                assert relerr(host(out), want) < TOL32, (l, sh)
+                out.zero_()
+                h.smooth(l, 0, dev(r), None, out, nrhs=2)
+                assert relerr(host(out), want0) < TOL32, (l, sh, "e = 0")
+            h.set_kernel_shape(l, mcmg.OP_SMOOTH, -1)
+            if l == L - 1:
+                continue
+            cshp = tuple(n >> (l + 1) for n in m["shape"]) + (w["channels"][l + 1],)
+            want_rc = np.stack([O.restrict(lv["R"], r[k] - O.op_A(lv, a, e_in[k])) for k in range(2)])
+            for op in (mcmg.OP_RESIDUAL, mcmg.OP_RESTRICT):
+                for sh in range(mcmg.kernel_shape_count(op)):
+                    if not h.set_kernel_shape(l, op, sh):
+                        continue
+                    ran[op].add(sh)
+                    rc = torch.zeros((2,) + cshp, dtype=torch.complex64, device="cuda")
+                    h.residual_restrict(l, dev(r), dev(e_in), rc, nrhs=2)
+                    assert relerr(host(rc), want_rc) < TOL32, (l, op, sh)
+                h.set_kernel_shape(l, op, -1)
+            ec = I.complex_normal((2,) + cshp, rng(53))
+            want_p = np.stack([e_in[k] + O.prolong(lv["P"], ec[k], shp[:-1]) for k in range(2)])
+            for sh in range(mcmg.kernel_shape_count(mcmg.OP_PROLONG)):
+                if not h.set_kernel_shape(l, mcmg.OP_PROLONG, sh):
+                    continue
+                ran[3].add(sh)
+                ef = dev(e_in)
+                h.prolong_add(l, dev(ec), ef, nrhs=2)
+                assert relerr(host(ef), want_p) < TOL32, (l, "prolong", sh)
+            h.set_kernel_shape(l, mcmg.OP_PROLONG, -1)
+        assert len(ran[0]) >= 3 and len(ran[1]) >= 3 and 0 in ran[2] and 0 in ran[3]
+        if max(w["channels"]) >= 4:
+            assert ran[0] & set(range(6, mcmg.kernel_shape_count(0))), "no register-tiled smoothing"
+        pairs = [(w["channels"][l], w["channels"][l + 1]) for l in range(L - 1)]
+        if any(cf >= 4 and cc in (cf, 2 * cf) for cf, cc in pairs):
+            assert len(ran[2]) > 1 and len(ran[3]) > 1, "no register-tiled transfer"
+        # V-cycles with the register-tiled shapes forced on every level and
+        # operation (the captured graph must follow each change)
+        rv = I.complex_normal((2,) + m["shape"], rng(52))
+        want_v = np.stack([O.vcycle(w, m["feats"], ri) for ri in rv])
+        for k in range(1, 7):
+            for l in range(L):
+                for op in range(4 if l < L - 1 else 2):
+                    n_op = mcmg.kernel_shape_count(op)
+                    sh = (5 + k) % n_op if op < 2 else k % n_op
+                    h.set_kernel_shape(l, op, sh)
+            ev = torch.zeros(rv.shape, dtype=torch.complex64, device="cuda")
+            h.vcycle(dev(rv), ev, nrhs=2)
+            assert relerr(host(ev), want_v) < TOL32, k
+    finally:
+        for l in range(L):
+            for op in range(4 if l < L - 1 else 2):
+                h.set_kernel_shape(l, op, -1)
+
+
 def test_vcycle_and_batch(case):
     m, h = case
     r = I.complex_normal((3,) + m["shape"], rng(40))
