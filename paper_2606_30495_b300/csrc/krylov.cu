@@ -4,9 +4,12 @@
 // Precision split: the Krylov basis V and the preconditioned vectors Z are
 // complex64 (the V-cycle's input and output precision).  The Arnoldi work
 // vector w = A z_j is formed in FP64 from the complex64 z_j and stays FP64
-// through Gram-Schmidt; every inner product and norm accumulates in FP64; the
-// Hessenberg matrix, Givens rotations and least-squares solve are FP64; the
-// solution u and the true residual f - A u (at every restart) are complex128.
+// through Gram-Schmidt; every inner product, update and norm accumulates in
+// double-float (FP64-class, 48 significand bits, on the FP32 units) and the
+// block partials in FP64.  The Hessenberg matrix, Givens rotations and the
+// least-squares solve are FP64 on the host, fed by the step's inner products
+// (mirrored to mapped memory).  The solution u and the true residual f - A u
+// (at every restart) are complex128.
 // Forming A z in FP32 would lose up to ||A|| ||z|| / ||A z|| times the FP32
 // rounding, which for an indefinite Helmholtz operator and a preconditioned
 // z is large enough to separate the implicit and true residuals.
@@ -15,11 +18,12 @@
 //
 // The solve is a resumable state machine so that a server can interleave many
 // solves on separate streams: every stage enqueues device work, records an
-// event, and the host reads the few scalars it needs (residual estimates)
+// event, and the host reads the few scalars it needs (inner products, norms)
 // from mapped pinned memory once the event has completed.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <complex>
 #include <cstring>
 
 #include "mcmg_internal.cuh"
@@ -44,44 +48,98 @@ __device__ __forceinline__ void store_w(double2* p, double re, double im) {
   *p = make_double2(re, im);
 }
 
+// ---- double-float arithmetic ----------------------------------------------
+// FP64 arithmetic on this part runs at a small fraction of the FP32 rate, so
+// the Gram-Schmidt inner products and updates carry FP64-class precision as
+// double-float numbers: an unevaluated sum hi + lo of two FP32 values (48
+// significand bits).  Products of an FP32 value and a double-float are exact
+// up to the lo * lo term through the FMA (Dekker's product); sums use Knuth's
+// two-sum.  The correctly rounded intrinsics keep the compiler from fusing
+// or reassociating the error-free transformations.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// x += y
+__device__ __forceinline__ void df_add(DF& x, DF y) {
+  const DF s = df_two_sum(x.hi, y.hi);
+  const float lo = __fadd_rn(__fadd_rn(s.lo, x.lo), y.lo);
+  const float hi = __fadd_rn(s.hi, lo);
+  x = {hi, __fsub_rn(lo, __fsub_rn(hi, s.hi))};
+}
+// a * (bh + bl) for an FP32 a
+__device__ __forceinline__ DF df_mul(float a, float bh, float bl) {
+  const float p = __fmul_rn(a, bh);
+  return {p, __fmaf_rn(a, bl, __fmaf_rn(a, bh, -p))};
+}
+__device__ __forceinline__ DF df_from(double v) {
+  const float h = __double2float_rn(v);
+  return {h, __double2float_rn(v - (double)h)};
+}
+__device__ __forceinline__ DF df_from(float v) { return {v, 0.f}; }
+__device__ __forceinline__ double df_to(DF x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ DF df_shfl_xor(DF x, int o) {
+  return {__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+}
+// x^2 for a double-float x (the lo^2 term, 2^-48 relative, dropped)
+__device__ __forceinline__ DF df_sq(DF x) { return df_mul(x.hi, x.hi, __fmul_rn(2.f, x.lo)); }
+
 // part[(bx * ktot + i) * 2 + {0,1}] = sum over this block's range of conj(v_i) w,
-// v_i = V[i * ldv + .] for i < k, v_k = w when ktot = k + 1.
+// v_i = V[i * ldv + .] for i < k, v_k = w when ktot = k + 1.  Double-float
+// accumulation; block partials in a fixed order, written as FP64.
 template <typename WT>
 __global__ void __launch_bounds__(RED_T) k_multidot(const float2* __restrict__ V, long long ldv,
                                                     int k, int ktot, const WT* __restrict__ w,
                                                     long long n, double* __restrict__ part) {
   const int i0 = blockIdx.y * KV;
-  double ar[KV], ai[KV];
+  DF ar[KV], ai[KV];
 #pragma unroll
-  for (int i = 0; i < KV; ++i) ar[i] = ai[i] = 0.0;
+  for (int i = 0; i < KV; ++i) ar[i] = ai[i] = DF{0.f, 0.f};
   for (long long p = (long long)blockIdx.x * RED_T + threadIdx.x; p < n;
        p += (long long)gridDim.x * RED_T) {
-    const double2 wd = to_d2(w[p]);
-    const double wr = wd.x, wi = wd.y;
+    const WT wv = w[p];
+    const DF wx = df_from(wv.x), wy = df_from(wv.y);
 #pragma unroll
     for (int i = 0; i < KV; ++i) {
       const int ii = i0 + i;
-      if (ii < ktot) {
-        const double2 v = ii < k ? to_d2(V[(long long)ii * ldv + p]) : wd;
-        ar[i] += v.x * wr + v.y * wi;
-        ai[i] += v.x * wi - v.y * wr;
+      if (ii < k) {
+        const float2 v = V[(long long)ii * ldv + p];
+        // conj(v) w = (vx wx + vy wy) + i (vx wy - vy wx)
+        df_add(ar[i], df_mul(v.x, wx.hi, wx.lo));
+        df_add(ar[i], df_mul(v.y, wy.hi, wy.lo));
+        df_add(ai[i], df_mul(v.x, wy.hi, wy.lo));
+        df_add(ai[i], df_mul(-v.y, wx.hi, wx.lo));
+      } else if (ii < ktot) {  // |w|^2
+        df_add(ar[i], df_sq(wx));
+        df_add(ar[i], df_sq(wy));
       }
     }
   }
-  __shared__ double sh[RED_T / 32][KV][2];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // 2 KV values per thread: through shared memory, warp q sums values 2q, 2q+1
+  static_assert(2 * KV == 2 * (RED_T / 32), "one warp per pair of values");
+  __shared__ DF sh[2 * KV][RED_T];
 #pragma unroll
   for (int i = 0; i < KV; ++i) {
-    double a = warp_sum_d(ar[i]), b = warp_sum_d(ai[i]);
-    if (lane == 0) { sh[wid][i][0] = a; sh[wid][i][1] = b; }
+    sh[2 * i][threadIdx.x] = ar[i];
+    sh[2 * i + 1][threadIdx.x] = ai[i];
   }
   __syncthreads();
-  if (threadIdx.x < KV && i0 + (int)threadIdx.x < ktot) {
-    double a = 0.0, b = 0.0;
-    for (int q = 0; q < RED_T / 32; ++q) { a += sh[q][threadIdx.x][0]; b += sh[q][threadIdx.x][1]; }
-    size_t o = ((size_t)blockIdx.x * ktot + i0 + threadIdx.x) * 2;
-    part[o] = a;
-    part[o + 1] = b;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int val = 2 * wid + c;
+    DF acc = sh[val][lane];
+#pragma unroll
+    for (int q = 1; q < RED_T / 32; ++q) df_add(acc, sh[val][lane + 32 * q]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) df_add(acc, df_shfl_xor(acc, o));
+    const int vec = i0 + val / 2;
+    if (lane == 0 && vec < ktot) part[((size_t)blockIdx.x * ktot + vec) * 2 + (val & 1)] = df_to(acc);
   }
 }
 
@@ -101,8 +159,10 @@ __device__ __forceinline__ double2 block_sum2(double a, double b) {
 }
 
 // out[i] = sum_b part[(b * width + i) * 2 + {0,1}]; one block per output i.
+// out_host (mapped host memory, may be null) receives a copy.
 __global__ void __launch_bounds__(RED_T) k_reduce_parts(const double* __restrict__ part, int nblk,
-                                                        int width, double2* __restrict__ out) {
+                                                        int width, double2* __restrict__ out,
+                                                        double2* out_host) {
   const int i = blockIdx.x;
   double a = 0.0, b = 0.0;
   for (int q = threadIdx.x; q < nblk; q += RED_T) {
@@ -110,47 +170,85 @@ __global__ void __launch_bounds__(RED_T) k_reduce_parts(const double* __restrict
     b += part[((size_t)q * width + i) * 2 + 1];
   }
   const double2 r = block_sum2(a, b);
-  if (threadIdx.x == 0) out[i] = r;
+  if (threadIdx.x == 0) {
+    out[i] = r;
+    if (out_host) out_host[i] = r;
+  }
 }
 
-// w -= sum_{i<k} h_i V_i  (FP64 accumulation per element); part[bx] = sum |w|^2.
+// w -= sum_{i<k} h_i V_i (double-float accumulation per element, the
+// difference taken in w's precision); part[bx] = sum |w|^2 over the block's
+// elements.  h is split into double-float pairs once per block, in dynamic
+// shared memory (k * 16 bytes).
 template <typename WT>
 __global__ void __launch_bounds__(RED_T) k_update(const float2* __restrict__ V, long long ldv, int k,
                                                   const double2* __restrict__ hc,
                                                   WT* __restrict__ w, long long n,
                                                   double* __restrict__ part) {
-  double nn = 0.0;
+  extern __shared__ DF hs[];   // [k][2]
+  for (int i = threadIdx.x; i < k; i += RED_T) {
+    const double2 hh = hc[i];
+    hs[2 * i] = df_from(hh.x);
+    hs[2 * i + 1] = df_from(hh.y);
+  }
+  __syncthreads();
+  DF nn{0.f, 0.f};
   for (long long p = (long long)blockIdx.x * RED_T + threadIdx.x; p < n;
        p += (long long)gridDim.x * RED_T) {
-    double sr = 0.0, si = 0.0;
+    DF sr{0.f, 0.f}, si{0.f, 0.f};
     for (int i = 0; i < k; ++i) {
       const float2 v = V[(long long)i * ldv + p];
-      const double2 hh = hc[i];
-      sr += hh.x * v.x - hh.y * v.y;
-      si += hh.x * v.y + hh.y * v.x;
+      const DF hx = hs[2 * i], hy = hs[2 * i + 1];
+      // h v = (hx vx - hy vy) + i (hx vy + hy vx)
+      df_add(sr, df_mul(v.x, hx.hi, hx.lo));
+      df_add(sr, df_mul(-v.y, hy.hi, hy.lo));
+      df_add(si, df_mul(v.y, hx.hi, hx.lo));
+      df_add(si, df_mul(v.x, hy.hi, hy.lo));
     }
     const double2 wd = to_d2(w[p]);
-    store_w(w + p, wd.x - sr, wd.y - si);
+    store_w(w + p, wd.x - df_to(sr), wd.y - df_to(si));
     const double2 o = to_d2(w[p]);
-    nn += o.x * o.x + o.y * o.y;
+    df_add(nn, df_sq(df_from(o.x)));
+    df_add(nn, df_sq(df_from(o.y)));
   }
-  __shared__ double sh[RED_T / 32];
-  nn = warp_sum_d(nn);
+  __shared__ DF sh[RED_T / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) df_add(nn, df_shfl_xor(nn, o));
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nn;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int q = 0; q < RED_T / 32; ++q) a += sh[q];
-    part[blockIdx.x] = a;
+    DF a = sh[0];
+    for (int q = 1; q < RED_T / 32; ++q) df_add(a, sh[q]);
+    part[blockIdx.x] = df_to(a);
   }
 }
 
+// Launch of k_update with its shared memory for k coefficients.
+template <typename WT>
+static mcmg_status launch_update(const float2* V, long long ldv, int k, const double2* hc, WT* w,
+                                 long long n, double* part, int nblk, cudaStream_t st) {
+  const size_t smem = (size_t)k * 2 * sizeof(DF);
+  if (smem > 227 * 1024) {
+    set_error("Gram-Schmidt against %d vectors exceeds shared memory", k);
+    return MCMG_ERR_SHAPE;
+  }
+  if (smem > 48 * 1024)
+    MCMG_CUDA(cudaFuncSetAttribute(k_update<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  k_update<WT><<<nblk, RED_T, smem, st>>>(V, ldv, k, hc, w, n, part);
+  MCMG_CHECK_LAUNCH("update");
+  return MCMG_OK;
+}
+
 __global__ void __launch_bounds__(RED_T) k_reduce_scalar(const double* __restrict__ part, int nblk,
-                                                         double* out) {
+                                                         double* out, double* out_host) {
   double a = 0.0;
   for (int q = threadIdx.x; q < nblk; q += RED_T) a += part[q];
   const double2 r = block_sum2(a, 0.0);
-  if (threadIdx.x == 0) *out = r.x;
+  if (threadIdx.x == 0) {
+    *out = r.x;
+    if (out_host) *out_host = r.x;
+  }
 }
 
 // Residual partials [nblk][2] -> rr, ff
@@ -168,10 +266,9 @@ __global__ void __launch_bounds__(RED_T) k_reduce_res(const double* __restrict__
   }
 }
 
-// v0 = r / beta (to complex64), g = (beta, 0, ...)
+// v0 = r / beta (to complex64)
 __global__ void k_start_cycle(const double2* __restrict__ r, const double* __restrict__ dsc,
-                              float2* __restrict__ v0, long long n, double2* __restrict__ g,
-                              int m) {
+                              float2* __restrict__ v0, long long n) {
   const double beta = sqrt(dsc[0]);
   const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -179,60 +276,11 @@ __global__ void k_start_cycle(const double2* __restrict__ r, const double* __res
     const double2 v = r[p];
     v0[p] = make_float2((float)(v.x * inv), (float)(v.y * inv));
   }
-  if (p <= m) g[p] = make_double2(p == 0 ? beta : 0.0, 0.0);
 }
 
 struct Stat {
-  double res;     // |g_{j+1}|
-  double hn;      // h_{j+1, j}
-  double w0;      // ||A z_j|| before orthogonalisation
   double rr, ff;  // |f - A u|^2, |f|^2 at the last restart
 };
-
-// Hessenberg column j = dots + dots2, h_{j+1,j} = sqrt(nrm2); previous Givens
-// rotations, new rotation, rhs update.  One thread.
-__global__ void k_givens(int j, int m, const double2* __restrict__ d1, const double2* __restrict__ d2,
-                         const double* __restrict__ dsc, double2* __restrict__ H, double* cs,
-                         double2* sn, double2* g, Stat* st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double2* col = H + (size_t)j * (m + 1);
-  for (int i = 0; i <= j; ++i) col[i] = make_double2(d1[i].x + d2[i].x, d1[i].y + d2[i].y);
-  const double hn = sqrt(dsc[3]);
-  col[j + 1] = make_double2(hn, 0.0);
-  for (int i = 0; i < j; ++i) {
-    const double2 h0 = col[i], h1 = col[i + 1];
-    const double c = cs[i];
-    const double2 s = sn[i];
-    // [c, s; -conj(s), c] applied to (h0, h1)
-    col[i] = make_double2(c * h0.x + s.x * h1.x - s.y * h1.y, c * h0.y + s.x * h1.y + s.y * h1.x);
-    col[i + 1] = make_double2(-(s.x * h0.x + s.y * h0.y) + c * h1.x,
-                              -(s.x * h0.y - s.y * h0.x) + c * h1.y);
-  }
-  const double2 a = col[j], b = col[j + 1];
-  const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
-  const double rho = hypot(aa, bb);
-  double c;
-  double2 s;
-  if (aa == 0.0) {
-    c = 0.0;
-    s = make_double2(1.0, 0.0);
-  } else {
-    c = aa / rho;
-    // s = (a / |a|) conj(b) / rho
-    const double2 ua = make_double2(a.x / aa, a.y / aa);
-    s = make_double2((ua.x * b.x + ua.y * b.y) / rho, (ua.y * b.x - ua.x * b.y) / rho);
-  }
-  cs[j] = c;
-  sn[j] = s;
-  col[j] = make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
-  col[j + 1] = make_double2(0.0, 0.0);
-  const double2 gj = g[j];
-  g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
-  g[j] = make_double2(c * gj.x, c * gj.y);
-  st->res = hypot(g[j + 1].x, g[j + 1].y);
-  st->hn = hn;
-  st->w0 = sqrt(d1[j + 1].x);
-}
 
 // v_{j+1} = w / sqrt(nrm2)
 __global__ void k_scale(const double2* __restrict__ w, const double* __restrict__ dsc,
@@ -254,33 +302,6 @@ __global__ void k_stationary_update(const float2* __restrict__ z, const double* 
   const float2 zz = z[p];
   const double2 o = u[p];
   u[p] = make_double2(o.x + beta * zz.x, o.y + beta * zz.y);
-}
-
-// y = R^{-1} g for the k x k upper triangle of the rotated Hessenberg matrix.
-__global__ void __launch_bounds__(1024) k_backsolve(const double2* __restrict__ H, int m, int k,
-                                                    const double2* __restrict__ g,
-                                                    double2* __restrict__ gw,
-                                                    double2* __restrict__ y) {
-  for (int l = threadIdx.x; l < k; l += blockDim.x) gw[l] = g[l];
-  __syncthreads();
-  __shared__ double2 yi;
-  for (int i = k - 1; i >= 0; --i) {
-    if (threadIdx.x == 0) {
-      const double2 d = H[(size_t)i * (m + 1) + i];
-      const double2 num = gw[i];
-      const double den = d.x * d.x + d.y * d.y;
-      yi = make_double2((num.x * d.x + num.y * d.y) / den, (num.y * d.x - num.x * d.y) / den);
-      y[i] = yi;
-    }
-    __syncthreads();
-    const double2 v = yi;
-    const double2* col = H + (size_t)i * (m + 1);
-    for (int l = threadIdx.x; l < i; l += blockDim.x) {
-      const double2 hc = col[l];
-      gw[l] = make_double2(gw[l].x - (hc.x * v.x - hc.y * v.y), gw[l].y - (hc.x * v.y + hc.y * v.x));
-    }
-    __syncthreads();
-  }
 }
 
 // u += sum_{i<k} y_i Z_i (complex128 accumulate)
@@ -313,14 +334,19 @@ struct Krylov {
   double* part = nullptr;
   double2* d1 = nullptr;
   double2* d2 = nullptr;
-  double2* H = nullptr;
-  double* cs = nullptr;
-  double2* sn = nullptr;
-  double2* g = nullptr;
-  double2* gw = nullptr;
-  double2* y = nullptr;
+  double2* y = nullptr;             // device copy of the least-squares solution
+  // Host side of the Arnoldi process (FP64): Hessenberg columns, Givens
+  // rotations, rotated right-hand side, and the least-squares solution.
+  std::vector<std::complex<double>> Hh, sn, g;
+  std::vector<double> cs;
+  double2* y_h = nullptr;           // pinned staging of y
+  // per Arnoldi step j, mapped: [0, m+2) first-pass dots (with |w|^2 last),
+  // [m+2, 2m+4) second-pass dots, [2m+4].x = ||w||^2 after Gram-Schmidt
+  double2* mir_h = nullptr;
+  double2* mir_d = nullptr;
+  int mir_stride = 0;
   double* dsc = nullptr;
-  Stat* stat_h = nullptr;   // mapped pinned: [0, m) per Arnoldi step, [m + 1] restart
+  Stat* stat_h = nullptr;   // mapped pinned: the restart residual
   Stat* stat_d = nullptr;
   cudaEvent_t ev = nullptr;         // restart residual ready
   cudaEvent_t evs[2] = {};          // Arnoldi step j ready: evs[j & 1]
@@ -366,11 +392,6 @@ mcmg_status krylov_create(mcmg_handle_s* h, int m, Krylov** out, bool own_vcycle
       (s = A((void**)&k->part, sizeof(double) * 2 * (size_t)k->nblk * (m + 2))) ||
       (s = A((void**)&k->d1, sizeof(double2) * (m + 2))) ||
       (s = A((void**)&k->d2, sizeof(double2) * (m + 2))) ||
-      (s = A((void**)&k->H, sizeof(double2) * (size_t)m * (m + 1))) ||
-      (s = A((void**)&k->cs, sizeof(double) * (m + 1))) ||
-      (s = A((void**)&k->sn, sizeof(double2) * (m + 1))) ||
-      (s = A((void**)&k->g, sizeof(double2) * (m + 2))) ||
-      (s = A((void**)&k->gw, sizeof(double2) * (m + 2))) ||
       (s = A((void**)&k->y, sizeof(double2) * (m + 1))) ||
       (s = A((void**)&k->dsc, sizeof(double) * 8))) {
     krylov_destroy(h, k);
@@ -380,8 +401,18 @@ mcmg_status krylov_create(mcmg_handle_s* h, int m, Krylov** out, bool own_vcycle
     krylov_destroy(h, k);
     return s;
   }
-  cudaError_t e = cudaHostAlloc((void**)&k->stat_h, sizeof(Stat) * (m + 2), cudaHostAllocMapped);
+  k->Hh.assign((size_t)m * (m + 1), 0.0);
+  k->sn.assign(m + 1, 0.0);
+  k->g.assign(m + 2, 0.0);
+  k->cs.assign(m + 1, 0.0);
+  k->mir_stride = 2 * m + 5;
+  cudaError_t e = cudaHostAlloc((void**)&k->stat_h, sizeof(Stat), cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&k->stat_d, k->stat_h, 0);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc((void**)&k->mir_h, sizeof(double2) * (size_t)m * k->mir_stride,
+                      cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&k->mir_d, k->mir_h, 0);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&k->y_h, sizeof(double2) * (m + 1), cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&k->ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&k->evs[0], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&k->evs[1], cudaEventDisableTiming);
@@ -399,6 +430,8 @@ void krylov_destroy(mcmg_handle_s* h, Krylov* k) {
   if (k->vw) vwork_destroy(h, k->vw);
   arena_free(h, k->arena);
   if (k->stat_h) cudaFreeHost(k->stat_h);
+  if (k->mir_h) cudaFreeHost(k->mir_h);
+  if (k->y_h) cudaFreeHost(k->y_h);
   if (k->ev) cudaEventDestroy(k->ev);
   for (cudaEvent_t e : k->evs)
     if (e) cudaEventDestroy(e);
@@ -410,19 +443,19 @@ void krylov_destroy(mcmg_handle_s* h, Krylov* k) {
 static mcmg_status enqueue_restart(Krylov* k) {
   mcmg_handle_s* h = k->h;
   MCMG_TRY(launch_residual64(h->q64, k->f, k->u, k->r64, k->part, k->nblk, h->g0, 1, k->st));
-  k_reduce_res<<<1, RED_T, 0, k->st>>>(k->part, k->nblk, k->dsc, &k->stat_d[k->m + 1].rr);
+  k_reduce_res<<<1, RED_T, 0, k->st>>>(k->part, k->nblk, k->dsc, &k->stat_d->rr);
   MCMG_CHECK_LAUNCH("reduce_res");
   MCMG_CUDA(cudaEventRecord(k->ev, k->st));
   k->phase = Krylov::WAIT_RES;
   return MCMG_OK;
 }
 
-static mcmg_status multidot(Krylov* k, int nv, bool self, double2* out) {
+static mcmg_status multidot(Krylov* k, int nv, bool self, double2* out, double2* out_host) {
   const int ktot = nv + (self ? 1 : 0);
   dim3 grid((unsigned)k->nblk, (unsigned)((ktot + KV - 1) / KV));
   k_multidot<double2><<<grid, RED_T, 0, k->st>>>(k->V, k->n, nv, ktot, k->w, k->n, k->part);
   MCMG_CHECK_LAUNCH("multidot");
-  k_reduce_parts<<<ktot, RED_T, 0, k->st>>>(k->part, k->nblk, ktot, out);
+  k_reduce_parts<<<ktot, RED_T, 0, k->st>>>(k->part, k->nblk, ktot, out, out_host);
   MCMG_CHECK_LAUNCH("reduce_parts");
   return MCMG_OK;
 }
@@ -434,17 +467,14 @@ static mcmg_status enqueue_arnoldi(Krylov* k, int j) {
   const long long n = k->n;
   float2* zj = k->Z + (size_t)j * n;
   MCMG_TRY(launch_apply_A_mixed(h->q64, zj, k->w, h->g0, 1, k->st));
-  MCMG_TRY(multidot(k, j + 1, true, k->d1));
-  k_update<double2><<<k->nblk, RED_T, 0, k->st>>>(k->V, n, j + 1, k->d1, k->w, n, k->part);
-  MCMG_CHECK_LAUNCH("update");
-  MCMG_TRY(multidot(k, j + 1, false, k->d2));
-  k_update<double2><<<k->nblk, RED_T, 0, k->st>>>(k->V, n, j + 1, k->d2, k->w, n, k->part);
-  MCMG_CHECK_LAUNCH("update");
-  k_reduce_scalar<<<1, RED_T, 0, k->st>>>(k->part, k->nblk, k->dsc + 3);
+  double2* mir = k->mir_d + (size_t)j * k->mir_stride;
+  MCMG_TRY(multidot(k, j + 1, true, k->d1, mir));
+  MCMG_TRY(launch_update(k->V, n, j + 1, k->d1, k->w, n, k->part, k->nblk, k->st));
+  MCMG_TRY(multidot(k, j + 1, false, k->d2, mir + (k->m + 2)));
+  MCMG_TRY(launch_update(k->V, n, j + 1, k->d2, k->w, n, k->part, k->nblk, k->st));
+  k_reduce_scalar<<<1, RED_T, 0, k->st>>>(k->part, k->nblk, k->dsc + 3,
+                                          &mir[2 * k->m + 4].x);
   MCMG_CHECK_LAUNCH("reduce_scalar");
-  k_givens<<<1, 32, 0, k->st>>>(j, k->m, k->d1, k->d2, k->dsc, k->H, k->cs, k->sn, k->g,
-                                k->stat_d + j);
-  MCMG_CHECK_LAUNCH("givens");
   if (j + 1 <= k->m) {
     k_scale<<<(unsigned)((n + 255) / 256), 256, 0, k->st>>>(k->w, k->dsc, k->V + (size_t)(j + 1) * n, n);
     MCMG_CHECK_LAUNCH("scale");
@@ -463,19 +493,75 @@ static mcmg_status enqueue_step(Krylov* k, int j) {
   return MCMG_OK;
 }
 
-// Step j + 1 may be enqueued before the host has read step j's residual
-// estimate: it only reads v_{j+1} and the rotations, all produced on the
-// device in stream order, and if step j ends the cycle its writes (z_{j+1},
-// column j+1 of H, g_{j+1}, g_{j+2}, v_{j+2}) are never read (the back
-// substitution and update use columns 0..j).  So the device never waits for
-// the host between steps; a cycle that stops early wastes one step.
+// Step j + 1 may be enqueued before the host has read step j's results: it
+// needs only v_{j+1}, produced on the device in stream order, and its own
+// outputs (z_{j+1}, v_{j+2}, its mirrored inner products) are read only if
+// the cycle continues past step j.  So the device never waits for the host
+// between steps; a cycle that stops early wastes one step.
 static bool may_run_ahead(const Krylov* k, int step) {
   return step < k->m && k->iters + (step - k->j) + 1 <= k->max_iters;
 }
 
+// Host side of Arnoldi step j (after its event): Hessenberg column j from the
+// step's mirrored inner products, the previous Givens rotations applied to
+// it, the new rotation, and the rotated right-hand side g.  Returns
+// |g_{j+1}| (the least-squares residual norm), h_{j+1,j} and ||A z_j||.
+static void host_givens(Krylov* k, int j, double* res, double* hn, double* w0) {
+  using cd = std::complex<double>;
+  const int m = k->m;
+  std::vector<double2> buf(k->mir_stride);
+  std::memcpy(buf.data(), (const void*)(k->mir_h + (size_t)j * k->mir_stride),
+              sizeof(double2) * k->mir_stride);
+  const double2* d1 = buf.data();
+  const double2* d2 = buf.data() + (m + 2);
+  const double hnv = std::sqrt(std::max(buf[2 * m + 4].x, 0.0));
+  cd* col = k->Hh.data() + (size_t)j * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = cd(d1[i].x + d2[i].x, d1[i].y + d2[i].y);
+  col[j + 1] = cd(hnv, 0.0);
+  for (int i = 0; i < j; ++i) {   // [c, s; -conj(s), c] applied to (h_i, h_{i+1})
+    const cd h0 = col[i], h1 = col[i + 1];
+    col[i] = k->cs[i] * h0 + k->sn[i] * h1;
+    col[i + 1] = -std::conj(k->sn[i]) * h0 + k->cs[i] * h1;
+  }
+  const cd a = col[j], b = col[j + 1];
+  const double aa = std::abs(a), bb = std::abs(b), rho = std::hypot(aa, bb);
+  double c;
+  cd sv;
+  if (aa == 0.0) {
+    c = 0.0;
+    sv = 1.0;
+  } else {
+    c = aa / rho;
+    sv = (a / aa) * std::conj(b) / rho;
+  }
+  k->cs[j] = c;
+  k->sn[j] = sv;
+  col[j] = c * a + sv * b;
+  col[j + 1] = 0.0;
+  const cd gj = k->g[j];
+  k->g[j + 1] = -std::conj(sv) * gj;
+  k->g[j] = c * gj;
+  *res = std::abs(k->g[j + 1]);
+  *hn = hnv;
+  *w0 = std::sqrt(std::max(d1[j + 1].x, 0.0));
+}
+
+// y = R^{-1} g for the kk x kk upper triangle of the rotated Hessenberg
+// matrix (host, FP64), staged in pinned memory.
+static void host_backsolve(Krylov* k, int kk) {
+  using cd = std::complex<double>;
+  const int m = k->m;
+  std::vector<cd> gw(k->g.begin(), k->g.begin() + kk), y(kk);
+  for (int i = kk - 1; i >= 0; --i) {
+    y[i] = gw[i] / k->Hh[(size_t)i * (m + 1) + i];
+    for (int l = 0; l < i; ++l) gw[l] -= k->Hh[(size_t)i * (m + 1) + l] * y[i];
+  }
+  for (int i = 0; i < kk; ++i) k->y_h[i] = make_double2(y[i].real(), y[i].imag());
+}
+
 static mcmg_status enqueue_finish_cycle(Krylov* k, int kk) {
-  k_backsolve<<<1, 1024, 0, k->st>>>(k->H, k->m, kk, k->g, k->gw, k->y);
-  MCMG_CHECK_LAUNCH("backsolve");
+  host_backsolve(k, kk);
+  MCMG_CUDA(cudaMemcpyAsync(k->y, k->y_h, sizeof(double2) * kk, cudaMemcpyHostToDevice, k->st));
   k_update_x<<<(unsigned)((k->n + 255) / 256), 256, 0, k->st>>>(k->Z, k->n, kk, k->y, k->u, k->n);
   MCMG_CHECK_LAUNCH("update_x");
   k->restarts += 1;
@@ -528,7 +614,7 @@ mcmg_status krylov_advance(Krylov* k, bool blocking, int* done) {
   }
   if (k->phase == Krylov::WAIT_RES) {
     Stat st;
-    std::memcpy(&st, (const void*)(k->stat_h + k->m + 1), sizeof(Stat));
+    std::memcpy(&st, (const void*)k->stat_h, sizeof(Stat));
     if (k->fnorm < 0.0) k->fnorm = std::sqrt(st.ff);
     const double beta = std::sqrt(st.rr);
     if (!std::isfinite(beta)) {
@@ -548,10 +634,10 @@ mcmg_status krylov_advance(Krylov* k, bool blocking, int* done) {
       *done = 1;
       return MCMG_OK;
     }
-    const long long cover = std::max<long long>(k->n, k->m + 1);
-    k_start_cycle<<<(unsigned)((cover + 255) / 256), 256, 0, k->st>>>(k->r64, k->dsc, k->V, k->n,
-                                                                        k->g, k->m);
+    k_start_cycle<<<(unsigned)((k->n + 255) / 256), 256, 0, k->st>>>(k->r64, k->dsc, k->V, k->n);
     MCMG_CHECK_LAUNCH("start_cycle");
+    std::fill(k->g.begin(), k->g.end(), 0.0);
+    k->g[0] = beta;
     k->j = 0;
     k->phase = Krylov::WAIT_STEP;
     MCMG_TRY(enqueue_step(k, 0));
@@ -559,16 +645,16 @@ mcmg_status krylov_advance(Krylov* k, bool blocking, int* done) {
     return MCMG_OK;
   }
   // WAIT_STEP: step j has finished (step j + 1 may be queued behind it)
-  Stat st;
-  std::memcpy(&st, (const void*)(k->stat_h + k->j), sizeof(Stat));
+  double res, hn, w0;
+  host_givens(k, k->j, &res, &hn, &w0);
   k->iters += 1;
-  const double est = st.res / k->fnorm;
+  const double est = res / k->fnorm;
   if (!std::isfinite(est)) {
     finish(k, false, MCMG_ERR_NUMERIC);
     *done = 1;
     return MCMG_OK;
   }
-  const bool stop = est <= k->o.tol || st.hn <= 1e-14 * st.w0 || k->j + 1 >= k->m ||
+  const bool stop = est <= k->o.tol || hn <= 1e-14 * w0 || k->j + 1 >= k->m ||
                     k->iters >= k->max_iters;
   if (stop) return enqueue_finish_cycle(k, k->j + 1);
   k->j += 1;
@@ -607,20 +693,18 @@ mcmg_status stationary_run(Krylov* k, const double2* f, double2* u, const mcmg_s
   bool conv = false;
   for (;; ++it) {
     MCMG_TRY(launch_residual64(h->q64, f, u, k->r64, k->part, k->nblk, h->g0, 1, st));
-    k_reduce_res<<<1, RED_T, 0, st>>>(k->part, k->nblk, k->dsc, &k->stat_d[k->m + 1].rr);
+    k_reduce_res<<<1, RED_T, 0, st>>>(k->part, k->nblk, k->dsc, &k->stat_d->rr);
     MCMG_CHECK_LAUNCH("reduce_res");
     MCMG_CUDA(cudaStreamSynchronize(st));
     Stat sv;
-    std::memcpy(&sv, (const void*)(k->stat_h + k->m + 1), sizeof(Stat));
+    std::memcpy(&sv, (const void*)k->stat_h, sizeof(Stat));
     if (fnorm < 0.0) fnorm = std::sqrt(sv.ff);
     rel = fnorm > 0.0 ? std::sqrt(sv.rr) / fnorm : 0.0;
     if (!std::isfinite(rel)) { fs = MCMG_ERR_NUMERIC; break; }
     if (rel <= o.tol) { conv = true; break; }
     if (it >= max_iters) { fs = MCMG_ERR_NOT_CONVERGED; break; }
     if (h->err_host && *(volatile int*)h->err_host) { fs = MCMG_ERR_TIMEOUT; break; }
-    const long long cover = std::max<long long>(n, k->m + 1);
-    k_start_cycle<<<(unsigned)((cover + 255) / 256), 256, 0, st>>>(k->r64, k->dsc, k->V, n, k->g,
-                                                                   k->m);
+    k_start_cycle<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(k->r64, k->dsc, k->V, n);
     MCMG_CHECK_LAUNCH("start_cycle");
     MCMG_TRY(vcycle_run(h, k->vw, k->V, k->Z, 1, st));
     k_stationary_update<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(k->Z, k->dsc, u, n);
@@ -712,8 +796,7 @@ mcmg_status block_begin(KrylovBlock* b, const double2* f, double2* u, const mcmg
 // Read one member's results of the last round and decide its next stage.
 static mcmg_status member_process(Krylov* k) {
   Stat st;
-  const int slot = k->phase == Krylov::WAIT_RES ? k->m + 1 : k->j;
-  std::memcpy(&st, (const void*)(k->stat_h + slot), sizeof(Stat));
+  std::memcpy(&st, (const void*)k->stat_h, sizeof(Stat));
   if (k->h->err_host && *(volatile int*)k->h->err_host) {
     set_error("a bounded wait in a tensor-core kernel ran out (code %d)", *k->h->err_host);
     finish(k, false, MCMG_ERR_TIMEOUT);
@@ -736,22 +819,24 @@ static mcmg_status member_process(Krylov* k) {
       finish(k, false, MCMG_ERR_NOT_CONVERGED);
       return MCMG_OK;
     }
-    const long long cover = std::max<long long>(k->n, k->m + 1);
-    k_start_cycle<<<(unsigned)((cover + 255) / 256), 256, 0, k->st>>>(k->r64, k->dsc, k->V, k->n,
-                                                                        k->g, k->m);
+    k_start_cycle<<<(unsigned)((k->n + 255) / 256), 256, 0, k->st>>>(k->r64, k->dsc, k->V, k->n);
     MCMG_CHECK_LAUNCH("start_cycle");
+    std::fill(k->g.begin(), k->g.end(), 0.0);
+    k->g[0] = beta;
     k->j = 0;
     k->phase = Krylov::NEED_STEP;
     return MCMG_OK;
   }
   if (k->phase == Krylov::WAIT_STEP) {
+    double res, hn, w0;
+    host_givens(k, k->j, &res, &hn, &w0);
     k->iters += 1;
-    const double est = st.res / k->fnorm;
+    const double est = res / k->fnorm;
     if (!std::isfinite(est)) {
       finish(k, false, MCMG_ERR_NUMERIC);
       return MCMG_OK;
     }
-    const bool stop = est <= k->o.tol || st.hn <= 1e-14 * st.w0 || k->j + 1 >= k->m ||
+    const bool stop = est <= k->o.tol || hn <= 1e-14 * w0 || k->j + 1 >= k->m ||
                       k->iters >= k->max_iters;
     if (stop) return enqueue_finish_cycle(k, k->j + 1);   // -> WAIT_RES
     k->j += 1;
@@ -837,12 +922,11 @@ mcmg_status cgs2_once(mcmg_handle_s* h, const float2* V, int kv, long long n, fl
       double2* dd = pass == 0 ? d1 : d2;
       k_multidot<float2><<<grid, RED_T, 0, st>>>(V, n, kv, kv, w, n, part);
       MCMG_CHECK_LAUNCH("multidot");
-      k_reduce_parts<<<kv, RED_T, 0, st>>>(part, nblk, kv, dd);
+      k_reduce_parts<<<kv, RED_T, 0, st>>>(part, nblk, kv, dd, nullptr);
       MCMG_CHECK_LAUNCH("reduce_parts");
-      k_update<float2><<<nblk, RED_T, 0, st>>>(V, n, kv, dd, w, n, part);
-      MCMG_CHECK_LAUNCH("update");
+      MCMG_TRY(launch_update(V, n, kv, dd, w, n, part, nblk, st));
     }
-    k_reduce_scalar<<<1, RED_T, 0, st>>>(part, nblk, dsc);
+    k_reduce_scalar<<<1, RED_T, 0, st>>>(part, nblk, dsc, nullptr);
     MCMG_CHECK_LAUNCH("reduce_scalar");
     std::vector<double2> a(kv), b(kv);
     double nrm2 = 0.0;
@@ -941,12 +1025,11 @@ mcmg_status mcmg_cgs2_noalloc(const void* V_dev, int k, size_t n, void* w_dev, d
     double2* dd = pass == 0 ? d1 : d2;
     k_multidot<float2><<<grid, RED_T, 0, st>>>(V, nn, k, k, w, nn, part);
     MCMG_CHECK_LAUNCH("multidot");
-    k_reduce_parts<<<k, RED_T, 0, st>>>(part, nblk, k, dd);
+    k_reduce_parts<<<k, RED_T, 0, st>>>(part, nblk, k, dd, nullptr);
     MCMG_CHECK_LAUNCH("reduce_parts");
-    k_update<float2><<<nblk, RED_T, 0, st>>>(V, nn, k, dd, w, nn, part);
-    MCMG_CHECK_LAUNCH("update");
+    MCMG_TRY(launch_update(V, nn, k, dd, w, nn, part, nblk, st));
   }
-  k_reduce_scalar<<<1, RED_T, 0, st>>>(part, nblk, dsc);
+  k_reduce_scalar<<<1, RED_T, 0, st>>>(part, nblk, dsc, nullptr);
   MCMG_CHECK_LAUNCH("reduce_scalar");
   k_sum_coeffs<<<(k + 127) / 128, 128, 0, st>>>(d1, d2, k, part);   // part is free again
   MCMG_CHECK_LAUNCH("sum_coeffs");
