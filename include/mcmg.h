@@ -158,8 +158,8 @@ mcmg_status mcmg_ctx_memory(mcmg_ctx ctx, size_t* used_bytes);
  * (1 - i gamma) with k = omega / c and h = 1/n[0], runs the setup networks on
  * the device and caches a_l, s_l for every level, and converts the weights to
  * the device layouts.  Grid sizes must be divisible by 2^(levels-1) with the
- * coarsest grid at least 2 nodes per axis (else MCMG_ERR_SHAPE).  Blocks until
- * the setup is complete.                                                     */
+ * coarsest grid at least 2 nodes per axis, and the grid below 2^31 nodes
+ * (else MCMG_ERR_SHAPE).  Blocks until the setup is complete.                */
 mcmg_status mcmg_setup(mcmg_ctx ctx, const mcmg_medium* medium, double omega,
                        const mcmg_weights* weights, mcmg_handle* out);
 mcmg_status mcmg_destroy(mcmg_handle h);
@@ -206,9 +206,10 @@ mcmg_status mcmg_drain(mcmg_ctx ctx);
 /* ---- single steps of the path (used by tests and diagnostics) ------------- */
 
 /* Wait for the device and read the handle's error word: 0 = fine; non-zero
- * means a bounded wait inside a tensor-core kernel ran out (that kernel
- * released its resources and skipped its output).  mcmg_solve reports the
- * same condition as MCMG_ERR_TIMEOUT.                                        */
+ * means a bounded wait inside a kernel ran out (1: a tensor-core MMA, 2: a
+ * bulk copy of mixing weights; that kernel released its resources and
+ * skipped its output).  mcmg_solve reports the same condition as
+ * MCMG_ERR_TIMEOUT.                                                          */
 mcmg_status mcmg_device_error(mcmg_handle h, int* code);
 
 /* y = h^2 A x (Eq. FDM_stencil with the sponge).  fp64 = 0: x, y dev c64;

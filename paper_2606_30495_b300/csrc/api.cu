@@ -549,6 +549,14 @@ mcmg_status mcmg_setup(mcmg_ctx c, const mcmg_medium* m, double omega, const mcm
   }
   for (int a = 0; a < m->dim; ++a)
     if (m->n[a] < 2) { set_error("grid axis %d too small", a); return MCMG_ERR_SHAPE; }
+  {
+    long long nodes = 1;
+    for (int a = 0; a < m->dim; ++a) nodes *= m->n[a];
+    if (nodes > 2147483647LL) {  // kernels index nodes in 32 bits
+      set_error("grid of %lld nodes exceeds 2^31 - 1", nodes);
+      return MCMG_ERR_SHAPE;
+    }
+  }
   MCMG_CUDA(cudaSetDevice(c->device));
   mcmg_handle_s* h = new mcmg_handle_s();
   h->ctx = c;

@@ -7,6 +7,8 @@ namespace mcmg {
 // rc[J][co] = sum_o sum_ci R[o][co][ci] t[2J + o][ci]   (CI fine, CO coarse channels)
 template <int CI, int CO, int D, int TN, int CV, int KQ>
 __global__ void __launch_bounds__(256) k_restrict_rt(TransferParams p) {
+  pdl_launch_dependents();
+  pdl_wait();
   using T = XTile<CI, CO, TN, CV, KQ>;
   constexpr int NB = T::NB, KS = T::KS, T3 = D == 3 ? 27 : 9, CI2 = CI / 2;
   extern __shared__ float4 sm4[];
@@ -29,7 +31,7 @@ __global__ void __launch_bounds__(256) k_restrict_rt(TransferParams p) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (n < NC) {
       int jx, jy, jz;
-      node_xyz(n, p.cx, p.cy, jx, jy, jz);
+      node_xyz32((int)n, p.cx, p.cy, jx, jy, jz);
       const int x = 2 * jx + o % 3 - 1, y = 2 * jy + (o / 3) % 3 - 1;
       const int z = D == 3 ? 2 * jz + o / 9 - 1 : 0;
       if (x >= 0 && x < p.fx && y >= 0 && y < p.fy && z >= 0 && z < p.fz)
@@ -78,6 +80,8 @@ __global__ void __launch_bounds__(256) k_restrict_rt(TransferParams p) {
 // coarse, CO fine channels).  The block stages e_c at J + {0,1}^d.
 template <int CI, int CO, int D, int TN, int CV, int KQ>
 __global__ void __launch_bounds__(256) k_prolong_rt(TransferParams p) {
+  pdl_launch_dependents();
+  pdl_wait();
   using T = XTile<CI, CO, TN, CV, KQ>;
   constexpr int NB = T::NB, KS = T::KS, T3 = D == 3 ? 27 : 9, NP = D == 3 ? 8 : 4;
   constexpr int CI2 = CI / 2;
@@ -101,7 +105,7 @@ __global__ void __launch_bounds__(256) k_prolong_rt(TransferParams p) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (n < NC) {
       int jx, jy, jz;
-      node_xyz(n, p.cx, p.cy, jx, jy, jz);
+      node_xyz32((int)n, p.cx, p.cy, jx, jy, jz);
       const int X = jx + (c & 1), Y = jy + ((c >> 1) & 1), Z = jz + ((c >> 2) & 1);
       if (X < p.cx && Y < p.cy && (D == 3 ? Z < p.cz : true))
         v = __ldg(reinterpret_cast<const float4*>(ec + (((long long)(D == 3 ? Z : 0) * p.cy + Y) * p.cx + X) * CI) + c2);
@@ -149,7 +153,7 @@ __global__ void __launch_bounds__(256) k_prolong_rt(TransferParams p) {
 #pragma unroll
       for (int q = 1; q < KS; ++q) v = cadd(v, red[q * NB * NP * CO + idx]);
       int jx, jy, jz;
-      node_xyz(n, p.cx, p.cy, jx, jy, jz);
+      node_xyz32((int)n, p.cx, p.cy, jx, jy, jz);
       const long long fx = 2 * jx + (b & 1), fy = 2 * jy + ((b >> 1) & 1),
                       fz = D == 3 ? 2 * jz + ((b >> 2) & 1) : 0;
       const long long fi = ((fz * p.fy + fy) * p.fx + fx) * CO + co;
@@ -177,11 +181,11 @@ static mcmg_status transfer_rt(const TransferParams& p, bool restrict_, int nrhs
     if (restrict_) {
       auto k = k_restrict_rt<CI, CO, D, TN, CV, KQ>;
       if (smem_r > 48 * 1024) MCMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
-      k<<<grid, 256, smem_r, st>>>(p);
+      MCMG_LAUNCH_PDL(k, grid, dim3(256), smem_r, st, p);
     } else {
       auto k = k_prolong_rt<CI, CO, D, TN, CV, KQ>;
       if (smem_p > 48 * 1024) MCMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
-      k<<<grid, 256, smem_p, st>>>(p);
+      MCMG_LAUNCH_PDL(k, grid, dim3(256), smem_p, st, p);
     }
     MCMG_CHECK_LAUNCH(restrict_ ? "restrict_rt" : "prolong_rt");
     return MCMG_OK;

@@ -23,30 +23,23 @@ namespace mcmg {
 // complex FMAs.  The shape is chosen per level and mode by the autotuner at
 // setup (autotune_smooth); pick_shape is the fallback heuristic.
 struct Shape {
-  int kind;    // 0: k_smooth (Tile), 1: k_smooth_ks (KsTile), 2: k_smooth_rt (RtTile)
+  int kind;    // 0: k_smooth (Tile), 1: k_smooth_ks (KsTile), 2: k_smooth_rt (RtTile),
+               // 3: k_smooth_rtb (RtTile, matrices staged by bulk copies)
   int tn, co;  // nodes and output channels per thread
   int kq;      // input channels per K-group (k_smooth_rt)
 };
 static constexpr Shape kShapes[] = {{0, 8, 1, 0}, {0, 2, 1, 0}, {0, 1, 1, 0}, {0, 2, 4, 0},
                                     {0, 1, 4, 0}, {1, 1, 1, 0}, {2, 8, 4, 4}, {2, 4, 4, 4},
-                                    {2, 8, 4, 2}, {2, 4, 4, 2}, {2, 8, 4, 8}, {2, 4, 4, 8}};
+                                    {2, 8, 4, 2}, {2, 4, 4, 2}, {2, 8, 4, 8}, {2, 4, 4, 8},
+                                    {3, 8, 4, 4}, {3, 4, 4, 4}, {3, 4, 4, 8}};
 static constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
-
-// Shared memory of k_smooth_rt: the staged fields of the 2D+1 taps (reused
-// for t and z) and two sets of KS partial tiles (K_A and the rest).
-static size_t rt_smem(int C, int D, int tn, int co, int kq) {
-  if (co > C || C % co || kq > C || C % kq) return 0;
-  const int cg = C / co, ks = C / kq;
-  if (cg * ks > 256 || 256 % (cg * ks)) return 0;
-  const size_t nb = (size_t)(256 / (cg * ks)) * tn;
-  return (size_t)(2 * D + 1 + 2 * ks) * nb * C * sizeof(float2);
-}
 
 static bool shape_ok(int s, int C, int D) {
   const Shape& k = kShapes[s];
   if (k.kind == 1) return C >= 8;
-  if (k.kind == 2) {
-    const size_t b = rt_smem(C, D, k.tn, k.co, k.kq);
+  if (k.kind == 2 || k.kind == 3) {
+    if (k.kind == 3 && C < 8) return false;
+    const size_t b = rt_smem(C, D, k.tn, k.co, k.kq, k.kind == 3);
     return b > 0 && b <= kMaxSmem;
   }
   return k.co <= C;
@@ -72,6 +65,8 @@ static int pick_tn(long long nodes, int C, int nrhs) {
 
 template <int C, int D, int MODE, int TN, int CO>
 __global__ void __launch_bounds__(256) k_smooth(SmoothParams p) {
+  pdl_launch_dependents();
+  pdl_wait();
   using T = Tile<C, TN, CO>;
   extern __shared__ float2 sm[];
   const int cg = threadIdx.x % T::CG;
@@ -245,9 +240,9 @@ static mcmg_status smooth_shape(const SmoothParams& p, int mode, int nrhs, cudaS
     dim3 grid((unsigned)((p.nodes + T::NB - 1) / T::NB), (unsigned)nrhs);
     size_t smem = mode == 0 ? 2 * (size_t)T::NB * C * sizeof(float2) : 0;
     if (mode == 0)
-      k_smooth<C, D, 0, TN, CO><<<grid, 256, smem, st>>>(p);
+      MCMG_LAUNCH_PDL((k_smooth<C, D, 0, TN, CO>), grid, dim3(256), smem, st, p);
     else
-      k_smooth<C, D, 1, TN, CO><<<grid, 256, smem, st>>>(p);
+      MCMG_LAUNCH_PDL((k_smooth<C, D, 1, TN, CO>), grid, dim3(256), smem, st, p);
     MCMG_CHECK_LAUNCH("smooth");
     return MCMG_OK;
   }
@@ -277,6 +272,8 @@ __device__ __forceinline__ float2 quad_sum(float2 v) {
 
 template <int C, int D, int MODE>
 __global__ void __launch_bounds__(256) k_smooth_ks(SmoothParams p) {
+  pdl_launch_dependents();
+  pdl_wait();
   using T = KsTile<C>;
   __shared__ float2 sm_t[T::NB * C];
   __shared__ float2 sm_z[T::NB * C];
@@ -348,9 +345,9 @@ static mcmg_status smooth_ks(const SmoothParams& p, int mode, int nrhs, cudaStre
     using T = KsTile<C>;
     dim3 grid((unsigned)((p.nodes + T::NB - 1) / T::NB), (unsigned)nrhs);
     if (mode == 0)
-      k_smooth_ks<C, D, 0><<<grid, 256, 0, st>>>(p);
+      MCMG_LAUNCH_PDL((k_smooth_ks<C, D, 0>), grid, dim3(256), 0, st, p);
     else
-      k_smooth_ks<C, D, 1><<<grid, 256, 0, st>>>(p);
+      MCMG_LAUNCH_PDL((k_smooth_ks<C, D, 1>), grid, dim3(256), 0, st, p);
     MCMG_CHECK_LAUNCH("smooth_ks");
     return MCMG_OK;
   }
@@ -367,7 +364,7 @@ static mcmg_status smooth_c(const SmoothParams& p, int mode, int shape, int nrhs
     case 5: return smooth_ks<C, D>(p, mode, nrhs, st);
     default:
       return smooth_rt_launch(p, C, D, mode, kShapes[shape].tn, kShapes[shape].co,
-                              kShapes[shape].kq, nrhs, st);
+                              kShapes[shape].kq, kShapes[shape].kind == 3, nrhs, st);
   }
 }
 
@@ -403,6 +400,7 @@ static SmoothParams smooth_params(const Level& L, int step, const float2* r, con
   p.ny = L.g.ny;
   p.nz = L.g.nz;
   p.nodes = L.g.nodes();
+  p.err = L.err;
   return p;
 }
 
@@ -475,6 +473,8 @@ mcmg_status autotune_smooth(Level& L, float2* r, float2* e, float2* out, cudaStr
 // ---------------------------------------------------------------------------
 template <int CO, int D, int TN>
 __global__ void __launch_bounds__(256) k_restrict(TransferParams p) {
+  pdl_launch_dependents();
+  pdl_wait();
   using T = Tile<CO, TN, 1>;
   const int co = threadIdx.x % CO;
   const int g = threadIdx.x / CO;
@@ -527,6 +527,8 @@ __global__ void __launch_bounds__(256) k_restrict(TransferParams p) {
 // the coarse grid is zero.
 template <int CO, int D, int TN>
 __global__ void __launch_bounds__(256) k_prolong_add(TransferParams p) {
+  pdl_launch_dependents();
+  pdl_wait();
   using T = Tile<CO, TN, 1>;
   constexpr int NB2 = D == 3 ? 8 : 4;
   constexpr int T3 = D == 3 ? 27 : 9;
@@ -620,9 +622,9 @@ static mcmg_status transfer_tn(const TransferParams& p, bool restrict_, int nrhs
   const long long units = restrict_ ? p.dst_nodes : p.src_nodes;
   dim3 grid((unsigned)((units + T::NB - 1) / T::NB), (unsigned)nrhs);
   if (restrict_)
-    k_restrict<CO, D, TN><<<grid, 256, 0, st>>>(p);
+    MCMG_LAUNCH_PDL((k_restrict<CO, D, TN>), grid, dim3(256), 0, st, p);
   else
-    k_prolong_add<CO, D, TN><<<grid, 256, 0, st>>>(p);
+    MCMG_LAUNCH_PDL((k_prolong_add<CO, D, TN>), grid, dim3(256), 0, st, p);
   MCMG_CHECK_LAUNCH(restrict_ ? "restrict" : "prolong_add");
   return MCMG_OK;
 }

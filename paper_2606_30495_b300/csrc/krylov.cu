@@ -607,7 +607,7 @@ mcmg_status krylov_advance(Krylov* k, bool blocking, int* done) {
     if (e != cudaSuccess) return cuda_fail(e, "krylov event");
   }
   if (k->h->err_host && *(volatile int*)k->h->err_host) {
-    set_error("a bounded wait in a tensor-core kernel ran out (code %d)", *k->h->err_host);
+    set_error("a bounded wait in a device kernel ran out (code %d)", *k->h->err_host);
     finish(k, false, MCMG_ERR_TIMEOUT);
     *done = 1;
     return MCMG_OK;
@@ -798,7 +798,7 @@ static mcmg_status member_process(Krylov* k) {
   Stat st;
   std::memcpy(&st, (const void*)k->stat_h, sizeof(Stat));
   if (k->h->err_host && *(volatile int*)k->h->err_host) {
-    set_error("a bounded wait in a tensor-core kernel ran out (code %d)", *k->h->err_host);
+    set_error("a bounded wait in a device kernel ran out (code %d)", *k->h->err_host);
     finish(k, false, MCMG_ERR_TIMEOUT);
     return MCMG_OK;
   }

@@ -2,9 +2,45 @@
 // translation units (kernels_vcycle.cu, kernels_smooth_rt.cu,
 // kernels_transfer_rt.cu).
 #pragma once
+#include <utility>
+
 #include "mcmg_internal.cuh"
 
 namespace mcmg {
+
+// Programmatic dependent launch.  The V-cycle's kernels are launched so that
+// each may start while its predecessor drains: a kernel first lets its own
+// dependents launch, reads only setup-time data (weights, features) before
+// pdl_wait(), and touches fields written by earlier kernels only after it.
+// pdl_wait() returns once every prerequisite grid has completed and its
+// memory is visible; both are no-ops in a kernel launched without the
+// attribute.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+#define MCMG_LAUNCH_PDL(kernel, grid, block, smem, st, ...)                      \
+  do {                                                                          \
+    cudaError_t _e = ::mcmg::launch_pdl(kernel, grid, block, smem, st, __VA_ARGS__); \
+    if (_e != cudaSuccess) return ::mcmg::cuda_fail(_e, #kernel);              \
+  } while (0)
 
 template <int C, int TN_, int CO_>
 struct Tile {
@@ -41,6 +77,7 @@ struct SmoothParams {
   const float2* Wst;    // W^(i) for this step, [C][C]
   int nx, ny, nz;
   long long nodes;
+  int* err;             // handle's error word (bounded waits that ran out)
 };
 
 __device__ __forceinline__ void node_xyz(long long n, int nx, int ny, int& x, int& y, int& z) {
@@ -48,6 +85,14 @@ __device__ __forceinline__ void node_xyz(long long n, int nx, int ny, int& x, in
   long long rest = n / nx;
   y = (int)(rest % ny);
   z = (int)(rest / ny);
+}
+
+// The same for node indices below 2^31 (every grid; checked at setup).
+__device__ __forceinline__ void node_xyz32(int n, int nx, int ny, int& x, int& y, int& z) {
+  const int rest = n / nx;
+  x = n - rest * nx;
+  y = rest % ny;
+  z = rest / ny;
 }
 
 // CO consecutive complex values (one float2, or two float4 for CO = 4).
@@ -98,8 +143,12 @@ struct XTile {
 
 // Register-tiled smoothing step (kernels_smooth_rt.cu): shape (tn, co, kq)
 // on C channels in D dimensions; MCMG_ERR_SHAPE if it is not built.
+// bulk: the variant that stages each mixing matrix in shared memory with
+// bulk asynchronous copies.
 mcmg_status smooth_rt_launch(const SmoothParams& p, int C, int D, int mode, int tn, int co, int kq,
-                             int nrhs, cudaStream_t st);
+                             bool bulk, int nrhs, cudaStream_t st);
+// Shared memory of the register-tiled smoothing step (0: the shape cannot run).
+size_t rt_smem(int C, int D, int tn, int co, int kq, bool bulk);
 // Register-tiled restriction (restrict_) or prolongation-add between Cf fine
 // and Cc coarse channels (kernels_transfer_rt.cu).
 mcmg_status transfer_rt_launch(const TransferParams& p, int Cf, int Cc, int D, bool restrict_,
