@@ -57,6 +57,10 @@ def parse():
     p.add_argument("--requests", type=int, default=24,
                    help="serving_stream: how many requests of the 256-request stream to serve")
     p.add_argument("--budget-gb", type=float, default=150.0)
+    p.add_argument("--shapes", default="",
+                   help="JSON [[op0, op1, op2, op3] per level] of CUDA-core kernel shapes to "
+                        "use instead of setup's timed choice (the line's kernel_shapes); keeps "
+                        "a profiler run on the kernels a plain run chose")
     return p.parse_args()
 
 
@@ -388,6 +392,13 @@ def main():
     t0 = time.perf_counter()
     h = mcmg.Handle(ctx, c, omega, wl["sponge"], wl["gamma_max"], w, precision=prec)
     t_setup = time.perf_counter() - t0
+    if args.shapes:
+        for l, ops in enumerate(json.loads(args.shapes)):
+            for op, sh in enumerate(ops):
+                if not h.set_kernel_shape(l, op, sh):
+                    raise SystemExit(f"shape {sh} cannot run op {op} on level {l}")
+    kernel_shapes = [[h.kernel_shape(l, op) for op in range(4 if l < wl["levels"] - 1 else 2)]
+                     for l in range(wl["levels"])]
     shape = c.shape
     n = int(np.prod(shape))
     f_host = I.point_source(shape)
@@ -527,6 +538,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 16 * n * 2,
                 "d2h_bytes_per_step": 16 * n},
         "peaks_source": pk_src,
+        "kernel_shapes": kernel_shapes,
     }
     if cpu:
         out["cpu_baseline"] = cpu

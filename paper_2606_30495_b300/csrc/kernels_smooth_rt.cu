@@ -14,15 +14,12 @@ namespace mcmg {
 // give every thread a dense contraction: the shape for coarse levels, where
 // one block per handful of nodes is all the parallelism there is.
 // The block first stages, per stencil tap, the neighbour values of its NB
-// nodes ([tap][node][C], zero outside the grid: Dirichlet closure).  The
-// thread's KQ x CO slice of the next mixing matrix is loaded into registers
-// while the current one is applied (K_A, the 2D+1 taps, K_S, W^(i) in turn),
-// so weight latency overlaps arithmetic across the phase barriers.  K_A
+// nodes ([tap][node][C], zero outside the grid: Dirichlet closure).  K_A
 // partials go to their own buffer so a_l (.) is applied once, in the sum.
 // Two blocks per SM (at most 128 registers a thread) while the accumulator
-// tile and the two weight slices take at most 96 registers.
+// tile and one weight slice take at most 96 registers.
 template <int TN, int CO, int KQ>
-__host__ __device__ constexpr int rt_min_blocks() { return 2 * TN * CO + 4 * KQ * CO <= 96 ? 2 : 1; }
+__host__ __device__ constexpr int rt_min_blocks() { return 2 * TN * CO + 2 * KQ * CO <= 96 ? 2 : 1; }
 
 template <int C, int D, int MODE, int TN, int CO, int KQ>
 __global__ void __launch_bounds__(256, rt_min_blocks<TN, CO, KQ>())
@@ -90,11 +87,6 @@ k_smooth_rt(SmoothParams p) {
     return;
   }
 
-  float2 w[2][KQ][CO];      // this thread's slice of the current and next matrix
-  auto load_w = [&](const float2* __restrict__ Mt, float2 (&dst)[KQ][CO]) {
-#pragma unroll
-    for (int i = 0; i < KQ; ++i) ldc<CO>(Mt + (ci0 + i) * C + co0, dst[i]);
-  };
   float2 acc[TN][CO];
   auto zero = [&]() {
 #pragma unroll
@@ -102,15 +94,18 @@ k_smooth_rt(SmoothParams p) {
 #pragma unroll
       for (int c = 0; c < CO; ++c) acc[k][c] = make_float2(0.f, 0.f);
   };
-  // acc += (slice of M^T) applied to X[node][ci]
-  auto contract = [&](const float2 (&wm)[KQ][CO], const float2* X) {
+  // acc += (this thread's slice of M^T) applied to X[node][ci]
+  auto contract = [&](const float2* __restrict__ Mt, const float2* X) {
+    float2 w[KQ][CO];
+#pragma unroll
+    for (int i = 0; i < KQ; ++i) ldc<CO>(Mt + (ci0 + i) * C + co0, w[i]);
 #pragma unroll
     for (int i = 0; i < KQ; ++i) {
 #pragma unroll
       for (int k = 0; k < TN; ++k) {
         const float2 v = X[(j0 + k) * C + ci0 + i];
 #pragma unroll
-        for (int c = 0; c < CO; ++c) cfma(acc[k][c], wm[i][c], v);
+        for (int c = 0; c < CO; ++c) cfma(acc[k][c], w[i][c], v);
       }
     }
   };
@@ -126,8 +121,6 @@ k_smooth_rt(SmoothParams p) {
   };
 
   if (ein) {
-    load_w(p.KAt, w[0]);
-    load_w(p.Wt, w[1]);
     const long long sxy = (long long)p.nx * p.ny;
     for (int idx = tid; idx < NT * NB * C2; idx += 256) {
       const int c2 = idx % C2;
@@ -153,77 +146,80 @@ k_smooth_rt(SmoothParams p) {
       }
       sm4[(tap * NB + j) * C2 + c2] = v;
     }
-    __syncthreads();
-
-    // t = r - (W_l * e + a (.) (K_A e))
-    zero();
-    contract(w[0], E);
-    store_partial(redA);
-    zero();
-#pragma unroll
-    for (int tap = 0; tap < NT; ++tap) {
-      // W_tap sits in w[(tap + 1) & 1]; the next matrix goes to the other buffer
-      if (tap + 1 < NT)
-        load_w(p.Wt + (size_t)(tap + 1) * C * C, w[tap & 1]);
-      else if (MODE == 0)
-        load_w(p.KSt, w[tap & 1]);
-      contract(w[(tap + 1) & 1], E + tap * NB * C);
-    }
-    store_partial(red);
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < RQ; ++q) {
-      const int idx = tid + 256 * q;
-      if (idx < NB * C) {
-        const long long n = n0 + idx / C;
-        float2 t = make_float2(0.f, 0.f);
-        if (n < N) t = csub(csub(pre(rq, r, q), reduced(red, idx)), cmul(pre(aq, p.a, q), reduced(redA, idx)));
-        if (MODE == 1) {
-          if (n < N) eout[n0 * C + idx] = t;
-        } else {
-          Ts[idx] = t;
-        }
-      }
-    }
-    if (MODE == 1) return;
-    __syncthreads();
   } else {
-    load_w(p.KSt, w[0]);
     for (int idx = tid; idx < NB * C2; idx += 256) {
       const long long n = n0 + idx / C2;
       sm4[idx] = n < N ? __ldg(reinterpret_cast<const float4*>(r + n0 * C) + idx)
                        : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __syncthreads();
-  }
-  // K_S is in w[0] on both paths ((2D+1) taps leave it in w[(NT-1) & 1] = w[0])
-  static_assert(((NT - 1) & 1) == 0, "tap count is odd");
-
-  // z = s (.) (K_S t)
-  load_w(p.Wst, w[1]);
-  zero();
-  contract(w[0], Ts);
-  store_partial(red);
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < RQ; ++q) {
-    const int idx = tid + 256 * q;
-    if (idx < NB * C)
-      Zs[idx] = n0 + idx / C < N ? cmul(pre(sq, p.s, q), reduced(red, idx)) : make_float2(0.f, 0.f);
   }
   __syncthreads();
 
-  // e' = e + W^(i) z
+  // One contraction per round, the code emitted once (a fully unrolled round
+  // sequence overflows the instruction cache): with e, K_A on the centre
+  // values, then W_tap on each tap's values (t = r - W_l * e - a (.) K_A e);
+  // then K_S on t (z = s (.) K_S t) and W^(i) on z (e' = e + W^(i) z).
+  const int nA = ein ? NT + 1 : 0;
+  const int nm = nA + (MODE == 0 ? 2 : 0);
   zero();
-  contract(w[1], Zs);
-  store_partial(red);
-  __syncthreads();
+#pragma unroll 1
+  for (int m = 0; m < nm; ++m) {
+    const float2* Mt;
+    const float2* X;
+    if (m < nA) {
+      Mt = m == 0 ? p.KAt : p.Wt + (size_t)(m - 1) * C * C;
+      X = E + (m == 0 ? 0 : m - 1) * NB * C;
+    } else {
+      Mt = m == nA ? p.KSt : p.Wst;
+      X = m == nA ? Ts : Zs;
+    }
+    contract(Mt, X);
+    if (m == 0 && nA > 0) {            // K_A partials apart
+      store_partial(redA);
+      zero();
+    } else if (m == nA - 1) {          // t = r - sum - a (.) sum_A
+      store_partial(red);
+      __syncthreads();
 #pragma unroll
-  for (int q = 0; q < RQ; ++q) {
-    const int idx = tid + 256 * q;
-    if (idx < NB * C && n0 + idx / C < N) {
-      const float2 u = reduced(red, idx);
-      eout[n0 * C + idx] = ein ? cadd(u, pre(eq, ein, q)) : u;
+      for (int q = 0; q < RQ; ++q) {
+        const int idx = tid + 256 * q;
+        if (idx < NB * C) {
+          const long long n = n0 + idx / C;
+          float2 t = make_float2(0.f, 0.f);
+          if (n < N)
+            t = csub(csub(pre(rq, r, q), reduced(red, idx)), cmul(pre(aq, p.a, q), reduced(redA, idx)));
+          if (MODE == 1) {
+            if (n < N) eout[n0 * C + idx] = t;
+          } else {
+            Ts[idx] = t;
+          }
+        }
+      }
+      if (MODE == 1) return;
+      __syncthreads();
+      zero();
+    } else if (m == nA) {              // z = s (.) (K_S t)
+      store_partial(red);
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < RQ; ++q) {
+        const int idx = tid + 256 * q;
+        if (idx < NB * C)
+          Zs[idx] = n0 + idx / C < N ? cmul(pre(sq, p.s, q), reduced(red, idx)) : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      zero();
+    } else if (m == nA + 1) {          // e' = e + W^(i) z
+      store_partial(red);
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < RQ; ++q) {
+        const int idx = tid + 256 * q;
+        if (idx < NB * C && n0 + idx / C < N) {
+          const float2 u = reduced(red, idx);
+          eout[n0 * C + idx] = ein ? cadd(u, pre(eq, ein, q)) : u;
+        }
+      }
     }
   }
 }
@@ -489,6 +485,7 @@ k_smooth_rtb(SmoothParams p) {
     store_partial(redA);
     ++mi;
     zero();
+#pragma unroll 1
     for (int tap = 0; tap < NT; ++tap, ++mi) {
       if (!acquire(mi)) return;
       contract(mi & 1, E + tap * NB * C);

@@ -24,18 +24,21 @@ namespace mcmg {
 // setup (autotune_smooth); pick_shape is the fallback heuristic.
 struct Shape {
   int kind;    // 0: k_smooth (Tile), 1: k_smooth_ks (KsTile), 2: k_smooth_rt (RtTile),
-               // 3: k_smooth_rtb (RtTile, matrices staged by bulk copies)
+               // 3: k_smooth_rtb (RtTile, matrices staged by bulk copies),
+               // 4: k_smooth_tpn (co = output channels per lane)
   int tn, co;  // nodes and output channels per thread
   int kq;      // input channels per K-group (k_smooth_rt)
 };
 static constexpr Shape kShapes[] = {{0, 8, 1, 0}, {0, 2, 1, 0}, {0, 1, 1, 0}, {0, 2, 4, 0},
                                     {0, 1, 4, 0}, {1, 1, 1, 0}, {2, 8, 4, 4}, {2, 4, 4, 4},
                                     {2, 8, 4, 2}, {2, 4, 4, 2}, {2, 8, 4, 8}, {2, 4, 4, 8},
-                                    {3, 8, 4, 4}, {3, 4, 4, 4}, {3, 4, 4, 8}};
+                                    {3, 8, 4, 4}, {3, 4, 4, 4}, {3, 4, 4, 8},
+                                    {4, 1, 8, 0}, {4, 1, 4, 0}};
 static constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 static bool shape_ok(int s, int C, int D) {
   const Shape& k = kShapes[s];
+  if (k.kind == 4) return (C == 4 || C == 8 || C == 16) && k.co <= C && C / k.co <= 4;
   if (k.kind == 1) return C >= 8;
   if (k.kind == 2 || k.kind == 3) {
     if (k.kind == 3 && C < 8) return false;
@@ -353,6 +356,173 @@ static mcmg_status smooth_ks(const SmoothParams& p, int mode, int nrhs, cudaStre
   }
 }
 
+// Thread-per-node smoothing step for few channels (C = 4, 8, 16).  G = C / CT
+// adjacent lanes share a node, each owning CT output channels; a block covers
+// 256 / G nodes.  Every mixing matrix of the step sits in shared memory and is
+// read as a broadcast (all nodes' lanes read the same weights); each lane loads
+// the C values of every tap of its node with 16-byte loads (a warp reads
+// whole rows of consecutive nodes); t and z stay in registers and reach a
+// node's G lanes through warp shuffles.  No block barrier after the weights
+// are staged, no shared-memory traffic for the fields.
+template <int C, int D, int MODE, int CT>
+__global__ void __launch_bounds__(256) k_smooth_tpn(SmoothParams p) {
+  pdl_launch_dependents();
+  constexpr int G = C / CT, NPB = 256 / G, NT = 2 * D + 1, MSZ = C * C, NM = NT + 3;
+  __shared__ __align__(16) float2 Wsm[NM * MSZ];   // taps, K_A, K_S, W^(i)
+  for (int i = threadIdx.x; i < NM * MSZ / 2; i += 256) {   // setup-time data
+    const int m = (2 * i) / MSZ, o = (2 * i) % MSZ;
+    const float2* src = m < NT ? p.Wt + (size_t)m * MSZ
+                               : (m == NT ? p.KAt : (m == NT + 1 ? p.KSt : p.Wst));
+    reinterpret_cast<float4*>(Wsm)[i] = __ldg(reinterpret_cast<const float4*>(src + o));
+  }
+  __syncthreads();
+  pdl_wait();
+  const int lane = threadIdx.x & 31;
+  const int g = threadIdx.x % G;
+  const int base = lane - g;                        // first lane of this node
+  const long long N = p.nodes;
+  const long long n = (long long)blockIdx.x * NPB + threadIdx.x / G;
+  const bool live = n < N;
+  const long long nc = live ? n : N - 1;            // every lane joins the shuffles
+  const size_t off = (size_t)blockIdx.y * (size_t)N * C;
+  const float2* __restrict__ r = p.r + off;
+  const float2* __restrict__ ein = p.e_in ? p.e_in + off : nullptr;
+  float2* __restrict__ eout = p.e_out + off;
+  const int c0 = g * CT;
+
+  auto load_vec = [&](const float2* q, float2* x, int cnt) {   // cnt complex, 16-byte loads
+    const float4* q4 = reinterpret_cast<const float4*>(q);
+    for (int i = 0; i < cnt / 2; ++i) {
+      const float4 v = __ldg(q4 + i);
+      x[2 * i] = make_float2(v.x, v.y);
+      x[2 * i + 1] = make_float2(v.z, v.w);
+    }
+  };
+  // acc[co] += sum_ci M[c0 + co][ci] x[ci], M^T[ci][.] in shared memory
+  auto mix = [&](const float2* Mt, const float2 (&x)[C], float2 (&acc)[CT]) {
+#pragma unroll
+    for (int ci = 0; ci < C; ++ci) {
+      const float4* w4 = reinterpret_cast<const float4*>(Mt + ci * C + c0);
+#pragma unroll
+      for (int h = 0; h < CT / 2; ++h) {
+        const float4 w = w4[h];
+        cfma(acc[2 * h], make_float2(w.x, w.y), x[ci]);
+        cfma(acc[2 * h + 1], make_float2(w.z, w.w), x[ci]);
+      }
+    }
+  };
+  // all C values of a node from its G lanes' CT each
+  auto gather = [&](const float2 (&v)[CT], float2 (&all)[C]) {
+#pragma unroll
+    for (int q = 0; q < G; ++q)
+#pragma unroll
+      for (int co = 0; co < CT; ++co) {
+        if constexpr (G == 1) {
+          all[co] = v[co];
+        } else {
+          all[q * CT + co] = make_float2(__shfl_sync(0xffffffffu, v[co].x, base + q),
+                                         __shfl_sync(0xffffffffu, v[co].y, base + q));
+        }
+      }
+  };
+
+  float2 t[CT];
+  if (ein) {
+    float2 acc[CT], accA[CT];
+#pragma unroll
+    for (int co = 0; co < CT; ++co) acc[co] = accA[co] = make_float2(0.f, 0.f);
+    const int ni = (int)nc, rest = ni / p.nx;
+    const int cx = ni - rest * p.nx, cy = rest % p.ny, cz = rest / p.ny;
+    const long long sxy = (long long)p.nx * p.ny;
+#pragma unroll
+    for (int tap = 0; tap < NT; ++tap) {
+      long long nb = nc;
+      bool ok = true;
+      if (tap > 0) {
+        const int axis = (tap - 1) >> 1;
+        const int sgn = (tap & 1) ? -1 : 1;
+        const int c = axis == 0 ? cx : (axis == 1 ? cy : cz);
+        const int ext = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
+        const long long stride = axis == 0 ? 1 : (axis == 1 ? p.nx : sxy);
+        ok = c + sgn >= 0 && c + sgn < ext;
+        nb = ok ? nc + sgn * stride : nc;
+      }
+      float2 x[C];
+      load_vec(ein + nb * C, x, C);
+      if (!ok)
+#pragma unroll
+        for (int ci = 0; ci < C; ++ci) x[ci] = make_float2(0.f, 0.f);
+      mix(Wsm + tap * MSZ, x, acc);
+      if (tap == 0) mix(Wsm + NT * MSZ, x, accA);
+    }
+    float2 rv[CT], av[CT];
+    load_vec(r + nc * C + c0, rv, CT);
+    load_vec(p.a + nc * C + c0, av, CT);
+#pragma unroll
+    for (int co = 0; co < CT; ++co) t[co] = csub(csub(rv[co], acc[co]), cmul(av[co], accA[co]));
+    if (MODE == 1) {
+      if (live) {
+        float4* o4 = reinterpret_cast<float4*>(eout + n * C + c0);
+#pragma unroll
+        for (int h = 0; h < CT / 2; ++h)
+          o4[h] = make_float4(t[2 * h].x, t[2 * h].y, t[2 * h + 1].x, t[2 * h + 1].y);
+      }
+      return;
+    }
+  } else {
+    load_vec(r + nc * C + c0, t, CT);
+  }
+  // z = s (.) (K_S t)
+  float2 all[C], z[CT], sv[CT];
+  gather(t, all);
+#pragma unroll
+  for (int co = 0; co < CT; ++co) z[co] = make_float2(0.f, 0.f);
+  mix(Wsm + (NT + 1) * MSZ, all, z);
+  load_vec(p.s + nc * C + c0, sv, CT);
+#pragma unroll
+  for (int co = 0; co < CT; ++co) z[co] = cmul(sv[co], z[co]);
+  // e' = e + W^(i) z
+  gather(z, all);
+  float2 u[CT];
+#pragma unroll
+  for (int co = 0; co < CT; ++co) u[co] = make_float2(0.f, 0.f);
+  mix(Wsm + (NT + 2) * MSZ, all, u);
+  if (live) {
+    if (ein) {
+      float2 ev[CT];
+      load_vec(ein + n * C + c0, ev, CT);
+#pragma unroll
+      for (int co = 0; co < CT; ++co) u[co] = cadd(u[co], ev[co]);
+    }
+    float4* o4 = reinterpret_cast<float4*>(eout + n * C + c0);
+#pragma unroll
+    for (int h = 0; h < CT / 2; ++h)
+      o4[h] = make_float4(u[2 * h].x, u[2 * h].y, u[2 * h + 1].x, u[2 * h + 1].y);
+  }
+}
+
+template <int C, int CT>
+constexpr bool tpn_valid() {
+  return (C == 4 || C == 8 || C == 16) && (CT == 4 || CT == 8) && CT <= C && C / CT <= 4;
+}
+
+template <int C, int D, int CT>
+static mcmg_status smooth_tpn(const SmoothParams& p, int mode, int nrhs, cudaStream_t st) {
+  if constexpr (!tpn_valid<C, CT>()) {
+    set_error("thread-per-node shape does not fit %d channels", C);
+    return MCMG_ERR_SHAPE;
+  } else {
+    constexpr int NPB = 256 / (C / CT);
+    dim3 grid((unsigned)((p.nodes + NPB - 1) / NPB), (unsigned)nrhs);
+    if (mode == 0)
+      MCMG_LAUNCH_PDL((k_smooth_tpn<C, D, 0, CT>), grid, dim3(256), 0, st, p);
+    else
+      MCMG_LAUNCH_PDL((k_smooth_tpn<C, D, 1, CT>), grid, dim3(256), 0, st, p);
+    MCMG_CHECK_LAUNCH("smooth_tpn");
+    return MCMG_OK;
+  }
+}
+
 template <int C, int D>
 static mcmg_status smooth_c(const SmoothParams& p, int mode, int shape, int nrhs, cudaStream_t st) {
   switch (shape) {
@@ -362,6 +532,8 @@ static mcmg_status smooth_c(const SmoothParams& p, int mode, int shape, int nrhs
     case 3: return smooth_shape<C, D, 2, 4>(p, mode, nrhs, st);
     case 4: return smooth_shape<C, D, 1, 4>(p, mode, nrhs, st);
     case 5: return smooth_ks<C, D>(p, mode, nrhs, st);
+    case 15: return smooth_tpn<C, D, 8>(p, mode, nrhs, st);
+    case 16: return smooth_tpn<C, D, 4>(p, mode, nrhs, st);
     default:
       return smooth_rt_launch(p, C, D, mode, kShapes[shape].tn, kShapes[shape].co,
                               kShapes[shape].kq, kShapes[shape].kind == 3, nrhs, st);

@@ -214,7 +214,7 @@ def test_every_kernel_shape(case):
         # operation (the captured graph must follow each change)
         rv = I.complex_normal((2,) + m["shape"], rng(52))
         want_v = np.stack([O.vcycle(w, m["feats"], ri) for ri in rv])
-        for k in range(1, 10):
+        for k in range(1, 13):
             for l in range(L):
                 for op in range(4 if l < L - 1 else 2):
                     n_op = mcmg.kernel_shape_count(op)
