@@ -26,13 +26,16 @@ __global__ void __launch_bounds__(256, rt_min_blocks<TN, CO, KQ>())
 k_smooth_rt(SmoothParams p) {
   pdl_launch_dependents();
   using T = RtTile<C, TN, CO, KQ>;
-  constexpr int NB = T::NB, KS = T::KS, NT = 2 * D + 1, C2 = C / 2;
+  // node rows of the staged fields are C + 1 apart, so a warp's node groups
+  // fall on different banks
+  constexpr int NB = T::NB, KS = T::KS, NT = 2 * D + 1, C2 = C / 2, CP = C + 1;
+  constexpr int ESZ = (NT * NB * CP + 1) & ~1;
   extern __shared__ float4 sm4[];
-  float2* E = reinterpret_cast<float2*>(sm4);   // [NT][NB][C]
-  float2* red = E + NT * NB * C;                // [KS][NB][C]  taps / K_S / W^(i)
+  float2* E = reinterpret_cast<float2*>(sm4);   // [NT][NB][CP]
+  float2* red = E + ESZ;                        // [KS][NB][C]  taps / K_S / W^(i)
   float2* redA = red + KS * NB * C;             // [KS][NB][C]  K_A
-  float2* Ts = E;                               // [NB][C], after the taps are used
-  float2* Zs = E + NB * C;                      // [NB][C]
+  float2* Ts = E;                               // [NB][CP], after the taps are used
+  float2* Zs = E + NB * CP;                     // [NB][CP]
   const int tid = threadIdx.x;
   const int cg = tid % T::CG;
   const int ng = (tid / T::CG) % T::NG;
@@ -103,7 +106,7 @@ k_smooth_rt(SmoothParams p) {
     for (int i = 0; i < KQ; ++i) {
 #pragma unroll
       for (int k = 0; k < TN; ++k) {
-        const float2 v = X[(j0 + k) * C + ci0 + i];
+        const float2 v = X[(j0 + k) * CP + ci0 + i];
 #pragma unroll
         for (int c = 0; c < CO; ++c) cfma(acc[k][c], w[i][c], v);
       }
@@ -144,13 +147,16 @@ k_smooth_rt(SmoothParams p) {
         }
         if (ok) v = __ldg(reinterpret_cast<const float4*>(ein + nb * C) + c2);
       }
-      sm4[(tap * NB + j) * C2 + c2] = v;
+      E[(tap * NB + j) * CP + 2 * c2] = make_float2(v.x, v.y);
+      E[(tap * NB + j) * CP + 2 * c2 + 1] = make_float2(v.z, v.w);
     }
   } else {
     for (int idx = tid; idx < NB * C2; idx += 256) {
       const long long n = n0 + idx / C2;
-      sm4[idx] = n < N ? __ldg(reinterpret_cast<const float4*>(r + n0 * C) + idx)
-                       : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 v = n < N ? __ldg(reinterpret_cast<const float4*>(r + n0 * C) + idx)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+      Ts[(idx / C2) * CP + 2 * (idx % C2)] = make_float2(v.x, v.y);
+      Ts[(idx / C2) * CP + 2 * (idx % C2) + 1] = make_float2(v.z, v.w);
     }
   }
   __syncthreads();
@@ -168,7 +174,7 @@ k_smooth_rt(SmoothParams p) {
     const float2* X;
     if (m < nA) {
       Mt = m == 0 ? p.KAt : p.Wt + (size_t)(m - 1) * C * C;
-      X = E + (m == 0 ? 0 : m - 1) * NB * C;
+      X = E + (m == 0 ? 0 : m - 1) * NB * CP;
     } else {
       Mt = m == nA ? p.KSt : p.Wst;
       X = m == nA ? Ts : Zs;
@@ -191,7 +197,7 @@ k_smooth_rt(SmoothParams p) {
           if (MODE == 1) {
             if (n < N) eout[n0 * C + idx] = t;
           } else {
-            Ts[idx] = t;
+            Ts[(idx / C) * CP + idx % C] = t;
           }
         }
       }
@@ -205,7 +211,8 @@ k_smooth_rt(SmoothParams p) {
       for (int q = 0; q < RQ; ++q) {
         const int idx = tid + 256 * q;
         if (idx < NB * C)
-          Zs[idx] = n0 + idx / C < N ? cmul(pre(sq, p.s, q), reduced(red, idx)) : make_float2(0.f, 0.f);
+          Zs[(idx / C) * CP + idx % C] =
+              n0 + idx / C < N ? cmul(pre(sq, p.s, q), reduced(red, idx)) : make_float2(0.f, 0.f);
       }
       __syncthreads();
       zero();
@@ -227,8 +234,8 @@ k_smooth_rt(SmoothParams p) {
 template <int C, int D, int TN, int CO, int KQ>
 static mcmg_status smooth_rt(const SmoothParams& p, int mode, int nrhs, cudaStream_t st) {
   using T = RtTile<C, TN, CO, KQ>;
-  constexpr size_t smem =
-      (size_t)(2 * D + 1 + 2 * (T::valid ? T::KS : 0)) * T::NB * C * sizeof(float2);
+  constexpr size_t smem = (size_t)((((2 * D + 1) * T::NB * (C + 1) + 1) & ~1) +
+                                   2 * (T::valid ? T::KS : 0) * T::NB * C) * sizeof(float2);
   if constexpr (!T::valid || C < 2 || smem > kMaxSmem) {
     set_error("register-tiled shape does not fit %d channels", C);
     return MCMG_ERR_SHAPE;
@@ -309,17 +316,17 @@ __global__ void __launch_bounds__(256, rt_min_blocks<TN, CO, KQ>())
 k_smooth_rtb(SmoothParams p) {
   pdl_launch_dependents();
   using T = RtTile<C, TN, CO, KQ>;
-  constexpr int NB = T::NB, KS = T::KS, NT = 2 * D + 1, C2 = C / 2, MSZ = C * C;
+  constexpr int NB = T::NB, KS = T::KS, NT = 2 * D + 1, C2 = C / 2, MSZ = C * C, CP = C + 1;
+  constexpr int ESZ = (NT * NB * CP + 1) & ~1;   // node rows C + 1 apart (banks)
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ int s_fail;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);            // [2]
   float2* Wb = reinterpret_cast<float2*>(smraw + 128);           // [2][C][C]
-  float2* E = Wb + 2 * MSZ;                                      // [NT][NB][C]
-  float4* sm4 = reinterpret_cast<float4*>(E);
-  float2* red = E + NT * NB * C;                                 // [KS][NB][C]
+  float2* E = Wb + 2 * MSZ;                                      // [NT][NB][CP]
+  float2* red = E + ESZ;                                         // [KS][NB][C]
   float2* redA = red + KS * NB * C;                              // [KS][NB][C]
   float2* Ts = E;
-  float2* Zs = E + NB * C;
+  float2* Zs = E + NB * CP;
   const int tid = threadIdx.x;
   const int cg = tid % T::CG;
   const int ng = (tid / T::CG) % T::NG;
@@ -434,7 +441,7 @@ k_smooth_rtb(SmoothParams p) {
       }
 #pragma unroll
       for (int k = 0; k < TN; ++k) {
-        const float2 v = X[(j0 + k) * C + ci0 + i];
+        const float2 v = X[(j0 + k) * CP + ci0 + i];
 #pragma unroll
         for (int c = 0; c < CO; ++c) cfma(acc[k][c], w[c], v);
       }
@@ -476,7 +483,8 @@ k_smooth_rtb(SmoothParams p) {
         }
         if (ok) v = __ldg(reinterpret_cast<const float4*>(ein + nb * C) + c2);
       }
-      sm4[(tap * NB + j) * C2 + c2] = v;
+      E[(tap * NB + j) * CP + 2 * c2] = make_float2(v.x, v.y);
+      E[(tap * NB + j) * CP + 2 * c2 + 1] = make_float2(v.z, v.w);
     }
     // t = r - (W_l * e + a (.) (K_A e))
     if (!acquire(mi)) return;
@@ -488,7 +496,7 @@ k_smooth_rtb(SmoothParams p) {
 #pragma unroll 1
     for (int tap = 0; tap < NT; ++tap, ++mi) {
       if (!acquire(mi)) return;
-      contract(mi & 1, E + tap * NB * C);
+      contract(mi & 1, E + tap * NB * CP);
     }
     store_partial(red);
     __syncthreads();
@@ -502,7 +510,7 @@ k_smooth_rtb(SmoothParams p) {
         if (MODE == 1) {
           if (n < N) eout[n0 * C + idx] = t;
         } else {
-          Ts[idx] = t;
+          Ts[(idx / C) * CP + idx % C] = t;
         }
       }
     }
@@ -510,8 +518,10 @@ k_smooth_rtb(SmoothParams p) {
   } else {
     for (int idx = tid; idx < NB * C2; idx += 256) {
       const long long n = n0 + idx / C2;
-      sm4[idx] = n < N ? __ldg(reinterpret_cast<const float4*>(r + n0 * C) + idx)
-                       : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 v = n < N ? __ldg(reinterpret_cast<const float4*>(r + n0 * C) + idx)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+      Ts[(idx / C2) * CP + 2 * (idx % C2)] = make_float2(v.x, v.y);
+      Ts[(idx / C2) * CP + 2 * (idx % C2) + 1] = make_float2(v.z, v.w);
     }
   }
 
@@ -526,7 +536,8 @@ k_smooth_rtb(SmoothParams p) {
   for (int q = 0; q < RQ; ++q) {
     const int idx = tid + 256 * q;
     if (idx < NB * C)
-      Zs[idx] = n0 + idx / C < N ? cmul(pre(sq, p.s, q), reduced(red, idx)) : make_float2(0.f, 0.f);
+      Zs[(idx / C) * CP + idx % C] =
+          n0 + idx / C < N ? cmul(pre(sq, p.s, q), reduced(red, idx)) : make_float2(0.f, 0.f);
   }
 
   // e' = e + W^(i) z
@@ -549,7 +560,8 @@ template <int C, int D, int TN, int CO, int KQ>
 static mcmg_status smooth_rtb(const SmoothParams& p, int mode, int nrhs, cudaStream_t st) {
   using T = RtTile<C, TN, CO, KQ>;
   constexpr size_t smem = 128 + (size_t)2 * C * C * sizeof(float2) +
-      (size_t)(2 * D + 1 + 2 * (T::valid ? T::KS : 0)) * T::NB * C * sizeof(float2);
+      (size_t)((((2 * D + 1) * T::NB * (C + 1) + 1) & ~1) + 2 * (T::valid ? T::KS : 0) * T::NB * C) *
+          sizeof(float2);
   if constexpr (!T::valid || C < 8 || smem > kMaxSmem) {
     set_error("bulk register-tiled shape does not fit %d channels", C);
     return MCMG_ERR_SHAPE;
@@ -574,7 +586,8 @@ size_t rt_smem(int C, int D, int tn, int co, int kq, bool bulk) {
   const int cg = C / co, ks = C / kq;
   if (cg * ks > 256 || 256 % (cg * ks)) return 0;
   const size_t nb = (size_t)(256 / (cg * ks)) * tn;
-  return (size_t)(2 * D + 1 + 2 * ks) * nb * C * sizeof(float2) +
+  const size_t esz = ((2 * D + 1) * nb * (C + 1) + 1) & ~(size_t)1;   // padded node rows
+  return (esz + 2 * ks * nb * C) * sizeof(float2) +
          (bulk ? 128 + (size_t)2 * C * C * sizeof(float2) : 0);
 }
 
