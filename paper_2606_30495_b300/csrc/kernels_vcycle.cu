@@ -35,6 +35,7 @@ static constexpr Shape kShapes[] = {{0, 8, 1, 0}, {0, 2, 1, 0}, {0, 1, 1, 0}, {0
                                     {3, 8, 4, 4}, {3, 4, 4, 4}, {3, 4, 4, 8},
                                     {4, 1, 8, 0}, {4, 1, 4, 0}};
 static constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+static constexpr int kTunePasses = 3, kTuneReps = 10;   // autotuner timing
 
 static bool shape_ok(int s, int C, int D) {
   const Shape& k = kShapes[s];
@@ -594,9 +595,9 @@ mcmg_status launch_smooth(const Level& L, int step, const float2* r, const float
 
 // Autotuner: time every valid thread shape of the CUDA-core smoothing kernel
 // on this level (the step with e and the residual mode) with CUDA events on
-// scratch fields, and keep the fastest in L.shape[mode].  Two passes over the
-// shapes, keeping each shape's better time, so a clock still ramping up at
-// the first pass does not decide.  Run once per medium at setup, before any
+// scratch fields, and keep the fastest in L.shape[mode].  Three passes of ten
+// launches over the shapes, keeping each shape's best time, so a clock still
+// ramping up or a noisy pass does not decide.  Run once per medium at setup, before any
 // V-cycle graph is captured.
 mcmg_status autotune_smooth(Level& L, float2* r, float2* e, float2* out, cudaStream_t st) {
   cudaEvent_t e0, e1;
@@ -608,14 +609,14 @@ mcmg_status autotune_smooth(Level& L, float2* r, float2* e, float2* out, cudaStr
     const SmoothParams p = smooth_params(L, 0, r, e, out, mode);
     float best_ms[kNumShapes];
     for (int s = 0; s < kNumShapes; ++s) best_ms[s] = 1e30f;
-    for (int pass = 0; pass < 2 && status == MCMG_OK; ++pass) {
+    for (int pass = 0; pass < kTunePasses && status == MCMG_OK; ++pass) {
       for (int s = 0; s < kNumShapes; ++s) {
         if (!shape_ok(s, L.C, L.g.d)) continue;
         for (int rep = 0; rep < 2; ++rep)
           if ((status = smooth_run(L, p, mode, s, 1, st)) != MCMG_OK) break;
         if (status != MCMG_OK) break;
         cudaEventRecord(e0, st);
-        const int reps = 5;
+        const int reps = kTuneReps;
         for (int rep = 0; rep < reps; ++rep)
           if ((status = smooth_run(L, p, mode, s, 1, st)) != MCMG_OK) break;
         if (status != MCMG_OK) break;
@@ -874,7 +875,7 @@ mcmg_status launch_prolong_add(const Level& L, const float2* ec, float2* e, int 
 }
 
 // Autotuner for the transfers of level L (L.shape[2] restriction, [3]
-// prolongation): two timed passes over the valid shapes, as for smoothing.
+// prolongation): timed passes over the valid shapes, as for smoothing.
 // fine, coarse: scratch fields of at least nodes_l * C_l and
 // nodes_{l+1} * C_{l+1} elements.
 mcmg_status autotune_transfer(Level& L, float2* fine, float2* coarse, cudaStream_t st) {
@@ -887,14 +888,14 @@ mcmg_status autotune_transfer(Level& L, float2* fine, float2* coarse, cudaStream
     const TransferParams p = transfer_params(L, r, r ? fine : coarse, r ? coarse : fine);
     float best_ms[kNumTShapes];
     for (int s = 0; s < kNumTShapes; ++s) best_ms[s] = 1e30f;
-    for (int pass = 0; pass < 2 && status == MCMG_OK; ++pass) {
+    for (int pass = 0; pass < kTunePasses && status == MCMG_OK; ++pass) {
       for (int s = 0; s < kNumTShapes; ++s) {
         if (!xshape_ok(s, L, r)) continue;
         for (int rep = 0; rep < 2; ++rep)
           if ((status = transfer_run(L, p, r, s, 1, st)) != MCMG_OK) break;
         if (status != MCMG_OK) break;
         cudaEventRecord(e0, st);
-        for (int rep = 0; rep < 5; ++rep)
+        for (int rep = 0; rep < kTuneReps; ++rep)
           if ((status = transfer_run(L, p, r, s, 1, st)) != MCMG_OK) break;
         if (status != MCMG_OK) break;
         cudaEventRecord(e1, st);
