@@ -33,13 +33,13 @@ static constexpr Shape kShapes[] = {{0, 8, 1, 0}, {0, 2, 1, 0}, {0, 1, 1, 0}, {0
                                     {0, 1, 4, 0}, {1, 1, 1, 0}, {2, 8, 4, 4}, {2, 4, 4, 4},
                                     {2, 8, 4, 2}, {2, 4, 4, 2}, {2, 8, 4, 8}, {2, 4, 4, 8},
                                     {3, 8, 4, 4}, {3, 4, 4, 4}, {3, 4, 4, 8},
-                                    {4, 1, 8, 0}, {4, 1, 4, 0}};
+                                    {4, 1, 8, 0}, {4, 1, 4, 0}, {4, 1, 2, 0}};
 static constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 static constexpr int kTunePasses = 3, kTuneReps = 10;   // autotuner timing
 
 static bool shape_ok(int s, int C, int D) {
   const Shape& k = kShapes[s];
-  if (k.kind == 4) return (C == 4 || C == 8 || C == 16) && k.co <= C && C / k.co <= 4;
+  if (k.kind == 4) return (C == 4 || C == 8 || C == 16 || C == 32) && k.co <= C && C / k.co <= 16;
   if (k.kind == 1) return C >= 8;
   if (k.kind == 2 || k.kind == 3) {
     if (k.kind == 3 && C < 8) return false;
@@ -357,7 +357,7 @@ static mcmg_status smooth_ks(const SmoothParams& p, int mode, int nrhs, cudaStre
   }
 }
 
-// Thread-per-node smoothing step for few channels (C = 4, 8, 16).  G = C / CT
+// Thread-per-node smoothing step for few channels (C = 4 .. 32).  G = C / CT
 // adjacent lanes share a node, each owning CT output channels; a block covers
 // 256 / G nodes.  Every mixing matrix of the step sits in shared memory and is
 // read as a broadcast (all nodes' lanes read the same weights); each lane loads
@@ -369,12 +369,13 @@ template <int C, int D, int MODE, int CT>
 __global__ void __launch_bounds__(256) k_smooth_tpn(SmoothParams p) {
   pdl_launch_dependents();
   constexpr int G = C / CT, NPB = 256 / G, NT = 2 * D + 1, MSZ = C * C, NM = NT + 3;
-  __shared__ __align__(16) float2 Wsm[NM * MSZ];   // taps, K_A, K_S, W^(i)
+  extern __shared__ float4 wsm4[];
+  float2* Wsm = reinterpret_cast<float2*>(wsm4);   // [NM][C][C]: taps, K_A, K_S, W^(i)
   for (int i = threadIdx.x; i < NM * MSZ / 2; i += 256) {   // setup-time data
     const int m = (2 * i) / MSZ, o = (2 * i) % MSZ;
     const float2* src = m < NT ? p.Wt + (size_t)m * MSZ
                                : (m == NT ? p.KAt : (m == NT + 1 ? p.KSt : p.Wst));
-    reinterpret_cast<float4*>(Wsm)[i] = __ldg(reinterpret_cast<const float4*>(src + o));
+    wsm4[i] = __ldg(reinterpret_cast<const float4*>(src + o));
   }
   __syncthreads();
   pdl_wait();
@@ -504,7 +505,8 @@ __global__ void __launch_bounds__(256) k_smooth_tpn(SmoothParams p) {
 
 template <int C, int CT>
 constexpr bool tpn_valid() {
-  return (C == 4 || C == 8 || C == 16) && (CT == 4 || CT == 8) && CT <= C && C / CT <= 4;
+  return (C == 4 || C == 8 || C == 16 || C == 32) && (CT == 2 || CT == 4 || CT == 8) && CT <= C &&
+         C / CT <= 16;
 }
 
 template <int C, int D, int CT>
@@ -514,11 +516,19 @@ static mcmg_status smooth_tpn(const SmoothParams& p, int mode, int nrhs, cudaStr
     return MCMG_ERR_SHAPE;
   } else {
     constexpr int NPB = 256 / (C / CT);
+    constexpr size_t smem = (size_t)(2 * D + 4) * C * C * sizeof(float2);
     dim3 grid((unsigned)((p.nodes + NPB - 1) / NPB), (unsigned)nrhs);
-    if (mode == 0)
-      MCMG_LAUNCH_PDL((k_smooth_tpn<C, D, 0, CT>), grid, dim3(256), 0, st, p);
-    else
-      MCMG_LAUNCH_PDL((k_smooth_tpn<C, D, 1, CT>), grid, dim3(256), 0, st, p);
+    if (mode == 0) {
+      if (smem > 48 * 1024)
+        MCMG_CUDA(cudaFuncSetAttribute(k_smooth_tpn<C, D, 0, CT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MCMG_LAUNCH_PDL((k_smooth_tpn<C, D, 0, CT>), grid, dim3(256), smem, st, p);
+    } else {
+      if (smem > 48 * 1024)
+        MCMG_CUDA(cudaFuncSetAttribute(k_smooth_tpn<C, D, 1, CT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MCMG_LAUNCH_PDL((k_smooth_tpn<C, D, 1, CT>), grid, dim3(256), smem, st, p);
+    }
     MCMG_CHECK_LAUNCH("smooth_tpn");
     return MCMG_OK;
   }
@@ -535,6 +545,7 @@ static mcmg_status smooth_c(const SmoothParams& p, int mode, int shape, int nrhs
     case 5: return smooth_ks<C, D>(p, mode, nrhs, st);
     case 15: return smooth_tpn<C, D, 8>(p, mode, nrhs, st);
     case 16: return smooth_tpn<C, D, 4>(p, mode, nrhs, st);
+    case 17: return smooth_tpn<C, D, 2>(p, mode, nrhs, st);
     default:
       return smooth_rt_launch(p, C, D, mode, kShapes[shape].tn, kShapes[shape].co,
                               kShapes[shape].kq, kShapes[shape].kind == 3, nrhs, st);
