@@ -64,8 +64,6 @@ struct CTraits<double2> {
 template <typename C2, typename X2 = C2>
 __global__ void k_apply_A(const C2* __restrict__ q, const X2* __restrict__ x, C2* __restrict__ y,
                           Grid g) {
-  pdl_launch_dependents();
-  pdl_wait();
   using R = typename CTraits<C2>::R;
   long long N = g.nodes();
   long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -98,7 +96,7 @@ mcmg_status launch_apply_A32(const float2* q, const float2* x, float2* y, const 
                              int nrhs, cudaStream_t st) {
   long long N = g.nodes();
   dim3 grid((unsigned)((N + 255) / 256), (unsigned)nrhs);
-  MCMG_LAUNCH_PDL(k_apply_A<float2>, grid, dim3(256), 0, st, q, x, y, g);
+  k_apply_A<float2><<<grid, 256, 0, st>>>(q, x, y, g);
   MCMG_CHECK_LAUNCH("apply_A32");
   return MCMG_OK;
 }
@@ -107,7 +105,7 @@ mcmg_status launch_apply_A64(const double2* q, const double2* x, double2* y, con
                              int nrhs, cudaStream_t st) {
   long long N = g.nodes();
   dim3 grid((unsigned)((N + 255) / 256), (unsigned)nrhs);
-  MCMG_LAUNCH_PDL(k_apply_A<double2>, grid, dim3(256), 0, st, q, x, y, g);
+  k_apply_A<double2><<<grid, 256, 0, st>>>(q, x, y, g);
   MCMG_CHECK_LAUNCH("apply_A64");
   return MCMG_OK;
 }
@@ -116,7 +114,7 @@ mcmg_status launch_apply_A_mixed(const double2* q, const float2* x, double2* y, 
                                  int nrhs, cudaStream_t st) {
   long long N = g.nodes();
   dim3 grid((unsigned)((N + 255) / 256), (unsigned)nrhs);
-  MCMG_LAUNCH_PDL((k_apply_A<double2, float2>), grid, dim3(256), 0, st, q, x, y, g);
+  k_apply_A<double2, float2><<<grid, 256, 0, st>>>(q, x, y, g);
   MCMG_CHECK_LAUNCH("apply_A_mixed");
   return MCMG_OK;
 }
@@ -134,8 +132,6 @@ __global__ void __launch_bounds__(256) k_residual64(const double2* __restrict__ 
                                                     const double2* __restrict__ x,
                                                     double2* __restrict__ r,
                                                     double* __restrict__ part, Grid g) {
-  pdl_launch_dependents();
-  pdl_wait();
   long long N = g.nodes();
   size_t off = (size_t)blockIdx.y * N;
   const double2* xx = x + off;
@@ -183,7 +179,7 @@ __global__ void __launch_bounds__(256) k_residual64(const double2* __restrict__ 
 mcmg_status launch_residual64(const double2* q, const double2* f, const double2* x, double2* r,
                               double* part, int nblk, const Grid& g, int nrhs, cudaStream_t st) {
   dim3 grid((unsigned)nblk, (unsigned)nrhs);
-  MCMG_LAUNCH_PDL(k_residual64, grid, dim3(256), 0, st, q, f, x, r, part, g);
+  k_residual64<<<grid, 256, 0, st>>>(q, f, x, r, part, g);
   MCMG_CHECK_LAUNCH("residual64");
   return MCMG_OK;
 }

@@ -939,8 +939,6 @@ bool kernel_shape_valid(const Level& L, int op, int shape) {
 // ---------------------------------------------------------------------------
 __global__ void k_lift(const float2* __restrict__ r, const float2* __restrict__ lift,
                        float2* __restrict__ r1, int C, long long N) {
-  pdl_launch_dependents();
-  pdl_wait();
   long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= N * C) return;
   size_t off = (size_t)blockIdx.y * N;
@@ -949,8 +947,6 @@ __global__ void k_lift(const float2* __restrict__ r, const float2* __restrict__ 
 
 __global__ void k_project(const float2* __restrict__ e1, const float2* __restrict__ proj,
                           float2* __restrict__ e, int C, long long N) {
-  pdl_launch_dependents();
-  pdl_wait();
   long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   size_t off = (size_t)blockIdx.y * N;
@@ -963,8 +959,6 @@ __global__ void k_project(const float2* __restrict__ e1, const float2* __restric
 // Batched forms: field k of the batch reads srcs[k] / writes dsts[k].
 __global__ void k_lift_gather(const float2* const* __restrict__ srcs, const float2* __restrict__ lift,
                               float2* __restrict__ r1, int C, long long N) {
-  pdl_launch_dependents();
-  pdl_wait();
   long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= N * C) return;
   const float2* r = srcs[blockIdx.y];
@@ -973,8 +967,6 @@ __global__ void k_lift_gather(const float2* const* __restrict__ srcs, const floa
 
 __global__ void k_project_scatter(const float2* __restrict__ e1, const float2* __restrict__ proj,
                                   float2* const* __restrict__ dsts, int C, long long N) {
-  pdl_launch_dependents();
-  pdl_wait();
   long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const float2* src = e1 + ((size_t)blockIdx.y * N + n) * C;
@@ -986,7 +978,7 @@ __global__ void k_project_scatter(const float2* __restrict__ e1, const float2* _
 mcmg_status launch_lift_gather(const float2* const* srcs, const float2* lift, float2* r1, int C,
                                long long nodes, int count, cudaStream_t st) {
   dim3 grid((unsigned)((nodes * C + 255) / 256), (unsigned)count);
-  MCMG_LAUNCH_PDL(k_lift_gather, grid, dim3(256), 0, st, srcs, lift, r1, C, nodes);
+  k_lift_gather<<<grid, 256, 0, st>>>(srcs, lift, r1, C, nodes);
   MCMG_CHECK_LAUNCH("lift_gather");
   return MCMG_OK;
 }
@@ -994,7 +986,7 @@ mcmg_status launch_lift_gather(const float2* const* srcs, const float2* lift, fl
 mcmg_status launch_project_scatter(const float2* e1, const float2* proj, float2* const* dsts, int C,
                                    long long nodes, int count, cudaStream_t st) {
   dim3 grid((unsigned)((nodes + 255) / 256), (unsigned)count);
-  MCMG_LAUNCH_PDL(k_project_scatter, grid, dim3(256), 0, st, e1, proj, dsts, C, nodes);
+  k_project_scatter<<<grid, 256, 0, st>>>(e1, proj, dsts, C, nodes);
   MCMG_CHECK_LAUNCH("project_scatter");
   return MCMG_OK;
 }
@@ -1002,7 +994,7 @@ mcmg_status launch_project_scatter(const float2* e1, const float2* proj, float2*
 mcmg_status launch_lift(const float2* r, const float2* lift, float2* r1, int C, long long nodes,
                         int nrhs, cudaStream_t st) {
   dim3 grid((unsigned)((nodes * C + 255) / 256), (unsigned)nrhs);
-  MCMG_LAUNCH_PDL(k_lift, grid, dim3(256), 0, st, r, lift, r1, C, nodes);
+  k_lift<<<grid, 256, 0, st>>>(r, lift, r1, C, nodes);
   MCMG_CHECK_LAUNCH("lift");
   return MCMG_OK;
 }
@@ -1010,7 +1002,7 @@ mcmg_status launch_lift(const float2* r, const float2* lift, float2* r1, int C, 
 mcmg_status launch_project(const float2* e1, const float2* proj, float2* e, int C,
                            long long nodes, int nrhs, cudaStream_t st) {
   dim3 grid((unsigned)((nodes + 255) / 256), (unsigned)nrhs);
-  MCMG_LAUNCH_PDL(k_project, grid, dim3(256), 0, st, e1, proj, e, C, nodes);
+  k_project<<<grid, 256, 0, st>>>(e1, proj, e, C, nodes);
   MCMG_CHECK_LAUNCH("project");
   return MCMG_OK;
 }

@@ -96,8 +96,6 @@ template <typename WT>
 __global__ void __launch_bounds__(RED_T) k_multidot(const float2* __restrict__ V, long long ldv,
                                                     int k, int ktot, const WT* __restrict__ w,
                                                     long long n, double* __restrict__ part) {
-  pdl_launch_dependents();
-  pdl_wait();
   const int i0 = blockIdx.y * KV;
   DF ar[KV], ai[KV];
 #pragma unroll
@@ -165,8 +163,6 @@ __device__ __forceinline__ double2 block_sum2(double a, double b) {
 __global__ void __launch_bounds__(RED_T) k_reduce_parts(const double* __restrict__ part, int nblk,
                                                         int width, double2* __restrict__ out,
                                                         double2* out_host) {
-  pdl_launch_dependents();
-  pdl_wait();
   const int i = blockIdx.x;
   double a = 0.0, b = 0.0;
   for (int q = threadIdx.x; q < nblk; q += RED_T) {
@@ -189,8 +185,6 @@ __global__ void __launch_bounds__(RED_T) k_update(const float2* __restrict__ V, 
                                                   const double2* __restrict__ hc,
                                                   WT* __restrict__ w, long long n,
                                                   double* __restrict__ part) {
-  pdl_launch_dependents();
-  pdl_wait();
   extern __shared__ DF hs[];   // [k][2]
   for (int i = threadIdx.x; i < k; i += RED_T) {
     const double2 hh = hc[i];
@@ -241,15 +235,13 @@ static mcmg_status launch_update(const float2* V, long long ldv, int k, const do
   if (smem > 48 * 1024)
     MCMG_CUDA(cudaFuncSetAttribute(k_update<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
-  MCMG_LAUNCH_PDL(k_update<WT>, dim3(nblk), dim3(RED_T), smem, st, V, ldv, k, hc, w, n, part);
+  k_update<WT><<<nblk, RED_T, smem, st>>>(V, ldv, k, hc, w, n, part);
   MCMG_CHECK_LAUNCH("update");
   return MCMG_OK;
 }
 
 __global__ void __launch_bounds__(RED_T) k_reduce_scalar(const double* __restrict__ part, int nblk,
                                                          double* out, double* out_host) {
-  pdl_launch_dependents();
-  pdl_wait();
   double a = 0.0;
   for (int q = threadIdx.x; q < nblk; q += RED_T) a += part[q];
   const double2 r = block_sum2(a, 0.0);
@@ -263,8 +255,6 @@ __global__ void __launch_bounds__(RED_T) k_reduce_scalar(const double* __restric
 __global__ void __launch_bounds__(RED_T) k_reduce_res(const double* __restrict__ part, int nblk,
                                                       double* __restrict__ dsc,
                                                       double* __restrict__ stat_rr) {
-  pdl_launch_dependents();
-  pdl_wait();
   double a = 0.0, b = 0.0;
   for (int q = threadIdx.x; q < nblk; q += RED_T) { a += part[2 * q]; b += part[2 * q + 1]; }
   const double2 r = block_sum2(a, b);
@@ -279,8 +269,6 @@ __global__ void __launch_bounds__(RED_T) k_reduce_res(const double* __restrict__
 // v0 = r / beta (to complex64)
 __global__ void k_start_cycle(const double2* __restrict__ r, const double* __restrict__ dsc,
                               float2* __restrict__ v0, long long n) {
-  pdl_launch_dependents();
-  pdl_wait();
   const double beta = sqrt(dsc[0]);
   const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -297,8 +285,6 @@ struct Stat {
 // v_{j+1} = w / sqrt(nrm2)
 __global__ void k_scale(const double2* __restrict__ w, const double* __restrict__ dsc,
                         float2* __restrict__ v, long long n) {
-  pdl_launch_dependents();
-  pdl_wait();
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const double hn = sqrt(dsc[3]);
@@ -310,8 +296,6 @@ __global__ void k_scale(const double2* __restrict__ w, const double* __restrict_
 // Stationary step: u += beta * z, beta = ||r|| (the V-cycle ran on r / beta).
 __global__ void k_stationary_update(const float2* __restrict__ z, const double* __restrict__ dsc,
                                     double2* __restrict__ u, long long n) {
-  pdl_launch_dependents();
-  pdl_wait();
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const double beta = sqrt(dsc[0]);
@@ -323,8 +307,6 @@ __global__ void k_stationary_update(const float2* __restrict__ z, const double* 
 // u += sum_{i<k} y_i Z_i (complex128 accumulate)
 __global__ void k_update_x(const float2* __restrict__ Z, long long ldz, int k,
                            const double2* __restrict__ y, double2* __restrict__ u, long long n) {
-  pdl_launch_dependents();
-  pdl_wait();
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   double sr = 0.0, si = 0.0;
@@ -461,7 +443,7 @@ void krylov_destroy(mcmg_handle_s* h, Krylov* k) {
 static mcmg_status enqueue_restart(Krylov* k) {
   mcmg_handle_s* h = k->h;
   MCMG_TRY(launch_residual64(h->q64, k->f, k->u, k->r64, k->part, k->nblk, h->g0, 1, k->st));
-  MCMG_LAUNCH_PDL(k_reduce_res, dim3(1), dim3(RED_T), 0, k->st, k->part, k->nblk, k->dsc, &k->stat_d->rr);
+  k_reduce_res<<<1, RED_T, 0, k->st>>>(k->part, k->nblk, k->dsc, &k->stat_d->rr);
   MCMG_CHECK_LAUNCH("reduce_res");
   MCMG_CUDA(cudaEventRecord(k->ev, k->st));
   k->phase = Krylov::WAIT_RES;
@@ -471,9 +453,9 @@ static mcmg_status enqueue_restart(Krylov* k) {
 static mcmg_status multidot(Krylov* k, int nv, bool self, double2* out, double2* out_host) {
   const int ktot = nv + (self ? 1 : 0);
   dim3 grid((unsigned)k->nblk, (unsigned)((ktot + KV - 1) / KV));
-  MCMG_LAUNCH_PDL(k_multidot<double2>, grid, dim3(RED_T), 0, k->st, k->V, k->n, nv, ktot, k->w, k->n, k->part);
+  k_multidot<double2><<<grid, RED_T, 0, k->st>>>(k->V, k->n, nv, ktot, k->w, k->n, k->part);
   MCMG_CHECK_LAUNCH("multidot");
-  MCMG_LAUNCH_PDL(k_reduce_parts, dim3(ktot), dim3(RED_T), 0, k->st, k->part, k->nblk, ktot, out, out_host);
+  k_reduce_parts<<<ktot, RED_T, 0, k->st>>>(k->part, k->nblk, ktot, out, out_host);
   MCMG_CHECK_LAUNCH("reduce_parts");
   return MCMG_OK;
 }
@@ -490,11 +472,11 @@ static mcmg_status enqueue_arnoldi(Krylov* k, int j) {
   MCMG_TRY(launch_update(k->V, n, j + 1, k->d1, k->w, n, k->part, k->nblk, k->st));
   MCMG_TRY(multidot(k, j + 1, false, k->d2, mir + (k->m + 2)));
   MCMG_TRY(launch_update(k->V, n, j + 1, k->d2, k->w, n, k->part, k->nblk, k->st));
-  MCMG_LAUNCH_PDL(k_reduce_scalar, dim3(1), dim3(RED_T), 0, k->st, k->part, k->nblk, k->dsc + 3,
+  k_reduce_scalar<<<1, RED_T, 0, k->st>>>(k->part, k->nblk, k->dsc + 3,
                                           &mir[2 * k->m + 4].x);
   MCMG_CHECK_LAUNCH("reduce_scalar");
   if (j + 1 <= k->m) {
-    MCMG_LAUNCH_PDL(k_scale, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, k->st, k->w, k->dsc, k->V + (size_t)(j + 1) * n, n);
+    k_scale<<<(unsigned)((n + 255) / 256), 256, 0, k->st>>>(k->w, k->dsc, k->V + (size_t)(j + 1) * n, n);
     MCMG_CHECK_LAUNCH("scale");
   }
   k->phase = Krylov::WAIT_STEP;
@@ -580,7 +562,7 @@ static void host_backsolve(Krylov* k, int kk) {
 static mcmg_status enqueue_finish_cycle(Krylov* k, int kk) {
   host_backsolve(k, kk);
   MCMG_CUDA(cudaMemcpyAsync(k->y, k->y_h, sizeof(double2) * kk, cudaMemcpyHostToDevice, k->st));
-  MCMG_LAUNCH_PDL(k_update_x, dim3((unsigned)((k->n + 255) / 256)), dim3(256), 0, k->st, k->Z, k->n, kk, k->y, k->u, k->n);
+  k_update_x<<<(unsigned)((k->n + 255) / 256), 256, 0, k->st>>>(k->Z, k->n, kk, k->y, k->u, k->n);
   MCMG_CHECK_LAUNCH("update_x");
   k->restarts += 1;
   return enqueue_restart(k);
@@ -652,7 +634,7 @@ mcmg_status krylov_advance(Krylov* k, bool blocking, int* done) {
       *done = 1;
       return MCMG_OK;
     }
-    MCMG_LAUNCH_PDL(k_start_cycle, dim3((unsigned)((k->n + 255) / 256)), dim3(256), 0, k->st, k->r64, k->dsc, k->V, k->n);
+    k_start_cycle<<<(unsigned)((k->n + 255) / 256), 256, 0, k->st>>>(k->r64, k->dsc, k->V, k->n);
     MCMG_CHECK_LAUNCH("start_cycle");
     std::fill(k->g.begin(), k->g.end(), 0.0);
     k->g[0] = beta;
@@ -711,7 +693,7 @@ mcmg_status stationary_run(Krylov* k, const double2* f, double2* u, const mcmg_s
   bool conv = false;
   for (;; ++it) {
     MCMG_TRY(launch_residual64(h->q64, f, u, k->r64, k->part, k->nblk, h->g0, 1, st));
-    MCMG_LAUNCH_PDL(k_reduce_res, dim3(1), dim3(RED_T), 0, st, k->part, k->nblk, k->dsc, &k->stat_d->rr);
+    k_reduce_res<<<1, RED_T, 0, st>>>(k->part, k->nblk, k->dsc, &k->stat_d->rr);
     MCMG_CHECK_LAUNCH("reduce_res");
     MCMG_CUDA(cudaStreamSynchronize(st));
     Stat sv;
@@ -722,10 +704,10 @@ mcmg_status stationary_run(Krylov* k, const double2* f, double2* u, const mcmg_s
     if (rel <= o.tol) { conv = true; break; }
     if (it >= max_iters) { fs = MCMG_ERR_NOT_CONVERGED; break; }
     if (h->err_host && *(volatile int*)h->err_host) { fs = MCMG_ERR_TIMEOUT; break; }
-    MCMG_LAUNCH_PDL(k_start_cycle, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, k->r64, k->dsc, k->V, n);
+    k_start_cycle<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(k->r64, k->dsc, k->V, n);
     MCMG_CHECK_LAUNCH("start_cycle");
     MCMG_TRY(vcycle_run(h, k->vw, k->V, k->Z, 1, st));
-    MCMG_LAUNCH_PDL(k_stationary_update, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, k->Z, k->dsc, u, n);
+    k_stationary_update<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(k->Z, k->dsc, u, n);
     MCMG_CHECK_LAUNCH("stationary_update");
   }
   if (info) {
@@ -837,7 +819,7 @@ static mcmg_status member_process(Krylov* k) {
       finish(k, false, MCMG_ERR_NOT_CONVERGED);
       return MCMG_OK;
     }
-    MCMG_LAUNCH_PDL(k_start_cycle, dim3((unsigned)((k->n + 255) / 256)), dim3(256), 0, k->st, k->r64, k->dsc, k->V, k->n);
+    k_start_cycle<<<(unsigned)((k->n + 255) / 256), 256, 0, k->st>>>(k->r64, k->dsc, k->V, k->n);
     MCMG_CHECK_LAUNCH("start_cycle");
     std::fill(k->g.begin(), k->g.end(), 0.0);
     k->g[0] = beta;
@@ -938,13 +920,13 @@ mcmg_status cgs2_once(mcmg_handle_s* h, const float2* V, int kv, long long n, fl
     dim3 grid((unsigned)nblk, (unsigned)((kv + KV - 1) / KV));
     for (int pass = 0; pass < 2; ++pass) {
       double2* dd = pass == 0 ? d1 : d2;
-      MCMG_LAUNCH_PDL(k_multidot<float2>, grid, dim3(RED_T), 0, st, V, n, kv, kv, w, n, part);
+      k_multidot<float2><<<grid, RED_T, 0, st>>>(V, n, kv, kv, w, n, part);
       MCMG_CHECK_LAUNCH("multidot");
-      MCMG_LAUNCH_PDL(k_reduce_parts, dim3(kv), dim3(RED_T), 0, st, part, nblk, kv, dd, (double2*)nullptr);
+      k_reduce_parts<<<kv, RED_T, 0, st>>>(part, nblk, kv, dd, nullptr);
       MCMG_CHECK_LAUNCH("reduce_parts");
       MCMG_TRY(launch_update(V, n, kv, dd, w, n, part, nblk, st));
     }
-    MCMG_LAUNCH_PDL(k_reduce_scalar, dim3(1), dim3(RED_T), 0, st, part, nblk, dsc, (double*)nullptr);
+    k_reduce_scalar<<<1, RED_T, 0, st>>>(part, nblk, dsc, nullptr);
     MCMG_CHECK_LAUNCH("reduce_scalar");
     std::vector<double2> a(kv), b(kv);
     double nrm2 = 0.0;
@@ -1041,13 +1023,13 @@ mcmg_status mcmg_cgs2_noalloc(const void* V_dev, int k, size_t n, void* w_dev, d
   dim3 grid((unsigned)nblk, (unsigned)((k + KV - 1) / KV));
   for (int pass = 0; pass < 2; ++pass) {
     double2* dd = pass == 0 ? d1 : d2;
-    MCMG_LAUNCH_PDL(k_multidot<float2>, grid, dim3(RED_T), 0, st, V, nn, k, k, w, nn, part);
+    k_multidot<float2><<<grid, RED_T, 0, st>>>(V, nn, k, k, w, nn, part);
     MCMG_CHECK_LAUNCH("multidot");
-    MCMG_LAUNCH_PDL(k_reduce_parts, dim3(k), dim3(RED_T), 0, st, part, nblk, k, dd, (double2*)nullptr);
+    k_reduce_parts<<<k, RED_T, 0, st>>>(part, nblk, k, dd, nullptr);
     MCMG_CHECK_LAUNCH("reduce_parts");
     MCMG_TRY(launch_update(V, nn, k, dd, w, nn, part, nblk, st));
   }
-  MCMG_LAUNCH_PDL(k_reduce_scalar, dim3(1), dim3(RED_T), 0, st, part, nblk, dsc, (double*)nullptr);
+  k_reduce_scalar<<<1, RED_T, 0, st>>>(part, nblk, dsc, nullptr);
   MCMG_CHECK_LAUNCH("reduce_scalar");
   k_sum_coeffs<<<(k + 127) / 128, 128, 0, st>>>(d1, d2, k, part);   // part is free again
   MCMG_CHECK_LAUNCH("sum_coeffs");

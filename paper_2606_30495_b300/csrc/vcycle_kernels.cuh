@@ -2,10 +2,45 @@
 // translation units (kernels_vcycle.cu, kernels_smooth_rt.cu,
 // kernels_transfer_rt.cu).
 #pragma once
+#include <utility>
+
 #include "mcmg_internal.cuh"
 
 namespace mcmg {
 
+// Programmatic dependent launch.  The V-cycle's kernels are launched so that
+// each may start while its predecessor drains: a kernel first lets its own
+// dependents launch, reads only setup-time data (weights, features) before
+// pdl_wait(), and touches fields written by earlier kernels only after it.
+// pdl_wait() returns once every prerequisite grid has completed and its
+// memory is visible; both are no-ops in a kernel launched without the
+// attribute.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+#define MCMG_LAUNCH_PDL(kernel, grid, block, smem, st, ...)                      \
+  do {                                                                          \
+    cudaError_t _e = ::mcmg::launch_pdl(kernel, grid, block, smem, st, __VA_ARGS__); \
+    if (_e != cudaSuccess) return ::mcmg::cuda_fail(_e, #kernel);              \
+  } while (0)
 
 template <int C, int TN_, int CO_>
 struct Tile {
