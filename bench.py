@@ -341,6 +341,7 @@ def run_serving(args):
         un = bufs[k][1].cpu().numpy()
         for j in range(r["nrhs"]):
             worst = max(worst, float(np.linalg.norm(f[j] - O.apply_A(q, un[j])) / np.linalg.norm(f[j])))
+    dev_err = [h.device_error() for h in handles]
     for h in handles:
         h.close()
     ctx.close()
@@ -358,6 +359,8 @@ def run_serving(args):
                        "iters": plain_iters},
         "speedup_vs_plain": served_rate / plain_rate,
         "served_iters": [done[k][2]["iters"] for k in range(len(reqs))],
+        "served_status": [mcmg.STATUS.get(done[k][1], done[k][1]) for k in range(len(reqs))],
+        "served_device_error": dev_err,
         "converged": conv, "worst_true_rel_residual": worst, "gpu_launches": int(launches),
     }
     print(json.dumps(out))
