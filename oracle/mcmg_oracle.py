@@ -23,6 +23,7 @@ Functions and the passage each one follows:
 * ``fgmres``             -- flexible GMRES(m), right preconditioned (the paper's
   GMRES+McMg, Section 3.3 and Table 2, in Saad's flexible form)
 * ``stationary_solve``   -- the stationary McMg iteration (Eq. mcmg_iteration)
+* ``coarse_basis``       -- raw coarse-basis response (Eq. coarse_basis)
 * ``dense_matrix``       -- brute-force dense assembly for tiny grids
 
 Readings where the paper is silent (each is a parameter or stated here):
@@ -312,6 +313,21 @@ def vcycle(wts: dict, feats, r: np.ndarray) -> np.ndarray:
 # --------------------------------------------------------------------------
 # outer iterations
 # --------------------------------------------------------------------------
+
+
+def coarse_basis(wts: dict, level: int, index, channel: int, fine_shape) -> np.ndarray:
+    """Raw coarse-basis response of Eq. coarse_basis (Section 3.4): the one-hot
+    latent tensor delta_alpha at grid location `index` (slowest axis first)
+    and channel `channel` of `level` (0-based, >= 1), carried to the finest
+    level by the learned prolongations in turn, then mapped to a scalar field
+    by g_proj."""
+    lv = wts["lvl"]
+    shapes = [tuple(n >> l for n in fine_shape) for l in range(wts["levels"])]
+    y = np.zeros(shapes[level] + (wts["channels"][level],), dtype=np.complex128)
+    y[tuple(index) + (channel,)] = 1.0
+    for l in range(level - 1, -1, -1):
+        y = prolong(lv[l]["P"], y, shapes[l])
+    return y @ wts["proj"]
 
 
 def _norm(x):

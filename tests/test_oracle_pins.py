@@ -441,3 +441,46 @@ def test_fgmres_restarted_counts_iterations_and_converges():
     _, info = O.fgmres(A, lambda v: O.vcycle(w, feats, v), f, m=3, tol=1e-8)
     assert info["converged"] and info["restarts"] >= 2
     assert info["iters"] >= 3 * (info["restarts"] - 1)
+
+
+# ---------------------------------------------------------------------------
+# Coarse-basis response (Eq. coarse_basis)
+# ---------------------------------------------------------------------------
+
+def _tent(shape, centre, half):
+    """Tensor-product hat of half-width `half` (the bilinear / trilinear
+    interpolant of a unit spike on a grid `half` times coarser)."""
+    out = np.ones(shape)
+    for ax, (n, c) in enumerate(zip(shape, centre)):
+        t = np.clip(1.0 - np.abs(np.arange(n) - c) / half, 0.0, None)
+        out = out * t.reshape([-1 if a == ax else 1 for a in range(len(shape))])
+    return out
+
+
+@pytest.mark.parametrize("shape,levels,level,index", [
+    ((32, 32), 3, 2, (4, 3)),
+    ((32, 32), 3, 1, (5, 9)),
+    ((16, 16, 16), 2, 1, (3, 4, 2)),
+])
+def test_coarse_basis_of_classical_multigrid_is_the_tent(shape, levels, level, index):
+    """With the classical one-channel weights every prolongation is bilinear
+    (trilinear) interpolation and g_proj the identity, so the response of a
+    spike at coarse node J of level l is the hat of half-width 2^l centred at
+    2^l J (interior J, so the zero boundary does not clip it)."""
+    d = len(shape)
+    pre, post = I.nu_schedule(levels, degenerate=True)
+    w = I.make_weights(d, [1] * levels, pre, post, mode="degenerate", seed=0)
+    got = O.coarse_basis(w, level, index, 0, shape)
+    want = _tent(shape, [i << level for i in index], float(1 << level))
+    assert np.max(np.abs(got - want)) < 1e-14
+
+
+def test_coarse_basis_applies_g_proj_last():
+    """g_proj is applied once, last: scaling it scales the response by the
+    same complex factor."""
+    shape, levels = (16, 16), 2
+    pre, post = I.nu_schedule(levels, degenerate=True)
+    w = I.make_weights(2, [1] * levels, pre, post, mode="degenerate", seed=0)
+    base = O.coarse_basis(w, 1, (3, 4), 0, shape)
+    w["proj"] = w["proj"] * (2.5 - 1.0j)
+    assert np.max(np.abs(O.coarse_basis(w, 1, (3, 4), 0, shape) - (2.5 - 1.0j) * base)) < 1e-14
