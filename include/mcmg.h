@@ -243,6 +243,17 @@ mcmg_status mcmg_residual_restrict(mcmg_handle h, int level, const void* r_dev,
 mcmg_status mcmg_prolong_add(mcmg_handle h, int level, const void* e_coarse_dev,
                              void* e_dev, int nrhs, void* stream);
 
+/* Raw coarse-basis response (Eq. coarse_basis, Section 3.4):
+ *   Psi = g_proj(P_1 P_2 ... P_level (delta_alpha)),
+ * delta_alpha the one-hot latent field at node `node` (linear index on that
+ * level's grid, x fastest) and channel `channel` of `level` (1 <= level <
+ * levels).  out_dev: dev c64 [nodes_0].  Enqueued on `stream`; uses the
+ * handle's V-cycle workspace, so it must not overlap an mcmg_vcycle or
+ * single-step call on another stream.  MCMG_ERR_ARG for an out-of-range
+ * level, node or channel.                                                     */
+mcmg_status mcmg_coarse_basis(mcmg_handle h, int level, long long node, int channel,
+                              void* out_dev, void* stream);
+
 /* Classical Gram-Schmidt with one re-orthogonalisation (CGS2) against k
  * basis vectors, FP64 accumulation:  h = V^H w, w -= V h (twice, h summed),
  * norm = ||w||.  V: dev c64 [k][n]; w: dev c64 [n], updated in place;

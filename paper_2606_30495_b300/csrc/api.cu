@@ -798,6 +798,33 @@ mcmg_status mcmg_residual_restrict(mcmg_handle h, int level, const void* r, cons
   return launch_restrict(lv, h->work->t[level], (float2*)rc, nrhs, st);
 }
 
+mcmg_status mcmg_coarse_basis(mcmg_handle h, int level, long long node, int channel, void* out,
+                              void* stream) {
+  if (!h || !out || level < 1 || level >= h->L || channel < 0 || channel >= h->lv[level].C ||
+      node < 0 || node >= h->lv[level].g.nodes()) {
+    set_error("bad argument");
+    return MCMG_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(h->mu);
+  MCMG_CUDA(cudaSetDevice(h->device));
+  MCMG_TRY(ensure_work(h, 1));
+  cudaStream_t st = (cudaStream_t)stream;
+  VWork* w = h->work;
+  const Level& top = h->lv[level];
+  // delta_alpha on `level`, then P_l for l = level-1 .. 0 into zeroed fields
+  MCMG_CUDA(cudaMemsetAsync(w->e[level], 0, sizeof(float2) * top.g.nodes() * top.C, st));
+  const float2 one = make_float2(1.f, 0.f);
+  MCMG_CUDA(cudaMemcpyAsync(w->e[level] + node * top.C + channel, &one, sizeof(float2),
+                            cudaMemcpyHostToDevice, st));
+  for (int l = level - 1; l >= 0; --l) {
+    const Level& lv = h->lv[l];
+    MCMG_CUDA(cudaMemsetAsync(w->e[l], 0, sizeof(float2) * lv.g.nodes() * lv.C, st));
+    MCMG_TRY(launch_prolong_add(lv, w->e[l + 1], w->e[l], 1, st));
+  }
+  const Level& l0 = h->lv[0];
+  return launch_project(w->e[0], h->proj, (float2*)out, l0.C, l0.g.nodes(), 1, st);
+}
+
 mcmg_status mcmg_prolong_add(mcmg_handle h, int level, const void* ec, void* e, int nrhs,
                              void* stream) {
   MCMG_TRY(check_level(h, level, true));

@@ -81,6 +81,7 @@ _SIGS = {
     "mcmg_smooth": [_P, C.c_int, C.c_int, _P, _P, _P, C.c_int, _P],
     "mcmg_residual_restrict": [_P, C.c_int, _P, _P, _P, C.c_int, _P],
     "mcmg_prolong_add": [_P, C.c_int, _P, _P, C.c_int, _P],
+    "mcmg_coarse_basis": [_P, C.c_int, C.c_longlong, C.c_int, _P, _P],
     "mcmg_cgs2": [_P, _P, C.c_int, C.c_size_t, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "mcmg_cgs2_noalloc": [_P, C.c_int, C.c_size_t, _P, C.POINTER(C.c_double),
                           C.POINTER(C.c_double), _P],
@@ -333,6 +334,11 @@ class Handle:
 
     def prolong_add(self, level, ec, e, nrhs=1, stream=None):
         _check(self.lib.mcmg_prolong_add(self.h, level, ptr(ec), ptr(e), nrhs, _stream(stream)))
+
+    def coarse_basis(self, level, node, channel, out, stream=None):
+        """Raw coarse-basis response of (level, node, channel) into `out`
+        (complex64, finest grid)."""
+        _check(self.lib.mcmg_coarse_basis(self.h, level, node, channel, ptr(out), _stream(stream)))
 
     def cgs2(self, V, w):
         k = V.shape[0]

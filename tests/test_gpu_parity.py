@@ -229,6 +229,28 @@ def test_every_kernel_shape(case):
                 h.set_kernel_shape(l, op, -1)
 
 
+def test_coarse_basis(case):
+    """Raw coarse-basis response (Eq. coarse_basis) through the C ABI against
+    the oracle, for random (level, node, channel) on every case; out-of-range
+    arguments are refused."""
+    from paper_2606_30495_b300 import mcmg
+    m, h = case
+    w = m["w"]
+    g = rng(60)
+    out = torch.zeros(m["shape"], dtype=torch.complex64, device="cuda")
+    for level in range(1, w["levels"]):
+        cshape = tuple(n >> level for n in m["shape"])
+        for _ in range(2):
+            idx = tuple(int(g.integers(0, n)) for n in cshape)
+            ch = int(g.integers(0, w["channels"][level]))
+            h.coarse_basis(level, int(np.ravel_multi_index(idx, cshape)), ch, out)
+            want = O.coarse_basis(w, level, idx, ch, m["shape"])
+            assert relerr(host(out), want) < TOL32, (level, idx, ch)
+    for bad in ((0, 0, 0), (w["levels"], 0, 0), (1, -1, 0), (1, 0, w["channels"][1])):
+        with pytest.raises(mcmg.McmgError):
+            h.coarse_basis(*bad, out)
+
+
 def test_vcycle_and_batch(case):
     m, h = case
     r = I.complex_normal((3,) + m["shape"], rng(40))
