@@ -64,6 +64,26 @@ def parse():
     return p.parse_args()
 
 
+def replica_total(total, world, device):
+    """Whole-job seconds of `world` replicas: every rank passes its own timed
+    region, all get the maximum (the job ends with the slowest replica).
+    One rank: unchanged.  Ends with a barrier."""
+    if world <= 1:
+        return total
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, total):
+    """Units per second of the whole job: what all replicas processed over
+    the job's (max-over-ranks) time."""
+    return units_per_rank * world / total
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -439,16 +459,11 @@ def main():
     torch.cuda.synchronize()
     launches = mcmg.kernel_launches() - launches0 - 0
     clocks = clk.stop()
-    total = sum(times)
-    if world > 1:
-        t = torch.tensor([total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-        dist.barrier()
+    total = replica_total(sum(times), world, "cuda")
     iters = [i["iters"] for _, i in infos]
     res = max(i["rel_residual"] for _, i in infos)
     conv = all(i["converged"] for _, i in infos)
-    value = args.steps * world / total
+    value = job_rate(args.steps, world, total)
 
     # final answer checked against the FP64 operator (oracle) on rank 0
     true_res = None
@@ -503,7 +518,7 @@ def main():
         h.solve_host(f_pin, u_pin, tol=wl["tol"], restart_m=sp["restart"],
                      max_iters=sp["max_iters"])
         e2e_times.append(time.perf_counter() - t1)
-    e2e_value = len(e2e_times) * world / sum(e2e_times)
+    e2e_value = job_rate(len(e2e_times), world, replica_total(sum(e2e_times), world, "cuda"))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
