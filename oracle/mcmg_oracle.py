@@ -24,6 +24,9 @@ Functions and the passage each one follows:
   GMRES+McMg, Section 3.3 and Table 2, in Saad's flexible form)
 * ``stationary_solve``   -- the stationary McMg iteration (Eq. mcmg_iteration)
 * ``coarse_basis``       -- raw coarse-basis response (Eq. coarse_basis)
+* ``born_background``, ``green_symbol``, ``apply_G``, ``born_solve`` -- the
+  Born+McMg variant with the discrete Green operator (Appendix, Born-series
+  variant; Eq. discrete_symbol)
 * ``dense_matrix``       -- brute-force dense assembly for tiny grids
 
 Readings where the paper is silent (each is a parameter or stated here):
@@ -425,6 +428,57 @@ def stationary_solve(A, M, f: np.ndarray, tol: float = 1e-6, max_iters: int = 10
         if rel <= tol or it == max_iters or not np.isfinite(rel):
             return u, dict(iters=it, rel_residual=rel, history=hist, converged=rel <= tol)
         u = u + M(r)
+
+
+# --------------------------------------------------------------------------
+# Born+McMg (Appendix, Born-series variant and discrete Green operator)
+# --------------------------------------------------------------------------
+
+
+def born_background(q: np.ndarray) -> complex:
+    """Background q0 = (k0 h)^2 of the Born-series form, V = q - q0.  The
+    paper leaves k0 open; reading: Re q0 halfway between the extremes of
+    Re q, and Im q0 = -max |q - Re q0| (the convergent-Born-series choice,
+    with the sponge's damping sign), so the background symbol never vanishes
+    and |V| <= |Im q0|."""
+    mid = 0.5 * (float(q.real.max()) + float(q.real.min()))
+    eps = float(np.abs(q - mid).max())
+    return complex(mid, -eps)
+
+
+def green_symbol(shape, q0: complex) -> np.ndarray:
+    """Fourier multiplier of G = (-Delta_h - k0^2)^{-1} in the h^2-scaled
+    system: 1 / (sum_a 4 sin^2(pi m_a / N_a) - q0), the discrete-Laplacian
+    symbol of Eq. discrete_symbol at xi_a h = 2 pi m_a / N_a (periodic modes,
+    the FFT used as a diagonalisation of the five-/seven-point operator)."""
+    mu = np.zeros(shape)
+    for ax, n in enumerate(shape):
+        sa = 4.0 * np.sin(np.pi * np.arange(n) / n) ** 2
+        mu = mu + sa.reshape([-1 if a == ax else 1 for a in range(len(shape))])
+    return 1.0 / (mu - q0)
+
+
+def apply_G(q0: complex, x: np.ndarray) -> np.ndarray:
+    """G x through the FFT (discrete Green operator)."""
+    return np.fft.ifftn(np.fft.fftn(x) * green_symbol(x.shape, q0))
+
+
+def born_solve(A, G, M, f: np.ndarray, tol: float = 1e-6, max_iters: int = 1000):
+    """Born+McMg: u <- u + MG(G(V u + f) - u), the Born-series residual taken
+    in the paper's equivalent form G(f - A u) with the solver's own A (zero
+    Dirichlet closure; G is the periodic background inverse, so the iteration
+    is the Helmholtz residual left-preconditioned by G and corrected by MG).
+    Stops on the Helmholtz residual ||f - A u|| / ||f||."""
+    u = np.zeros_like(f)
+    fnorm = _norm(f)
+    hist = []
+    for it in range(max_iters + 1):
+        r = f - A(u)
+        rel = _norm(r) / fnorm
+        hist.append(rel)
+        if rel <= tol or it == max_iters or not np.isfinite(rel):
+            return u, dict(iters=it, rel_residual=rel, history=hist, converged=rel <= tol)
+        u = u + M(G(r))
 
 
 def dense_matrix(op, shape) -> np.ndarray:

@@ -484,3 +484,70 @@ def test_coarse_basis_applies_g_proj_last():
     base = O.coarse_basis(w, 1, (3, 4), 0, shape)
     w["proj"] = w["proj"] * (2.5 - 1.0j)
     assert np.max(np.abs(O.coarse_basis(w, 1, (3, 4), 0, shape) - (2.5 - 1.0j) * base)) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Born+McMg: discrete Green operator and the Born-series iteration
+# ---------------------------------------------------------------------------
+
+def _periodic_background(q0, x):
+    """(-Delta_h - q0) x on the periodic grid, written with np.roll (no FFT)."""
+    out = 2 * x.ndim * x - q0 * x
+    for ax in range(x.ndim):
+        out = out - np.roll(x, 1, axis=ax) - np.roll(x, -1, axis=ax)
+    return out
+
+
+@pytest.mark.parametrize("shape", [(12, 10), (6, 8, 5)])
+def test_green_operator_inverts_the_periodic_background(shape):
+    g = np.random.Generator(np.random.PCG64(70))
+    c = 1.0 + 2.0 * g.random(shape)
+    q = O.wavenumber_coef(c, 9.0, 2, 1.0)
+    q0 = O.born_background(q)
+    assert q0.imag < 0 and np.max(np.abs(q - q0.real)) <= -q0.imag + 1e-15
+    x = I.complex_normal(shape, g)
+    y = O.apply_G(q0, _periodic_background(q0, x))
+    assert np.linalg.norm(y - x) <= 1e-12 * np.linalg.norm(x)
+
+
+def test_green_operator_on_a_plane_wave():
+    """A periodic plane wave is an eigenvector of the five-point Laplacian with
+    eigenvalue sum_a (2 - 2 cos(2 pi m_a / N_a)): G divides it by that minus q0."""
+    shape, m = (16, 12), (3, 5)
+    yy, xx = np.meshgrid(np.arange(shape[0]), np.arange(shape[1]), indexing="ij")
+    e = np.exp(2j * np.pi * (m[0] * yy / shape[0] + m[1] * xx / shape[1]))
+    lam = sum(2.0 - 2.0 * np.cos(2 * np.pi * mi / n) for mi, n in zip(m, shape))
+    q0 = 0.7 - 0.4j
+    assert np.max(np.abs(O.apply_G(q0, e) - e / (lam - q0))) < 1e-12
+
+
+def test_born_residual_identity_on_the_periodic_grid():
+    """G(V u + f) - u = G(f - A u) with V = q - q0 and A = -Delta_h - q (both
+    periodic here, where G is the exact background inverse)."""
+    g = np.random.Generator(np.random.PCG64(71))
+    shape = (10, 14)
+    q = O.wavenumber_coef(1.0 + g.random(shape), 12.0, 2, 1.0)
+    q0 = O.born_background(q)
+    u, f = I.complex_normal(shape, g), I.complex_normal(shape, g)
+    A_per = _periodic_background(0.0, u) - q * u
+    lhs = O.apply_G(q0, (q - q0) * u + f) - u
+    rhs = O.apply_G(q0, f - A_per)
+    assert np.linalg.norm(lhs - rhs) <= 1e-12 * np.linalg.norm(rhs)
+
+
+def test_born_solve_with_the_exact_preconditioner_takes_one_step():
+    """With MG = (G A)^{-1} one Born+McMg step gives A^{-1} f exactly."""
+    g = np.random.Generator(np.random.PCG64(72))
+    shape = (6, 5)
+    q = O.wavenumber_coef(1.0 + g.random(shape), 7.0, 1, 1.0)
+    q0 = O.born_background(q)
+    A = lambda v: O.apply_A(q, v)
+    G = lambda v: O.apply_G(q0, v)
+    GA = O.dense_matrix(lambda v: G(A(v)), shape)
+    GAinv = np.linalg.inv(GA)
+    M = lambda v: (GAinv @ v.reshape(-1)).reshape(shape)
+    f = I.complex_normal(shape, g)
+    u, info = O.born_solve(A, G, M, f, tol=1e-10, max_iters=5)
+    assert info["iters"] == 1
+    Ad = O.dense_matrix(A, shape)
+    assert np.linalg.norm(u.reshape(-1) - np.linalg.solve(Ad, f.reshape(-1))) < 1e-10 * np.linalg.norm(u)
