@@ -133,6 +133,17 @@ typedef struct {
                                     (Eq. mcmg_iteration); restart_m is
                                     ignored; mcmg_solve only (the server
                                     refuses it with MCMG_ERR_ARG)             */
+#define MCMG_SOLVE_BORN 2        /* Born+McMg: u <- u + MG(G(f - A u)) with G
+                                    = (-Delta_h - k0^2)^{-1} applied by FFT
+                                    with the discrete-Laplacian symbol
+                                    (Appendix, Born-series variant and
+                                    discrete Green operator; periodic modes).
+                                    q0 = (k0 h)^2: Re q0 halfway between the
+                                    extremes of Re q, Im q0 = -max|q - Re q0|.
+                                    restart_m ignored; mcmg_solve only.  The
+                                    first Born solve on a handle builds an FFT
+                                    plan (cuFFT allocates its workspace outside
+                                    the HBM budget).                          */
 
 typedef struct {
   int iters;                 /* V-cycle applications (max over the rhs)      */

@@ -583,6 +583,7 @@ mcmg_status mcmg_destroy(mcmg_handle h) {
   if (h->kry) krylov_destroy(h, h->kry);
   if (h->blk) block_destroy(h, h->blk);
   if (h->work) vwork_destroy(h, h->work);
+  born_release(h);
   arena_free(h, h->arena);
   if (h->stream) cudaStreamDestroy(h->stream);
   if (h->err_host) cudaFreeHost(h->err_host);
@@ -622,8 +623,9 @@ mcmg_status mcmg_solve(mcmg_handle h, const void* f, void* u, const mcmg_solve_o
   MCMG_TRY(check_opts(o));
   std::lock_guard<std::mutex> lk(h->mu);
   MCMG_CUDA(cudaSetDevice(h->device));
-  const int m_need = (o->flags & MCMG_SOLVE_STATIONARY) ? 1 : o->restart_m;
-  const bool batched = o->nrhs > 1 && !(o->flags & MCMG_SOLVE_STATIONARY);
+  const bool plain_iter = (o->flags & (MCMG_SOLVE_STATIONARY | MCMG_SOLVE_BORN)) != 0;
+  const int m_need = plain_iter ? 1 : o->restart_m;
+  const bool batched = o->nrhs > 1 && !plain_iter;
   if (!batched) {
     if (h->kry && krylov_m(h->kry) != m_need) {
       krylov_destroy(h, h->kry);
@@ -652,7 +654,10 @@ mcmg_status mcmg_solve(mcmg_handle h, const void* f, void* u, const mcmg_solve_o
       cudaStream_t st = o->stream ? (cudaStream_t)o->stream : h->stream;
       mcmg_solve_info one;
       mcmg_status fs;
-      if (o->flags & MCMG_SOLVE_STATIONARY) {
+      if (o->flags & MCMG_SOLVE_BORN) {
+        MCMG_TRY(born_run(h->kry, (const double2*)f + (size_t)k * N,
+                          (double2*)u + (size_t)k * N, *o, st, &one, &fs));
+      } else if (o->flags & MCMG_SOLVE_STATIONARY) {
         MCMG_TRY(stationary_run(h->kry, (const double2*)f + (size_t)k * N,
                                 (double2*)u + (size_t)k * N, *o, st, &one, &fs));
       } else {
@@ -983,8 +988,8 @@ mcmg_status mcmg_submit(mcmg_ctx c, mcmg_handle h, const void* f, void* u,
     return MCMG_ERR_ARG;
   }
   MCMG_TRY(check_opts(o));
-  if (o->flags & MCMG_SOLVE_STATIONARY) {
-    set_error("the stationary iteration is not available in this build");
+  if (o->flags & (MCMG_SOLVE_STATIONARY | MCMG_SOLVE_BORN)) {
+    set_error("the server runs FGMRES solves only (no stationary or Born iteration)");
     return MCMG_ERR_ARG;
   }
   Request* r = new Request();

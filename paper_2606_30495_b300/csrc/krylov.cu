@@ -722,6 +722,70 @@ mcmg_status stationary_run(Krylov* k, const double2* f, double2* u, const mcmg_s
 }
 
 
+// part[bx] = sum |x|^2 over the block's elements (FP64)
+__global__ void __launch_bounds__(RED_T) k_norm2_parts(const double2* __restrict__ x, long long n,
+                                                       double* __restrict__ part) {
+  double a = 0.0;
+  for (long long p = (long long)blockIdx.x * RED_T + threadIdx.x; p < n;
+       p += (long long)gridDim.x * RED_T) {
+    const double2 v = x[p];
+    a += v.x * v.x + v.y * v.y;
+  }
+  const double2 r = block_sum2(a, 0.0);
+  if (threadIdx.x == 0) part[blockIdx.x] = r.x;
+}
+
+// Born+McMg (Appendix, Born-series variant): r = f - A u in FP64, the
+// Born-series residual G r (FFT, born.cu), u <- u + MG(G r) with the V-cycle
+// run on G r / ||G r|| (it is linear).  Stops on ||f - A u|| / ||f|| like
+// the stationary iteration.  Synchronous.
+mcmg_status born_run(Krylov* k, const double2* f, double2* u, const mcmg_solve_opts& o,
+                     cudaStream_t st, mcmg_solve_info* info, mcmg_status* final_status) {
+  mcmg_handle_s* h = k->h;
+  const long long n = k->n;
+  MCMG_TRY(born_prepare(h));
+  const int max_iters = o.max_iters > 0 ? o.max_iters : 20 * (h->g0.d == 3 ? h->g0.nz : h->g0.ny);
+  const auto t0 = std::chrono::steady_clock::now();
+  double fnorm = -1.0, rel = 0.0;
+  int it = 0;
+  mcmg_status fs = MCMG_OK;
+  bool conv = false;
+  for (;; ++it) {
+    MCMG_TRY(launch_residual64(h->q64, f, u, k->r64, k->part, k->nblk, h->g0, 1, st));
+    k_reduce_res<<<1, RED_T, 0, st>>>(k->part, k->nblk, k->dsc, &k->stat_d->rr);
+    MCMG_CHECK_LAUNCH("reduce_res");
+    MCMG_CUDA(cudaStreamSynchronize(st));
+    Stat sv;
+    std::memcpy(&sv, (const void*)k->stat_h, sizeof(Stat));
+    if (fnorm < 0.0) fnorm = std::sqrt(sv.ff);
+    rel = fnorm > 0.0 ? std::sqrt(sv.rr) / fnorm : 0.0;
+    if (!std::isfinite(rel)) { fs = MCMG_ERR_NUMERIC; break; }
+    if (rel <= o.tol) { conv = true; break; }
+    if (it >= max_iters) { fs = MCMG_ERR_NOT_CONVERGED; break; }
+    if (h->err_host && *(volatile int*)h->err_host) { fs = MCMG_ERR_TIMEOUT; break; }
+    MCMG_TRY(born_apply_G(h, k->r64, st));                       // G (f - A u)
+    k_norm2_parts<<<k->nblk, RED_T, 0, st>>>(k->r64, n, k->part);
+    MCMG_CHECK_LAUNCH("norm2_parts");
+    k_reduce_scalar<<<1, RED_T, 0, st>>>(k->part, k->nblk, k->dsc, nullptr);   // dsc[0]
+    MCMG_CHECK_LAUNCH("reduce_scalar");
+    k_start_cycle<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(k->r64, k->dsc, k->V, n);
+    MCMG_CHECK_LAUNCH("start_cycle");
+    MCMG_TRY(vcycle_run(h, k->vw, k->V, k->Z, 1, st));
+    k_stationary_update<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(k->Z, k->dsc, u, n);
+    MCMG_CHECK_LAUNCH("stationary_update");
+  }
+  if (info) {
+    info->iters = it;
+    info->restarts = 0;
+    info->rel_residual = rel;
+    info->converged = conv ? 1 : 0;
+    info->t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  *final_status = fs;
+  return MCMG_OK;
+}
+
+
 // ---------------------------------------------------------------------------
 // Block of right-hand sides of one medium.
 // ---------------------------------------------------------------------------

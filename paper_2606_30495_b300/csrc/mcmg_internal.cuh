@@ -208,6 +208,9 @@ mcmg_status krylov_advance(Krylov* k, bool blocking, int* done);
 void krylov_info(const Krylov* k, mcmg_solve_info* info, mcmg_status* final_status);
 int krylov_m(const Krylov* k);
 // The stationary iteration u <- u + MG(f - A u), synchronous, on a Krylov workspace.
+// Born+McMg: u <- u + MG(G(f - A u)), synchronous, on a Krylov workspace.
+mcmg_status born_run(Krylov* k, const double2* f, double2* u, const mcmg_solve_opts& o,
+                     cudaStream_t st, mcmg_solve_info* info, mcmg_status* final_status);
 mcmg_status stationary_run(Krylov* k, const double2* f, double2* u, const mcmg_solve_opts& o,
                            cudaStream_t st, mcmg_solve_info* info, mcmg_status* final_status);
 cudaStream_t krylov_stream(const Krylov* k);   // the solve's private stream
@@ -254,4 +257,17 @@ struct mcmg_handle_s {
   int* err_host = nullptr;      // error word, mapped pinned (bounded waits that ran out)
   int* err_dev = nullptr;
   unsigned shape_gen = 0;       // bumped when a smoothing shape is overridden
+  // Born-series variant (born.cu): FFT plan, per-axis Laplacian symbols, q0
+  bool born_ready = false;
+  int born_plan = 0;
+  double* born_sym[3] = {};
+  double born_q0r = 0.0, born_q0i = 0.0;
 };
+
+namespace mcmg {
+// Green operator of the Born-series variant (born.cu): plan, symbols and q0
+// once per handle; x <- G x in place (x: c128 [nodes_0]) on st.
+mcmg_status born_prepare(mcmg_handle_s* h);
+mcmg_status born_apply_G(mcmg_handle_s* h, double2* x, cudaStream_t st);
+void born_release(mcmg_handle_s* h);
+}  // namespace mcmg

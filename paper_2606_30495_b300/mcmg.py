@@ -26,6 +26,7 @@ STATUS = {0: "OK", 1: "PENDING", -1: "ERR_ARG", -2: "ERR_SHAPE", -3: "ERR_OOM", 
           -5: "ERR_NOT_CONVERGED", -6: "ERR_TIMEOUT", -7: "ERR_NUMERIC", -8: "ERR_BUSY"}
 FP32, BF16 = 0, 1
 SOLVE_STATIONARY = 1
+SOLVE_BORN = 2
 
 
 class McmgError(RuntimeError):

@@ -487,3 +487,34 @@ def test_multi_rhs_block_solve_equals_single_solves(ctx):
         assert info["iters"] == max(iters)
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("name", ["helm2d_n64_homogeneous", "helm2d_n64_slmg"])
+def test_born_iteration_matches_oracle(ctx, name):
+    """Born+McMg (Appendix, Born-series variant): the true residual after
+    k = 1..5 Born steps u <- u + MG(G(f - A u)), G applied by FFT with the
+    discrete-Laplacian symbol, matches the oracle's iterates."""
+    from paper_2606_30495_b300 import mcmg
+    m = workload_model(name)
+    feats = O.setup(m["q"], m["w"])
+    f = I.point_source(m["shape"])
+    q0 = O.born_background(m["q"])
+    _, oinfo = O.born_solve(lambda u: O.apply_A(m["q"], u), lambda v: O.apply_G(q0, v),
+                            lambda v: O.vcycle(m["w"], feats, v), f, tol=1e-30, max_iters=5)
+    h = handle(ctx, m)
+    try:
+        for k in range(1, 6):
+            u = torch.zeros(m["shape"], dtype=torch.complex128, device="cuda")
+            st, info = h.solve(dev(f, torch.complex128), u, tol=1e-30, restart_m=1, max_iters=k,
+                               flags=mcmg.SOLVE_BORN)
+            assert st == -5 and info["iters"] == k
+            want = oinfo["history"][k]
+            assert abs(info["rel_residual"] - want) <= 1e-4 * want, (k, info, want)
+            res = np.linalg.norm(f - O.apply_A(m["q"], host(u))) / np.linalg.norm(f)
+            assert abs(res - want) <= 1e-4 * want
+        # the server runs FGMRES only
+        with pytest.raises(mcmg.McmgError):
+            ctx.submit(h, dev(f, torch.complex128), torch.zeros(m["shape"], dtype=torch.complex128,
+                       device="cuda"), tol=1e-6, restart_m=1, max_iters=2, flags=mcmg.SOLVE_BORN)
+    finally:
+        h.close()
