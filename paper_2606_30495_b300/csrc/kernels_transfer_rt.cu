@@ -192,9 +192,185 @@ static mcmg_status transfer_rt(const TransferParams& p, bool restrict_, int nrhs
   }
 }
 
+// Thread per coarse node (few channels).  G = CO / CT adjacent lanes share a
+// coarse node J, each owning CT output channels; the transfer weights sit in
+// shared memory ([tap][CI][CO], read as broadcasts: every node's lanes read
+// the same weights) and each lane reads a source node's CI values with
+// 16-byte loads.  No block barrier after the weights are staged.
+template <int CI, int CO, int D, int CT, bool RESTRICT>
+constexpr bool tpnx_valid() {
+  constexpr int G = CT > 0 && CO % CT == 0 ? CO / CT : 0;
+  return G >= 1 && 32 % G == 0 && CI <= 32 && CI % 2 == 0 && CT % 2 == 0 &&
+         (RESTRICT || (D == 3 ? 8 : 4) * CT <= 32);
+}
+
+// rc[J][co] = sum_o sum_ci R[o][co][ci] t[2J + o][ci]   (CI fine, CO coarse)
+template <int CI, int CO, int D, int CT>
+__global__ void __launch_bounds__(256) k_restrict_tpn(TransferParams p) {
+  pdl_launch_dependents();
+  constexpr int G = CO / CT, NPB = 256 / G, T3 = D == 3 ? 27 : 9, MSZ = CI * CO;
+  extern __shared__ float4 xw4[];
+  const float2* Wsm = reinterpret_cast<const float2*>(xw4);   // [T3][CI][CO]
+  for (int i = threadIdx.x; i < T3 * MSZ / 2; i += 256)
+    xw4[i] = __ldg(reinterpret_cast<const float4*>(p.Wt) + i);
+  __syncthreads();
+  pdl_wait();
+  const int c0 = (threadIdx.x % G) * CT;
+  const long long NC = p.dst_nodes;
+  const long long J = (long long)blockIdx.x * NPB + threadIdx.x / G;
+  if (J >= NC) return;
+  const float2* __restrict__ t = p.src + (size_t)blockIdx.y * p.src_nodes * CI;
+  float2* __restrict__ rc = p.dst + (size_t)blockIdx.y * NC * CO;
+  int jx, jy, jz;
+  node_xyz32((int)J, p.cx, p.cy, jx, jy, jz);
+  float2 acc[CT];
+#pragma unroll
+  for (int c = 0; c < CT; ++c) acc[c] = make_float2(0.f, 0.f);
+#pragma unroll 3
+  for (int o = 0; o < T3; ++o) {
+    const int x = 2 * jx + o % 3 - 1, y = 2 * jy + (o / 3) % 3 - 1;
+    const int z = D == 3 ? 2 * jz + o / 9 - 1 : 0;
+    if (x < 0 || x >= p.fx || y < 0 || y >= p.fy || z < 0 || z >= p.fz) continue;
+    const float4* src4 =
+        reinterpret_cast<const float4*>(t + (((long long)z * p.fy + y) * p.fx + x) * CI);
+    float2 xv[CI];
+#pragma unroll
+    for (int h = 0; h < CI / 2; ++h) {
+      const float4 v = __ldg(src4 + h);
+      xv[2 * h] = make_float2(v.x, v.y);
+      xv[2 * h + 1] = make_float2(v.z, v.w);
+    }
+    const float2* Mt = Wsm + o * MSZ;
+#pragma unroll
+    for (int ci = 0; ci < CI; ++ci) {
+      const float4* w4 = reinterpret_cast<const float4*>(Mt + ci * CO + c0);
+#pragma unroll
+      for (int h = 0; h < CT / 2; ++h) {
+        const float4 w = w4[h];
+        cfma(acc[2 * h], make_float2(w.x, w.y), xv[ci]);
+        cfma(acc[2 * h + 1], make_float2(w.z, w.w), xv[ci]);
+      }
+    }
+  }
+  float4* o4 = reinterpret_cast<float4*>(rc + J * CO + c0);
+#pragma unroll
+  for (int h = 0; h < CT / 2; ++h)
+    o4[h] = make_float4(acc[2 * h].x, acc[2 * h].y, acc[2 * h + 1].x, acc[2 * h + 1].y);
+}
+
+// e[2J + b] += sum over taps o with b(o) = b of P[o] e_c[J + c(o)] (coarse-node
+// form, as k_prolong_rt; CI coarse, CO fine channels): a lane accumulates its
+// CT channels of all 2^d fine nodes of J, reading each of the 2^d coarse
+// neighbours once.
+template <int CI, int CO, int D, int CT>
+__global__ void __launch_bounds__(256) k_prolong_tpn(TransferParams p) {
+  pdl_launch_dependents();
+  constexpr int G = CO / CT, NPB = 256 / G, T3 = D == 3 ? 27 : 9, NP = D == 3 ? 8 : 4;
+  constexpr int MSZ = CI * CO;
+  extern __shared__ float4 xw4[];
+  const float2* Wsm = reinterpret_cast<const float2*>(xw4);   // [T3][CI][CO]
+  for (int i = threadIdx.x; i < T3 * MSZ / 2; i += 256)
+    xw4[i] = __ldg(reinterpret_cast<const float4*>(p.Wt) + i);
+  __syncthreads();
+  pdl_wait();
+  const int c0 = (threadIdx.x % G) * CT;
+  const long long NC = p.src_nodes;
+  const long long J = (long long)blockIdx.x * NPB + threadIdx.x / G;
+  if (J >= NC) return;
+  const float2* __restrict__ ec = p.src + (size_t)blockIdx.y * NC * CI;
+  float2* __restrict__ e = p.dst + (size_t)blockIdx.y * p.dst_nodes * CO;
+  int jx, jy, jz;
+  node_xyz32((int)J, p.cx, p.cy, jx, jy, jz);
+  float2 acc[NP][CT];
+#pragma unroll
+  for (int b = 0; b < NP; ++b)
+#pragma unroll
+    for (int c = 0; c < CT; ++c) acc[b][c] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int cs = 0; cs < NP; ++cs) {          // coarse neighbour J + {0,1}^d
+    const int X = jx + (cs & 1), Y = jy + ((cs >> 1) & 1), Z = jz + ((cs >> 2) & 1);
+    if (X >= p.cx || Y >= p.cy || (D == 3 && Z >= p.cz)) continue;
+    const float4* src4 = reinterpret_cast<const float4*>(
+        ec + (((long long)(D == 3 ? Z : 0) * p.cy + Y) * p.cx + X) * CI);
+    float2 xv[CI];
+#pragma unroll
+    for (int h = 0; h < CI / 2; ++h) {
+      const float4 v = __ldg(src4 + h);
+      xv[2 * h] = make_float2(v.x, v.y);
+      xv[2 * h + 1] = make_float2(v.z, v.w);
+    }
+#pragma unroll
+    for (int o = 0; o < T3; ++o) {
+      const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = D == 3 ? o / 9 - 1 : 0;
+      const int c = (ox == -1) | ((oy == -1) << 1) | ((oz == -1) << 2);
+      if (c != cs) continue;                  // taps reading this neighbour
+      const int b = (ox != 0) | ((oy != 0) << 1) | ((oz != 0) << 2);
+      const float2* Mt = Wsm + o * MSZ;
+#pragma unroll
+      for (int ci = 0; ci < CI; ++ci) {
+        const float4* w4 = reinterpret_cast<const float4*>(Mt + ci * CO + c0);
+#pragma unroll
+        for (int h = 0; h < CT / 2; ++h) {
+          const float4 w = w4[h];
+          cfma(acc[b][2 * h], make_float2(w.x, w.y), xv[ci]);
+          cfma(acc[b][2 * h + 1], make_float2(w.z, w.w), xv[ci]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NP; ++b) {
+    const long long fx = 2 * jx + (b & 1), fy = 2 * jy + ((b >> 1) & 1),
+                    fz = D == 3 ? 2 * jz + ((b >> 2) & 1) : 0;
+    float4* o4 = reinterpret_cast<float4*>(e + ((fz * p.fy + fy) * p.fx + fx) * CO + c0);
+#pragma unroll
+    for (int h = 0; h < CT / 2; ++h) {
+      const float4 v = o4[h];
+      o4[h] = make_float4(v.x + acc[b][2 * h].x, v.y + acc[b][2 * h].y,
+                          v.z + acc[b][2 * h + 1].x, v.w + acc[b][2 * h + 1].y);
+    }
+  }
+}
+
+template <int CI, int CO, int D, int CT>
+static mcmg_status transfer_tpn(const TransferParams& p, bool restrict_, int nrhs,
+                                cudaStream_t st) {
+  constexpr bool okr = tpnx_valid<CI, CO, D, CT, true>();
+  constexpr bool okp = tpnx_valid<CI, CO, D, CT, false>();
+  constexpr size_t smem = (size_t)(D == 3 ? 27 : 9) * CI * CO * sizeof(float2);
+  if (smem > kMaxSmem || (restrict_ ? !okr : !okp)) {
+    set_error("thread-per-node transfer shape does not fit %d -> %d channels", CI, CO);
+    return MCMG_ERR_SHAPE;
+  }
+  constexpr int NPB = CT > 0 && CO % CT == 0 ? 256 / (CO / CT) : 1;
+  const long long units = restrict_ ? p.dst_nodes : p.src_nodes;
+  dim3 grid((unsigned)((units + NPB - 1) / NPB), (unsigned)nrhs);
+  if constexpr (okr && smem <= kMaxSmem) {
+    if (restrict_) {
+      auto k = k_restrict_tpn<CI, CO, D, CT>;
+      if (smem > 48 * 1024) MCMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MCMG_LAUNCH_PDL(k, grid, dim3(256), smem, st, p);
+    }
+  }
+  if constexpr (okp && smem <= kMaxSmem) {
+    if (!restrict_) {
+      auto k = k_prolong_tpn<CI, CO, D, CT>;
+      if (smem > 48 * 1024) MCMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MCMG_LAUNCH_PDL(k, grid, dim3(256), smem, st, p);
+    }
+  }
+  MCMG_CHECK_LAUNCH(restrict_ ? "restrict_tpn" : "prolong_tpn");
+  return MCMG_OK;
+}
+
 template <int CI, int CO, int D>
 static mcmg_status transfer_rt_shape(const TransferParams& p, bool r, int tn, int cv, int kq,
                                      int nrhs, cudaStream_t st) {
+  if (kq < 0) {   // thread per coarse node, cv output channels per lane
+    if (cv == 2) return transfer_tpn<CI, CO, D, 2>(p, r, nrhs, st);
+    if (cv == 4) return transfer_tpn<CI, CO, D, 4>(p, r, nrhs, st);
+    if (cv == 8) return transfer_tpn<CI, CO, D, 8>(p, r, nrhs, st);
+  }
   if (cv == 4) {
     if (tn == 1 && kq == 4) return transfer_rt<CI, CO, D, 1, 4, 4>(p, r, nrhs, st);
     if (tn == 2 && kq == 4) return transfer_rt<CI, CO, D, 2, 4, 4>(p, r, nrhs, st);

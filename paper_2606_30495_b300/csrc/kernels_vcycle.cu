@@ -778,7 +778,9 @@ __global__ void __launch_bounds__(256) k_prolong_add(TransferParams p) {
 struct TShape {
   int tn, cv, kq;
 };
-static constexpr TShape kTShapes[] = {{0, 0, 0}, {1, 4, 4}, {2, 4, 4}, {1, 4, 8}, {2, 4, 8}, {1, 4, 2}};
+// kq < 0: thread per coarse node (k_restrict_tpn / k_prolong_tpn), cv channels per lane
+static constexpr TShape kTShapes[] = {{0, 0, 0}, {1, 4, 4}, {2, 4, 4}, {1, 4, 8}, {2, 4, 8},
+                                     {1, 4, 2}, {1, 2, -1}, {1, 4, -1}, {1, 8, -1}};
 static constexpr int kNumTShapes = sizeof(kTShapes) / sizeof(kTShapes[0]);
 
 // Register-tiled transfers are built for channel pairs (fine, coarse) with
@@ -790,6 +792,12 @@ static bool xt_pair(int Cf, int Cc) {
 
 // Shared memory of a register-tiled transfer (0: shape cannot run).
 static size_t xt_smem(bool restrict_, int CI, int CO, int D, int tn, int cv, int kq) {
+  if (kq < 0) {   // thread per coarse node: the weights only
+    const int G = cv > 0 && CO % cv == 0 ? CO / cv : 0;
+    const int NP = D == 3 ? 8 : 4;
+    if (G < 1 || 32 % G || CI > 32 || CI % 2 || cv % 2 || (!restrict_ && NP * cv > 32)) return 0;
+    return (size_t)(D == 3 ? 27 : 9) * CI * CO * sizeof(float2);
+  }
   if (cv > CO || CO % cv || kq > CI || CI % kq || CI % 2) return 0;
   const int cg = CO / cv, ks = CI / kq;
   if (cg * ks > 256 || 256 % (cg * ks)) return 0;
@@ -902,6 +910,10 @@ mcmg_status autotune_transfer(Level& L, float2* fine, float2* coarse, cudaStream
     for (int pass = 0; pass < kTunePasses && status == MCMG_OK; ++pass) {
       for (int s = 0; s < kNumTShapes; ++s) {
         if (!xshape_ok(s, L, r)) continue;
+        // thread-per-node transfers time well alone but slowed the whole
+        // V-cycle on grids with small coarse levels (measured on 256^2;
+        // faster on 1024^2): candidates only from 2^16 coarse nodes on
+        if (kTShapes[s].kq < 0 && L.g.coarse().nodes() < (1 << 16)) continue;
         for (int rep = 0; rep < 2; ++rep)
           if ((status = transfer_run(L, p, r, s, 1, st)) != MCMG_OK) break;
         if (status != MCMG_OK) break;
