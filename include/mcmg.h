@@ -63,8 +63,12 @@ typedef enum {
 
 typedef enum {
   MCMG_FP32 = 0,   /* channel mixing and stencils in FP32 (FFMA)               */
-  MCMG_BF16 = 1    /* channel mixing on tcgen05 tensor cores, BF16 operands,
+  MCMG_BF16 = 1,   /* channel mixing on tcgen05 tensor cores, BF16 operands,
                       FP32 accumulation; stencil arithmetic stays FP32        */
+  MCMG_FP32_TC = 2 /* FP32-accurate channel mixing on tcgen05 tensor cores:
+                      every FP32 operand split into two TF32 parts and three
+                      TF32 products accumulated in FP32 (levels with C_l in
+                      {8, 16}; other levels as MCMG_FP32)                     */
 } mcmg_precision;
 
 /* The medium: wave speed on the grid plus the sponge layer (Section 2.1).
@@ -244,6 +248,12 @@ mcmg_status mcmg_project(mcmg_handle h, const void* e1_dev, void* e_dev, int nrh
 mcmg_status mcmg_smooth(mcmg_handle h, int level, int step, const void* r_dev,
                         const void* e_in_dev, void* e_out_dev, int nrhs, void* stream);
 
+/* The residual of Algorithm 2 on `level`:  t = r - A_l(e)  (the input of the
+ * restriction).  r, e, t: dev c64 [nrhs][nodes_l][C_l]; t may not overlap e.
+ * Enqueued on `stream`.                                                      */
+mcmg_status mcmg_residual(mcmg_handle h, int level, const void* r_dev, const void* e_dev,
+                          void* t_dev, int nrhs, void* stream);
+
 /* r_coarse = R_l(r - A_l(e)) for level < levels-1.  r, e: dev c64
  * [nrhs][nodes_l][C_l]; r_coarse: dev c64 [nrhs][nodes_{l+1}][C_{l+1}].       */
 mcmg_status mcmg_residual_restrict(mcmg_handle h, int level, const void* r_dev,
@@ -280,12 +290,13 @@ mcmg_status mcmg_cgs2(mcmg_handle h, const void* V_dev, int k, size_t n, void* w
  * its scratch (about 0.6 MB) is a static device array that every GPU which
  * loads this library holds until the process exits.  Same arguments and
  * results as mcmg_cgs2, with k at most 64 (larger k returns MCMG_ERR_ARG), no
- * handle, and the caller's stream (NULL = legacy default stream); the call
- * returns when the results are on the host.  The first call on a device looks
- * up the array's device address with that device current; make that first
- * call before any stream capture.  All calls share the one array, so calls
- * that overlap on the GPU race; nothing carries over from one call to the
- * next.                                                                      */
+ * handle, and the caller's stream (NULL = legacy default stream).  V and w
+ * must be device memory of the current device (else MCMG_ERR_ARG).  The call
+ * is synchronous: it copies the results to the host and synchronises the
+ * stream before returning, so it must not be issued on a stream that is being
+ * captured.  The first call on a device looks up the array's device address
+ * with that device current.  All calls share the one array, so calls that
+ * overlap on the GPU race; nothing carries over from one call to the next.   */
 mcmg_status mcmg_cgs2_noalloc(const void* V_dev, int k, size_t n, void* w_dev,
                               double* h_host, double* norm_host, void* stream);
 

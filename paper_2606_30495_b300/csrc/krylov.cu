@@ -370,9 +370,11 @@ struct Krylov {
 // Blocks of the grid-stride reductions: about one element per thread, at
 // most four blocks per SM (the update and multi-dot loops over the basis are
 // serial per element, so parallelism over elements hides their latency).
+constexpr int RED_MAX_BLK = 148 * 4;
+
 static int red_blocks(long long n) {
   long long b = (n + RED_T - 1) / RED_T;
-  long long cap = 148 * 4;
+  long long cap = RED_MAX_BLK;
   return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
@@ -1024,7 +1026,7 @@ mcmg_status cgs2_once(mcmg_handle_s* h, const float2* V, int kv, long long n, fl
 // it reads before reading it, so nothing depends on an earlier call's contents.
 // ---------------------------------------------------------------------------
 constexpr int NOALLOC_MAX_K = 64;                       // basis vectors per call
-constexpr int NOALLOC_MAX_BLK = 148 * 4;                // >= the red_blocks() cap
+constexpr int NOALLOC_MAX_BLK = RED_MAX_BLK;            // the red_blocks() cap
 constexpr size_t NOALLOC_PART = 2ull * NOALLOC_MAX_BLK * NOALLOC_MAX_K;
 constexpr size_t NOALLOC_DOUBLES = NOALLOC_PART + 4ull * NOALLOC_MAX_K + 8;
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
@@ -1073,11 +1075,29 @@ mcmg_status mcmg_cgs2_noalloc(const void* V_dev, int k, size_t n, void* w_dev, d
     set_error("mcmg_cgs2_noalloc takes 1..%d basis vectors, got %d", NOALLOC_MAX_K, k);
     return MCMG_ERR_ARG;
   }
+  int dev = 0;
+  MCMG_CUDA(cudaGetDevice(&dev));
+  for (const void* p : {V_dev, (const void*)w_dev}) {
+    // both vectors must live on the current device: the scratch and the
+    // kernels belong to it, and a peer pointer would be read across the link
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes");
+    if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev) {
+      set_error("mcmg_cgs2_noalloc: V and w must be device memory of the current device %d", dev);
+      return MCMG_ERR_ARG;
+    }
+  }
   double* base = nullptr;
   MCMG_TRY(noalloc_scratch(&base));
   cudaStream_t st = (cudaStream_t)stream;
   const long long nn = (long long)n;
   const int nblk = red_blocks(nn);
+  if (nblk > NOALLOC_MAX_BLK) {     // the partial sums would not fit the scratch
+    set_error("mcmg_cgs2_noalloc: %d reduction blocks exceed the scratch's %d", nblk,
+              NOALLOC_MAX_BLK);
+    return MCMG_ERR_ARG;
+  }
   double* part = base;
   double2* d1 = (double2*)(base + NOALLOC_PART);
   double2* d2 = d1 + NOALLOC_MAX_K;

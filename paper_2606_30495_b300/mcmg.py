@@ -24,7 +24,7 @@ MCMG_OK, MCMG_PENDING = 0, 1
 MCMG_ERR_SHAPE = -2
 STATUS = {0: "OK", 1: "PENDING", -1: "ERR_ARG", -2: "ERR_SHAPE", -3: "ERR_OOM", -4: "ERR_CUDA",
           -5: "ERR_NOT_CONVERGED", -6: "ERR_TIMEOUT", -7: "ERR_NUMERIC", -8: "ERR_BUSY"}
-FP32, BF16 = 0, 1
+FP32, BF16, FP32_TC = 0, 1, 2   # mcmg_precision
 SOLVE_STATIONARY = 1
 SOLVE_BORN = 2
 
@@ -80,6 +80,7 @@ _SIGS = {
     "mcmg_lift": [_P, _P, _P, C.c_int, _P],
     "mcmg_project": [_P, _P, _P, C.c_int, _P],
     "mcmg_smooth": [_P, C.c_int, C.c_int, _P, _P, _P, C.c_int, _P],
+    "mcmg_residual": [_P, C.c_int, _P, _P, _P, C.c_int, _P],
     "mcmg_residual_restrict": [_P, C.c_int, _P, _P, _P, C.c_int, _P],
     "mcmg_prolong_add": [_P, C.c_int, _P, _P, C.c_int, _P],
     "mcmg_coarse_basis": [_P, C.c_int, C.c_longlong, C.c_int, _P, _P],
@@ -205,12 +206,23 @@ def pack_weights(w: dict):
 def cgs2_noalloc(V, w, stream=None):
     """mcmg_cgs2_noalloc: CGS2 of w against the rows of V with no device
     allocation (scratch in a static device array).  Returns (h, ||w||)."""
+    import torch
     lib = load()
+    if V.dim() != 2 or not V.is_cuda or not w.is_cuda or V.device != w.device:
+        raise ValueError("V ([k][n]) and w ([n]) must be CUDA tensors on one device")
+    if V.dtype != torch.complex64 or w.dtype != torch.complex64:
+        raise ValueError("V and w must be complex64")
+    if not V.is_contiguous() or not w.is_contiguous():
+        raise ValueError("V and w must be contiguous")
     k, n = V.shape[0], V.shape[1]
+    if w.numel() != n:
+        raise ValueError(f"w has {w.numel()} elements, V's rows have {n}")
     hbuf = np.zeros(2 * k)
     nrm = C.c_double()
-    _check(lib.mcmg_cgs2_noalloc(ptr(V), k, n, ptr(w), hbuf.ctypes.data_as(C.POINTER(C.c_double)),
-                                 C.byref(nrm), _stream(stream)))
+    with torch.cuda.device(V.device):
+        _check(lib.mcmg_cgs2_noalloc(ptr(V), k, n, ptr(w),
+                                     hbuf.ctypes.data_as(C.POINTER(C.c_double)), C.byref(nrm),
+                                     _stream(stream)))
     return hbuf.view(np.complex128), nrm.value
 
 
@@ -328,6 +340,11 @@ class Handle:
     def smooth(self, level, step, r, e_in, e_out, nrhs=1, stream=None):
         _check(self.lib.mcmg_smooth(self.h, level, step, ptr(r), None if e_in is None else ptr(e_in),
                                     ptr(e_out), nrhs, _stream(stream)))
+
+    def residual(self, level, r, e, t, nrhs=1, stream=None):
+        """t = r - A_l(e) on `level` (enqueued on `stream`)."""
+        _check(self.lib.mcmg_residual(self.h, level, ptr(r), ptr(e), ptr(t), nrhs,
+                                      _stream(stream)))
 
     def residual_restrict(self, level, r, e, rc, nrhs=1, stream=None):
         _check(self.lib.mcmg_residual_restrict(self.h, level, ptr(r), ptr(e), ptr(rc), nrhs,

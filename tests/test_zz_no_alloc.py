@@ -42,3 +42,38 @@ def test_noalloc_cgs2_matches_allocating_cgs2_twice():
     finally:
         h.close()
         ctx.close()
+
+
+def test_noalloc_cgs2_allocates_nothing_and_runs_on_a_side_stream():
+    """A warm call leaves torch's reserved memory, the library's accounted
+    memory and the device's free memory unchanged, and a call on a
+    non-default stream gives the default stream's results."""
+    from paper_2606_30495_b300 import mcmg
+    ctx = mcmg.Context(0)
+    m = model((34, 30), [8, 16], mode="random", seed=4)
+    h = mcmg.Handle(ctx, m["c"], m["omega"], m["sponge"], m["gamma_max"], m["w"])
+    try:
+        n, k = 34 * 30, 20
+        Q, _ = np.linalg.qr(I.complex_normal((n, k), rng(80)))
+        V = torch.from_numpy(np.ascontiguousarray(Q.T)).to("cuda", torch.complex64)
+        w0 = torch.from_numpy(I.complex_normal(n, rng(81))).to("cuda", torch.complex64)
+        w_def, w_side = w0.clone(), w0.clone()
+        mcmg.cgs2_noalloc(V, w0.clone())                  # warm: modules loaded, address cached
+        torch.cuda.synchronize()
+        reserved, ctx_mem = torch.cuda.memory_reserved(), ctx.memory()
+        free0, _ = torch.cuda.mem_get_info()
+        h_def, n_def = mcmg.cgs2_noalloc(V, w_def)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        h_side, n_side = mcmg.cgs2_noalloc(V, w_side, stream=side)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert torch.cuda.memory_reserved() == reserved
+        assert ctx.memory() == ctx_mem
+        assert free1 == free0
+        assert relerr(h_side, h_def) < 1e-6
+        assert abs(n_side - n_def) < 1e-5 * n_def
+        assert relerr(w_side.cpu().numpy(), w_def.cpu().numpy()) < 1e-5
+    finally:
+        h.close()
+        ctx.close()
