@@ -439,8 +439,9 @@ def test_errors_are_reported(ctx):
 
 @pytest.mark.parametrize("name", ["helm2d_n64_homogeneous", "helm2d_n64_slmg"])
 def test_stationary_iteration_matches_oracle(ctx, name):
-    """The stationary McMg iteration (Eq. mcmg_iteration): the true residual
-    after k = 1..6 V-cycles matches the oracle's iterates."""
+    """The stationary McMg iteration (Eq. mcmg_iteration): the iterate u and
+    its true residual after k = 1..6 V-cycles match the oracle's, u element
+    by element."""
     m = workload_model(name)
     feats = O.setup(m["q"], m["w"])
     f = I.point_source(m["shape"])
@@ -458,6 +459,10 @@ def test_stationary_iteration_matches_oracle(ctx, name):
             assert abs(info["rel_residual"] - want) <= 1e-4 * want, (k, info, want)
             res = np.linalg.norm(f - O.apply_A(m["q"], host(u))) / np.linalg.norm(f)
             assert abs(res - want) <= 1e-4 * want
+            uk, _ = O.stationary_solve(lambda v: O.apply_A(m["q"], v),
+                                       lambda v: O.vcycle(m["w"], feats, v), f, tol=1e-30,
+                                       max_iters=k)
+            assert relerr(host(u), uk) < 1e-4, k
     finally:
         h.close()
 
@@ -491,9 +496,10 @@ def test_multi_rhs_block_solve_equals_single_solves(ctx):
 
 @pytest.mark.parametrize("name", ["helm2d_n64_homogeneous", "helm2d_n64_slmg"])
 def test_born_iteration_matches_oracle(ctx, name):
-    """Born+McMg (Appendix, Born-series variant): the true residual after
-    k = 1..5 Born steps u <- u + MG(G(f - A u)), G applied by FFT with the
-    discrete-Laplacian symbol, matches the oracle's iterates."""
+    """Born+McMg (Appendix, Born-series variant): the iterate u and its true
+    residual after k = 1..5 Born steps u <- u + MG(G(f - A u)), G applied by
+    FFT with the discrete-Laplacian symbol, match the oracle's, u element by
+    element."""
     from paper_2606_30495_b300 import mcmg
     m = workload_model(name)
     feats = O.setup(m["q"], m["w"])
@@ -512,6 +518,9 @@ def test_born_iteration_matches_oracle(ctx, name):
             assert abs(info["rel_residual"] - want) <= 1e-4 * want, (k, info, want)
             res = np.linalg.norm(f - O.apply_A(m["q"], host(u))) / np.linalg.norm(f)
             assert abs(res - want) <= 1e-4 * want
+            uk, _ = O.born_solve(lambda v: O.apply_A(m["q"], v), lambda v: O.apply_G(q0, v),
+                                 lambda v: O.vcycle(m["w"], feats, v), f, tol=1e-30, max_iters=k)
+            assert relerr(host(u), uk) < 1e-4, k
         # the server runs FGMRES only
         with pytest.raises(mcmg.McmgError):
             ctx.submit(h, dev(f, torch.complex128), torch.zeros(m["shape"], dtype=torch.complex128,

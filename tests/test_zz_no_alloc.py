@@ -58,12 +58,13 @@ def test_noalloc_cgs2_allocates_nothing_and_runs_on_a_side_stream():
         V = torch.from_numpy(np.ascontiguousarray(Q.T)).to("cuda", torch.complex64)
         w0 = torch.from_numpy(I.complex_normal(n, rng(81))).to("cuda", torch.complex64)
         w_def, w_side = w0.clone(), w0.clone()
+        side = torch.cuda.Stream()          # created (and used once) before measuring
         mcmg.cgs2_noalloc(V, w0.clone())                  # warm: modules loaded, address cached
+        mcmg.cgs2_noalloc(V, w0.clone(), stream=side)
         torch.cuda.synchronize()
         reserved, ctx_mem = torch.cuda.memory_reserved(), ctx.memory()
         free0, _ = torch.cuda.mem_get_info()
         h_def, n_def = mcmg.cgs2_noalloc(V, w_def)
-        side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         h_side, n_side = mcmg.cgs2_noalloc(V, w_side, stream=side)
         torch.cuda.synchronize()
