@@ -22,6 +22,10 @@ Section 4.1 where the paper fixes them):
 * ``helm3d_n256_grf``         -- 256^3 Gaussian random field c in [1, 3] plus
   three spheres of 5x contrast, 8 ppw, 10-cell sponge, 5 levels with
   8/16/32/64/64 channels, BF16 channel mixing, FGMRES(30).
+* ``helm2d_n256_layers``      -- the 1024^2 recipe (layers + discs, 6 ppw,
+  6 levels) on a 256^2 grid, small enough for the FP64 oracle's solve.
+* ``helm3d_n64_grf``          -- the 256^3 recipe (random field + spheres,
+  8 ppw, 10-cell sponge, 5 levels) on a 64^3 grid.
 * ``serving_stream``          -- 256 requests, grids from {128, 256, 512,
   1024}^2, one random-field medium per request, 1-8 point sources each.
 
@@ -89,6 +93,12 @@ WORKLOADS = {
                                6, [8, 16, 32, 64, 64, 64], "bf16", 30, seed=2),
     "helm3d_n256_grf": _wl("helm3d_n256_grf", 3, 256, "grf_spheres", 8, 10,
                            5, [8, 16, 32, 64, 64], "bf16", 30, seed=4),
+    # the two large recipes at the largest sizes the FP64 oracle solves in
+    # minutes: the same medium kind, ppw, sponge, levels, channels and Krylov
+    "helm2d_n256_layers": _wl("helm2d_n256_layers", 2, 256, "layers", 6, 16,
+                              6, [8, 16, 32, 64, 64, 64], "bf16", 30, seed=2),
+    "helm3d_n64_grf": _wl("helm3d_n64_grf", 3, 64, "grf_spheres", 8, 10,
+                          5, [8, 16, 32, 64, 64], "bf16", 30, seed=4),
 }
 
 

@@ -17,7 +17,9 @@ from oracle import mcmg_oracle as O  # noqa: E402
 from paper_2606_30495_b300 import inputs as I  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_solves.json")
-DEFAULT = ["helm2d_n64_homogeneous", "helm2d_n64_slmg", "helm2d_n256_grf"]
+DEFAULT = ["helm2d_n64_homogeneous", "helm2d_n64_slmg", "helm2d_n256_grf", "helm3d_n64_grf",
+           "helm2d_n256_layers"]
+MAX_ITERS = {"helm2d_n256_layers": 20000}
 
 
 def solve(name):
@@ -30,7 +32,7 @@ def solve(name):
     f = I.point_source(c.shape)
     t0 = time.time()
     _, info = O.fgmres(lambda u: O.apply_A(q, u), lambda v: O.vcycle(w, feats, v), f,
-                       m=wl["restart"], tol=wl["tol"], max_iters=4000)
+                       m=wl["restart"], tol=wl["tol"], max_iters=MAX_ITERS.get(name, 4000))
     return dict(iters=info["iters"], restarts=info["restarts"],
                 rel_residual=info["rel_residual"], converged=info["converged"],
                 restart=wl["restart"], tol=wl["tol"], oracle_seconds=round(time.time() - t0, 1))
@@ -38,9 +40,11 @@ def solve(name):
 
 if __name__ == "__main__":
     names = sys.argv[1:] or DEFAULT
-    data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for n in names:
-        data[n] = solve(n)
-        print(n, data[n], flush=True)
+        res = solve(n)
+        print(n, res, flush=True)
+        # re-read before writing, so runs of different workloads can overlap
+        data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+        data[n] = res
         with open(OUT, "w") as f:
             json.dump(data, f, indent=1, sort_keys=True)
