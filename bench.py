@@ -37,7 +37,8 @@ sys.path.insert(0, ROOT)
 METRIC = "solves/s and V-cycles/s to rel. residual 1e-6; p50/p99 solve latency"
 # Iteration cap per workload (the restart length is the workload's FGMRES(m)).
 MAX_ITERS = {"helm2d_n64_homogeneous": 2000, "helm2d_n64_slmg": 2000, "helm2d_n256_grf": 4000,
-             "helm2d_n1024_layers": 20000, "helm3d_n256_grf": 8000}
+             "helm2d_n1024_layers": 20000, "helm3d_n256_grf": 8000, "helm2d_n256_layers": 20000,
+             "helm3d_n64_grf": 4000}
 FP32_LANES_PER_SM = 128
 NUM_SMS = 148
 
@@ -49,6 +50,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="mcmg", choices=["mcmg", "reference"])
     p.add_argument("--workload", default="helm2d_n256_grf")
+    p.add_argument("--precision", default="", choices=["", "fp32", "bf16", "fp32tc"],
+                   help="override the workload's channel-mixing precision")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-iters", type=int, default=12)
     p.add_argument("--n", type=int, default=0,
@@ -164,11 +167,34 @@ def smooth_flops(C, d, first):
     return 8 * (2 if first else (2 * d + 4)) * C * C
 
 
+def residual_bytes(C):
+    """Residual t = r - A_l(e): read e, r, a, write t (32 C bytes per node)."""
+    return 32 * C
+
+
+def residual_flops(C, d):
+    """Residual: complex MACs of the stencil and K_A (8 (2d + 2) C^2)."""
+    return 8 * (2 * d + 2) * C * C
+
+
+def kernel_family(prec_name, C):
+    """Which kernel runs a level's smoothing step and residual: 'ts' (tensor
+    cores, A operands in tensor memory: BF16 for C in {8, 16, 32}, FP32-accurate
+    for C in {8, 16}), 'tc' (BF16 step with shared-memory operands, C = 64;
+    its residual on the CUDA cores) or 'cuda' (FP32 on the CUDA cores)."""
+    if prec_name == "bf16":
+        return "ts" if C in (8, 16, 32) else ("tc" if C == 64 else "cuda")
+    if prec_name == "fp32tc":
+        return "ts" if C in (8, 16) else "cuda"
+    return "cuda"
+
+
 def time_smoothing(h, wl, torch, stream, reps=20):
-    """CUDA-event time of every smoothing launch class of one V-cycle, through
-    the C ABI on `stream`.  Returns (total flops, total seconds, launches, detail)."""
+    """CUDA-event time of every smoothing and residual launch class of one
+    V-cycle, through the C ABI on `stream`.  Returns per-family totals
+    {family: dict(flops, bytes, s, launches)} and the per-class detail."""
     d = wl["dim"]
-    total_f, total_b, total_t, launches = 0.0, 0.0, 0.0, 0
+    fams = {}
     detail = []
     for l in range(wl["levels"]):
         C = wl["channels"][l]
@@ -179,30 +205,39 @@ def time_smoothing(h, wl, torch, stream, reps=20):
         o = torch.empty_like(e)
         n_full = wl["nu_pre"][l] + wl["nu_post"][l] - (1 if wl["nu_pre"][l] > 0 else 0)
         n_first = 1 if wl["nu_pre"][l] > 0 else 0
-        for first, count in ((True, n_first), (False, n_full)):
+        n_res = 1 if l < wl["levels"] - 1 else 0
+        fam = kernel_family(wl["precision"], C)
+        for kind, count in (("first", n_first), ("step", n_full), ("residual", n_res)):
             if count == 0:
                 continue
+            if kind == "residual":
+                run = lambda: h.residual(l, r, e, o, stream=stream)
+                fl, by = residual_flops(C, d) * nodes, residual_bytes(C) * nodes
+                kf = "cuda" if fam == "tc" else fam
+            else:
+                first = kind == "first"
+                run = lambda: h.smooth(l, 0, r, None if first else e, o, stream=stream)
+                fl, by = smooth_flops(C, d, first) * nodes, smooth_bytes(C, first) * nodes
+                kf = fam
             with torch.cuda.stream(stream):
                 for _ in range(3):
-                    h.smooth(l, 0, r, None if first else e, o, stream=stream)
+                    run()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 for _ in range(reps):
-                    h.smooth(l, 0, r, None if first else e, o, stream=stream)
+                    run()
                 e1.record(stream)
             e1.synchronize()
             per = e0.elapsed_time(e1) / 1e3 / reps
-            fl = smooth_flops(C, d, first) * nodes
-            by = smooth_bytes(C, first) * nodes
-            total_f += fl * count
-            total_b += by * count
-            total_t += per * count
-            launches += count
-            detail.append(dict(level=l, C=C, first=first, count=count, us=per * 1e6,
-                               tflops=fl / per / 1e12, gbs=by / per / 1e9,
-                               shape=h.kernel_shape(l, 0)))
-    return total_f, total_b, total_t, launches, detail
+            f = fams.setdefault(kf, dict(flops=0.0, bytes=0.0, s=0.0, launches=0))
+            f["flops"] += fl * count
+            f["bytes"] += by * count
+            f["s"] += per * count
+            f["launches"] += count
+            detail.append(dict(level=l, C=C, kind=kind, family=kf, count=count, us=per * 1e6,
+                               tflops=fl / per / 1e12, gbs=by / per / 1e9))
+    return fams, detail
 
 
 def oracle_rate(wl, c, omega, w, iters_full, sample_iters):
@@ -409,8 +444,10 @@ def main():
     from paper_2606_30495_b300 import mcmg
 
     wl, c, omega, w = setup_workload(args.workload, args.n)
+    if args.precision:
+        wl["precision"] = args.precision
     sp = dict(restart=wl["restart"], max_iters=args.max_iters or MAX_ITERS[args.workload])
-    prec = mcmg.BF16 if wl["precision"] == "bf16" else mcmg.FP32
+    prec = {"fp32": mcmg.FP32, "bf16": mcmg.BF16, "fp32tc": mcmg.FP32_TC}[wl["precision"]]
     ctx = mcmg.Context(local)
     t0 = time.perf_counter()
     h = mcmg.Handle(ctx, c, omega, wl["sponge"], wl["gamma_max"], w, precision=prec)
@@ -489,23 +526,29 @@ def main():
     v1.synchronize()
     vc_s = v0.elapsed_time(v1) / 1e3 / nv
 
-    # dominant kernel: the fused smoothing step (all launch classes of one V-cycle)
-    fl, by, tsec, nl, detail = time_smoothing(h, wl, torch, stream)
+    # dominant kernel family of the smoothing steps and residuals of one V-cycle
+    fams, detail = time_smoothing(h, wl, torch, stream)
     pk, pk_src = peaks()
     sm_mhz = pk.get("sm_max_mhz", 2032.0)
-    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    if prec == mcmg.FP32:
-        # FP32 channel mixing on the CUDA cores: FFMA-bound (1.6 C flop/B)
-        roof = {"bound": "alu", "kernel": "k_smooth (fused smoothing step, FP32 FFMA)",
-                "achieved": fl / tsec / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-                "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
+    alu_peak = pk.get("fp32_tflops") or NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    alu_src = ("measured FFMA loop" if pk.get("fp32_tflops")
+               else f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz")
+    dom = max(fams, key=lambda k: fams[k]["s"])
+    fd = fams[dom]
+    if dom == "cuda":
+        roof = {"bound": "alu", "kernel": "CUDA-core FP32 smoothing step / residual (FFMA)",
+                "achieved": fd["flops"] / fd["s"] / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                "peak_source": alu_src}
     else:
-        # BF16 channel mixing on the tensor cores: the step streams e, r, a, s
-        roof = {"bound": "hbm", "kernel": "k_smooth_tc (fused smoothing step, tcgen05 BF16)",
-                "achieved": by / tsec / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+        name = {"ts": "k_smooth_ts (tcgen05, A operands in TMEM)",
+                "tc": "k_smooth_tc (tcgen05 BF16, shared-memory operands)"}[dom]
+        roof = {"bound": "hbm", "kernel": name, "achieved": fd["bytes"] / fd["s"] / 1e9,
+                "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "peak_source": f"measured copy bandwidth ({pk_src})"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
+    roof["families"] = {k: dict(v, share=v["s"] / sum(x["s"] for x in fams.values()))
+                        for k, v in fams.items()}
     roof["detail"] = detail
 
     # end to end through the C ABI with host buffers (copies inside the call)
@@ -538,11 +581,13 @@ def main():
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if prec == mcmg.FP32 else "bf16/f32", "data": "synthetic",
+        "dtype": {mcmg.FP32: "f32", mcmg.BF16: "bf16/f32",
+                  mcmg.FP32_TC: "f32 (tf32x3 tensor-core mixing)"}[prec], "data": "synthetic",
         "config": {"workload": args.workload, "grid": [wl["n"]] * wl["dim"],
                    "levels": wl["levels"], "channels": wl["channels"],
                    "nu_pre": wl["nu_pre"], "nu_post": wl["nu_post"],
                    "fgmres_restart": sp["restart"], "tol": wl["tol"],
+                   "precision": wl["precision"],
                    "l2": "flushed between solves (256 MiB write)", "parallelism": f"replicas{world}"},
         "vcycles_per_s": sum(iters) * world / total,
         "vcycles_per_s_standalone": 1.0 / vc_s,

@@ -36,19 +36,37 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
+def _obj_stale(src: str, obj: str, flags_file: str, flags: str) -> bool:
+    """An object is rebuilt when it is missing, older than its source or any
+    header, or was compiled with other flags."""
+    if not os.path.exists(obj) or not os.path.exists(flags_file):
+        return True
+    if open(flags_file).read() != flags:
+        return True
+    t = os.path.getmtime(obj)
+    deps = [src] + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    return any(os.path.getmtime(p) > t for p in deps)
+
+
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD_DIR, exist_ok=True)
     objs = []
     procs = []
+    flags = " ".join([*ARCH, *FLAGS, *extra])
     for src in sources():
         obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+        flags_file = obj + ".flags"
+        objs.append(obj)
+        if not force and not _obj_stale(src, obj, flags_file, flags):
+            continue
+        with open(flags_file, "w") as fh:
+            fh.write(flags)
         cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd))
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
-        objs.append(obj)
     failed = []
     for src, p in procs:
         out, _ = p.communicate()
@@ -57,6 +75,11 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         elif verbose and out:
             print(out.decode())
     if failed:
+        for src, _ in failed:     # a failed object must not look fresh next time
+            obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+            for f in (obj, obj + ".flags"):
+                if os.path.exists(f):
+                    os.remove(f)
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
     tmp = LIB + ".tmp"

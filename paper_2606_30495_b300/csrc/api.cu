@@ -455,7 +455,36 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
         return cleanup(), s;
       MCMG_CUDA(cudaMemcpy(lv.tcw.tiles, host.data(), host.size() * sizeof(uint16_t),
                            cudaMemcpyHostToDevice));
-      lv.use_tc = true;
+      if (ts_supported(C, MCMG_BF16)) {      // TMEM-operand kernels, same tile layout
+        lv.use_ts = true;
+        lv.ts_prec = MCMG_BF16;
+        lv.ts_mats = lv.tcw.tiles;
+      } else {
+        lv.use_tc = true;
+      }
+    }
+    if (w->precision == MCMG_FP32_TC && ts_supported(C, MCMG_FP32_TC)) {
+      // TF32 hi / lo halves of every matrix: taps, K_A, K_S, W^(i)
+      const size_t per = (size_t)2 * (2 * C) * (2 * C);    // floats per matrix
+      const int ntile = T + 2 + ns;
+      std::vector<float> host(per * ntile);
+      std::vector<float2> mat((size_t)C * C);
+      auto put = [&](const double* src, int t) {
+        for (size_t i = 0; i < (size_t)C * C; ++i)
+          mat[i] = make_float2((float)src[2 * i], (float)src[2 * i + 1]);
+        pack_ts_tf32(mat.data(), C, host.data() + per * t);
+      };
+      for (int t = 0; t < T; ++t) put(lb[l].W + (size_t)2 * t * C * C, t);
+      put(lb[l].KA, T);
+      put(lb[l].KS, T + 1);
+      for (int i = 0; i < ns; ++i) put(lb[l].Ws + (size_t)2 * i * C * C, T + 2 + i);
+      uint4* dst = nullptr;
+      if ((s = dev_alloc(h, h->arena, (void**)&dst, host.size() * sizeof(float))))
+        return cleanup(), s;
+      MCMG_CUDA(cudaMemcpy(dst, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice));
+      lv.use_ts = true;
+      lv.ts_prec = MCMG_FP32_TC;
+      lv.ts_mats = dst;
     }
   }
   {
@@ -543,7 +572,7 @@ mcmg_status mcmg_setup(mcmg_ctx c, const mcmg_medium* m, double omega, const mcm
     set_error("levels must be in 1..%d", MCMG_MAX_LEVELS);
     return MCMG_ERR_ARG;
   }
-  if (w->precision != MCMG_FP32 && w->precision != MCMG_BF16) {
+  if (w->precision != MCMG_FP32 && w->precision != MCMG_BF16 && w->precision != MCMG_FP32_TC) {
     set_error("unknown precision %d", w->precision);
     return MCMG_ERR_ARG;
   }
@@ -801,6 +830,14 @@ mcmg_status mcmg_residual_restrict(mcmg_handle h, int level, const void* r, cons
   cudaStream_t st = (cudaStream_t)stream;
   MCMG_TRY(launch_smooth(lv, 0, (const float2*)r, (const float2*)e, h->work->t[level], 1, nrhs, st));
   return launch_restrict(lv, h->work->t[level], (float2*)rc, nrhs, st);
+}
+
+mcmg_status mcmg_residual(mcmg_handle h, int level, const void* r, const void* e, void* t,
+                          int nrhs, void* stream) {
+  MCMG_TRY(check_level(h, level, false));
+  if (!r || !e || !t || nrhs < 1 || t == e) { set_error("bad argument"); return MCMG_ERR_ARG; }
+  return launch_smooth(h->lv[level], 0, (const float2*)r, (const float2*)e, (float2*)t, 1, nrhs,
+                       (cudaStream_t)stream);
 }
 
 mcmg_status mcmg_coarse_basis(mcmg_handle h, int level, long long node, int channel, void* out,

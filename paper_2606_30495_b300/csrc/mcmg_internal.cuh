@@ -91,7 +91,10 @@ struct Level {
   float2* Wsmt = nullptr;     // [nsteps][C][C]
   float2* Rt = nullptr;       // [T3][C][Cn]
   float2* Pt = nullptr;       // [T3][Cn][C]
-  bool use_tc = false;        // smoothing step on tcgen05 (BF16 mixing)
+  bool use_tc = false;        // smoothing step on tcgen05 (BF16 mixing), SMEM operands
+  bool use_ts = false;        // smoothing step and residual on tcgen05, TMEM A operands
+  int ts_prec = -1;           // MCMG_BF16 or MCMG_FP32_TC when use_ts
+  const uint4* ts_mats = nullptr;  // weight matrices in the operand layout of ts_prec
   // CUDA-core kernel shape per operation in use (0 smoothing step, 1 residual,
   // 2 restriction, 3 prolongation) and the autotuner's choice
   int shape[4] = {-1, -1, -1, -1};
@@ -106,6 +109,14 @@ mcmg_status launch_smooth_tc(const Level& L, const TcWeights& W, int step, const
                              const float2* e_in, float2* e_out, int nrhs, int* err,
                              cudaStream_t st);
 void pack_tc_tile(const float2* Mc, int C, uint16_t* out);
+
+// tensor-core smoothing step and residual with A operands in tensor memory
+// (kernels_ts.cu); mode as launch_smooth
+bool ts_supported(int C, int prec);
+mcmg_status launch_smooth_ts(const Level& L, int step, const float2* r, const float2* e_in,
+                             float2* out, int mode, int nrhs, cudaStream_t st);
+// complex C x C matrix -> TF32 hi and lo halves of its real block form (2 * 4C^2 floats)
+void pack_ts_tf32(const float2* Mc, int C, float* out);
 
 // Launchers used by the V-cycle (kernels_vcycle.cu), asynchronous on `st`.
 // mode 0: e_out = e_in + S^(step)(r - A e_in); mode 1: e_out = r - A e_in.

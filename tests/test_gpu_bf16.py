@@ -114,7 +114,7 @@ def test_tc_workload_vcycle_256(ctx):
 
 def test_tc_residual_restrict(case):
     """Residual r - A_l(e) and restriction on a BF16 handle (the residual runs
-    on the CUDA cores in FP32)."""
+    on the tensor cores for C_l <= 32, on the CUDA cores in FP32 above)."""
     m, h = case
     w = m["w"]
     for l in range(w["levels"] - 1):

@@ -1,0 +1,194 @@
+"""Parity of the tensor-core smoothing step and residual whose A operands
+live in tensor memory (persistent CTAs), in both operand precisions, with the
+FP64 oracle.
+
+* FP32-accurate mixing (three TF32 products per FP32 product): held to the
+  FP32 bound, 1e-5 relative (L2 and element-wise), per step, per residual
+  and per V-cycle, and the full-size 256^2 solve to the stored oracle
+  iteration count within 10%.
+* BF16 mixing: 1e-2 per step, 2e-2 per V-cycle (the BF16 bound).
+
+The large cases have more 128-node tiles than the grid has CTAs, so every
+CTA walks several tiles, and node counts that are not a multiple of 128.
+Every bounded wait inside the kernels must have finished (error word 0).
+"""
+import numpy as np
+import pytest
+
+from oracle import mcmg_oracle as O
+from paper_2606_30495_b300 import inputs as I
+from tests._models import model, relerr, rng, workload_model
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL_BF16_STEP = 1e-2
+TOL_BF16_VCYCLE = 2e-2
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2606_30495_b300 import mcmg
+    c = mcmg.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=torch.complex64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def handle(ctx, m, precision):
+    from paper_2606_30495_b300 import mcmg
+    return mcmg.Handle(ctx, m["c"], m["omega"], m["sponge"], m["gamma_max"], m["w"],
+                       precision=precision)
+
+
+def _prec(name):
+    from paper_2606_30495_b300 import mcmg
+    return {"fp32tc": mcmg.FP32_TC, "bf16": mcmg.BF16}[name]
+
+
+def _tols(name):
+    return (TOL32, TOL32) if name == "fp32tc" else (TOL_BF16_STEP, TOL_BF16_VCYCLE)
+
+
+CASES = [
+    ("fp32tc", (34, 30), [8, 16], "random"),
+    ("fp32tc", (20, 36), [16, 32], "random"),
+    ("fp32tc", (34, 30), [8, 16], "structured"),
+    ("fp32tc", (6, 8, 10), [8, 16], "random"),
+    ("fp32tc", (10, 6, 14), [16, 16], "random"),
+    ("bf16", (22, 18), [8, 32], "random"),
+    ("bf16", (6, 10, 14), [32, 32], "random"),
+]
+IDS = [f"{p}-{'x'.join(map(str, s))}-C{'-'.join(map(str, c))}-{m}" for p, s, c, m in CASES]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=IDS)
+def case(request, ctx):
+    prec, shape, channels, mode = request.param
+    m = model(shape, channels, mode=mode, seed=6)
+    h = handle(ctx, m, _prec(prec))
+    yield prec, m, h
+    assert h.device_error() == 0
+    h.close()
+
+
+def _check_step(prec, m, h, l, first, nrhs=2, seed=10):
+    w = m["w"]
+    C = w["channels"][l]
+    shp = tuple(n >> l for n in m["shape"]) + (C,)
+    a, s = m["feats"][l]
+    nsteps = w["nu_pre"][l] + w["nu_post"][l]
+    tol = _tols(prec)[0]
+    for step in sorted({0, nsteps - 1}):
+        r = I.complex_normal((nrhs,) + shp, rng(seed + step))
+        e_in = None if first else I.complex_normal((nrhs,) + shp, rng(seed + 10 + step))
+        out = torch.zeros(r.shape, dtype=torch.complex64, device="cuda")
+        h.smooth(l, step, dev(r), None if first else dev(e_in), out, nrhs=nrhs)
+        want = []
+        for k in range(nrhs):
+            e0 = np.zeros(shp, complex) if first else e_in[k]
+            want.append(e0 + O.op_S(w["lvl"][l], s, step, r[k] - O.op_A(w["lvl"][l], a, e0)))
+        err = relerr(host(out), np.stack(want))
+        assert err < tol, (l, step, err)
+
+
+@pytest.mark.parametrize("first", [True, False])
+def test_step(case, first):
+    prec, m, h = case
+    for l in range(m["w"]["levels"]):
+        _check_step(prec, m, h, l, first)
+
+
+def test_residual_restrict(case):
+    """r - A_l(e) (the tensor-core residual on C_l in {8, 16[, 32]}), then R."""
+    prec, m, h = case
+    w = m["w"]
+    tol = _tols(prec)[0]
+    for l in range(w["levels"] - 1):
+        C, Cn = w["channels"][l], w["channels"][l + 1]
+        shp = tuple(n >> l for n in m["shape"])
+        cshp = tuple(n >> (l + 1) for n in m["shape"])
+        a, _ = m["feats"][l]
+        lv = w["lvl"][l]
+        r = I.complex_normal((2,) + shp + (C,), rng(30))
+        e = I.complex_normal((2,) + shp + (C,), rng(31))
+        rc = torch.zeros((2,) + cshp + (Cn,), dtype=torch.complex64, device="cuda")
+        h.residual_restrict(l, dev(r), dev(e), rc, nrhs=2)
+        want = np.stack([O.restrict(lv["R"], r[k] - O.op_A(lv, a, e[k])) for k in range(2)])
+        assert relerr(host(rc), want) < tol, l
+
+
+def test_vcycle(case):
+    prec, m, h = case
+    r = I.complex_normal((2,) + m["shape"], rng(40))
+    want = np.stack([O.vcycle(m["w"], m["feats"], ri) for ri in r])
+    e = torch.zeros(r.shape, dtype=torch.complex64, device="cuda")
+    h.vcycle(dev(r), e, nrhs=2)
+    assert relerr(host(e), want) < _tols(prec)[1]
+
+
+@pytest.mark.parametrize("prec,shape,channels", [
+    ("fp32tc", (254, 162), [16, 16]),       # 322 tiles over 2 CTAs per SM
+    ("fp32tc", (60, 66, 42), [8, 8]),       # 1300 tiles over 4 CTAs per SM, ragged
+    ("bf16", (60, 66, 42), [8, 8]),         # 1300 tiles over 8 CTAs per SM, ragged
+])
+def test_persistent_multi_tile(ctx, prec, shape, channels):
+    """More tiles than CTAs: each persistent CTA walks several tiles."""
+    m = model(shape, channels, mode="random", seed=8)
+    h = handle(ctx, m, _prec(prec))
+    try:
+        for first in (True, False):
+            _check_step(prec, m, h, 0, first, nrhs=1, seed=50)
+        w = m["w"]
+        a, _ = m["feats"][0]
+        lv = w["lvl"][0]
+        C, Cn = w["channels"][0], w["channels"][1]
+        r = I.complex_normal(shape + (C,), rng(60))
+        e = I.complex_normal(shape + (C,), rng(61))
+        rc = torch.zeros(tuple(n >> 1 for n in shape) + (Cn,), dtype=torch.complex64, device="cuda")
+        h.residual_restrict(0, dev(r), dev(e), rc, nrhs=1)
+        want = O.restrict(lv["R"], r - O.op_A(lv, a, e))
+        assert relerr(host(rc), want) < _tols(prec)[0]
+        assert h.device_error() == 0
+    finally:
+        h.close()
+
+
+def test_fp32tc_full_size_256_vcycle_and_solve(ctx):
+    """The 256^2 workload with FP32-accurate tensor-core mixing: V-cycle within
+    1e-5 of the oracle, and the solve within 10% of the stored oracle
+    iteration count with the true FP64 residual at 1e-6."""
+    import json
+    import os
+    from paper_2606_30495_b300 import mcmg
+    m = workload_model("helm2d_n256_grf")
+    feats = O.setup(m["q"], m["w"])
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                    "oracle_solves.json")))["helm2d_n256_grf"]
+    h = handle(ctx, m, mcmg.FP32_TC)
+    try:
+        for r in (I.point_source(m["shape"]), I.complex_normal(m["shape"], rng(6))):
+            want = O.vcycle(m["w"], feats, r)
+            e = torch.zeros(m["shape"], dtype=torch.complex64, device="cuda")
+            h.vcycle(dev(r), e)
+            assert relerr(host(e), want) < TOL32
+        f = I.point_source(m["shape"])
+        u = torch.zeros(m["shape"], dtype=torch.complex128, device="cuda")
+        st, info = h.solve(dev(f, torch.complex128), u, tol=1e-6, restart_m=g["restart"],
+                           max_iters=4000)
+        assert st == 0 and info["converged"], info
+        res = np.linalg.norm(f - O.apply_A(m["q"], host(u))) / np.linalg.norm(f)
+        assert res <= 1e-6, res
+        assert abs(info["iters"] - g["iters"]) <= 0.1 * g["iters"], (info, g)
+        assert h.device_error() == 0
+    finally:
+        h.close()
