@@ -6,16 +6,23 @@ restarted flexible GMRES preconditioned by one McMg V-cycle per iteration
 (every row of the hot path: operator, lift, smoothing, restriction,
 prolongation, projection, Krylov orthogonalisation, solution update).
 
-Default workload: 256^2 Gaussian-random-field medium (c in [1, 3], correlation
-16 cells), 8 points per wavelength at c = 1, 16-cell sponge, 4 levels with
-8/16/32/64 channels, FP32 channel mixing, one point source.  Inputs and the
-setup are resident on the device before the timed region; each timed solve
-is bracketed by CUDA events on its stream and L2 is flushed (a 256 MiB write)
+Default workload: the largest single-GPU configuration, 256^3 grid, 7-point
+stencil, Gaussian-random-field medium (c in [1, 3], correlation 16 cells)
+with three spheres of 5x contrast, 8 points per wavelength at c = 1, 10-cell
+sponge, 5 levels with 8/16/32/64/64 channels, FGMRES(30), one point source,
+with FP32-accurate channel mixing (three TF32 tensor-core products per FP32
+product where the kernels exist, FP32 FFMA elsewhere); the same solve with
+BF16 channel mixing is reported beside it under "bf16".  Inputs and the setup
+are resident on the device before the timed region; each timed solve is
+bracketed by CUDA events on its stream and L2 is flushed (a 256 MiB write)
 between solves, outside the events.
 
 `--impl reference` times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload (a few FGMRES iterations per step, scaled to a
-full solve by the oracle's iteration count).
+sample of the same workload: a few FGMRES iterations per step on the same
+recipe (on a 4x coarser copy of the grid when the grid has more than 2^18
+nodes, scaled by the node ratio, the oracle's cost per iteration being
+linear in the nodes), scaled to a full solve by the stored oracle iteration
+count or, without one, the GPU's.
 
 Prints one JSON line on rank 0.
 """
@@ -39,6 +46,14 @@ METRIC = "solves/s and V-cycles/s to rel. residual 1e-6; p50/p99 solve latency"
 MAX_ITERS = {"helm2d_n64_homogeneous": 2000, "helm2d_n64_slmg": 2000, "helm2d_n256_grf": 4000,
              "helm2d_n1024_layers": 20000, "helm3d_n256_grf": 8000, "helm2d_n256_layers": 20000,
              "helm3d_n64_grf": 4000}
+# GPU iteration counts of the workloads whose full-size oracle solve is out of
+# reach, to scale the oracle's sampled iterations (FP32-accurate mixing; B300)
+GPU_ITERS = {"helm3d_n256_grf": 227, "helm2d_n1024_layers": 8690}
+# DRAM bytes (read + write) per launch of the dominant launch class, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
+# (workload, precision, level, kind); the profile summaries record the
+# command and the scaling.  A key is dropped when its kernel changes.
+NCU_TRAFFIC = {}
 FP32_LANES_PER_SM = 128
 NUM_SMS = 148
 
@@ -49,11 +64,16 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="mcmg", choices=["mcmg", "reference"])
-    p.add_argument("--workload", default="helm2d_n256_grf")
-    p.add_argument("--precision", default="", choices=["", "fp32", "bf16", "fp32tc"],
-                   help="override the workload's channel-mixing precision")
+    p.add_argument("--workload", default="helm3d_n256_grf")
+    p.add_argument("--precision", default="fp32tc", choices=["native", "fp32", "bf16", "fp32tc"],
+                   help="channel-mixing precision ('native': the workload's own)")
+    p.add_argument("--no-bf16", action="store_true", help="skip the BF16 comparison solves")
+    p.add_argument("--profile-launch", default="",
+                   help="LEVEL,KIND[,REPS]: after setup, run only that smoothing launch class "
+                        "(KIND first | step | residual) REPS times (default 5) and exit; for "
+                        "profilers")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-sample-iters", type=int, default=12)
+    p.add_argument("--cpu-sample-iters", type=int, default=3)
     p.add_argument("--n", type=int, default=0,
                    help="override the grid size (smaller copies of a workload for profiling)")
     p.add_argument("--max-iters", type=int, default=0)
@@ -179,13 +199,10 @@ def residual_flops(C, d):
 
 def kernel_family(prec_name, C):
     """Which kernel runs a level's smoothing step and residual: 'ts' (tensor
-    cores, A operands in tensor memory: BF16 for C in {8, 16, 32}, FP32-accurate
-    for C in {8, 16}), 'tc' (BF16 step with shared-memory operands, C = 64;
-    its residual on the CUDA cores) or 'cuda' (FP32 on the CUDA cores)."""
-    if prec_name == "bf16":
-        return "ts" if C in (8, 16, 32) else ("tc" if C == 64 else "cuda")
-    if prec_name == "fp32tc":
-        return "ts" if C in (8, 16) else "cuda"
+    cores, A operands in tensor memory; BF16 or FP32-accurate mixing, C >= 8)
+    or 'cuda' (FP32 on the CUDA cores)."""
+    if prec_name in ("bf16", "fp32tc") and C >= 8:
+        return "ts"
     return "cuda"
 
 
@@ -213,7 +230,7 @@ def time_smoothing(h, wl, torch, stream, reps=20):
             if kind == "residual":
                 run = lambda: h.residual(l, r, e, o, stream=stream)
                 fl, by = residual_flops(C, d) * nodes, residual_bytes(C) * nodes
-                kf = "cuda" if fam == "tc" else fam
+                kf = fam
             else:
                 first = kind == "first"
                 run = lambda: h.smooth(l, 0, r, None if first else e, o, stream=stream)
@@ -240,22 +257,37 @@ def time_smoothing(h, wl, torch, stream, reps=20):
     return fams, detail
 
 
-def oracle_rate(wl, c, omega, w, iters_full, sample_iters):
-    """The FP64 oracle timed on the host: `sample_iters` FGMRES iterations
-    (one V-cycle + Gram-Schmidt each), scaled to a full solve of iters_full."""
-    import numpy as np
+def sample_size(wl):
+    """Grid size of the oracle's sample: the workload's own up to 2^18 nodes,
+    else a 4x coarser copy of the same recipe."""
+    return wl["n"] if wl["n"] ** wl["dim"] <= (1 << 18) else wl["n"] // 4
 
+
+def oracle_rate(name, wl, iters_full, sample_iters):
+    """The FP64 oracle timed on the host: `sample_iters` FGMRES iterations
+    (one V-cycle + Gram-Schmidt each) on the workload's recipe at
+    sample_size(wl), scaled by the node ratio to the full grid and by
+    iters_full to a full solve (the setup is outside the timing, as on the GPU)."""
     from oracle import mcmg_oracle as O
     from paper_2606_30495_b300 import inputs as I
-    q = O.wavenumber_coef(c, omega, wl["sponge"], wl["gamma_max"])
+    ns = sample_size(wl)
+    ws = I.workload(name, n=ns)
+    for k in ("precision",):
+        ws[k] = wl[k]
+    c = I.medium_for(ws)
+    omega = I.omega_for_ppw(c.min(), ws["ppw"], ns)
+    w = I.weights_for(ws)
+    q = O.wavenumber_coef(c, omega, ws["sponge"], ws["gamma_max"])
     feats = O.setup(q, w)
     f = I.point_source(c.shape)
     t0 = time.perf_counter()
     O.fgmres(lambda u: O.apply_A(q, u), lambda v: O.vcycle(w, feats, v), f,
              m=sample_iters + 1, tol=1e-300, max_iters=sample_iters)
     dt = time.perf_counter() - t0
-    per_iter = dt / sample_iters
-    return dict(per_iter_s=per_iter, solve_s=per_iter * iters_full, wall_s=dt)
+    scale = (wl["n"] / ns) ** wl["dim"]
+    per_iter = dt / sample_iters * scale
+    return dict(per_iter_s=per_iter, solve_s=per_iter * iters_full, wall_s=dt, n_sample=ns,
+                scale=scale)
 
 
 def cpu_cores():
@@ -275,34 +307,80 @@ def golden_iters(name):
     return None, None
 
 
+def profile_launch(args, h, wl, torch, mcmg, ctx):
+    """Run one launch class of the V-cycle (level, kind) on random fields of
+    that level, REPS times on one stream, and print its mean CUDA-event time."""
+    parts = args.profile_launch.split(",")
+    level, kind = int(parts[0]), parts[1]
+    reps = int(parts[2]) if len(parts) > 2 else 5
+    C = wl["channels"][level]
+    shp = tuple(n >> level for n in (wl["n"],) * wl["dim"]) + (C,)
+    r = torch.randn(shp, dtype=torch.complex64, device="cuda")
+    e = torch.randn(shp, dtype=torch.complex64, device="cuda")
+    o = torch.empty_like(e)
+    stream = torch.cuda.Stream()
+    run = {"first": lambda: h.smooth(level, 0, r, None, o, stream=stream),
+           "step": lambda: h.smooth(level, 0, r, e, o, stream=stream),
+           "residual": lambda: h.residual(level, r, e, o, stream=stream)}[kind]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(reps):
+            run()
+        e1.record(stream)
+    e1.synchronize()
+    print(json.dumps({"profile_launch": {"workload": args.workload, "precision": wl["precision"],
+                                         "level": level, "kind": kind, "C": C,
+                                         "nodes": math.prod(shp[:-1]), "reps": reps,
+                                         "us": e0.elapsed_time(e1) * 1e3 / reps}}))
+    h.close()
+    ctx.close()
+
+
+def config_of(args, wl, restart):
+    return {"workload": args.workload, "grid": [wl["n"]] * wl["dim"], "levels": wl["levels"],
+            "channels": wl["channels"], "nu_pre": wl["nu_pre"], "nu_post": wl["nu_post"],
+            "fgmres_restart": restart, "tol": wl["tol"], "precision": wl["precision"],
+            "l2": "flushed between solves (256 MiB write)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl, c, omega, w = setup_workload(args.workload, args.n)
+    from paper_2606_30495_b300 import inputs as I
+    wl = I.workload(args.workload, **({"n": args.n} if args.n else {}))
+    if args.precision != "native":
+        wl["precision"] = args.precision
     iters, src = golden_iters(args.workload)
     if iters is None:
+        iters, src = GPU_ITERS.get(args.workload), "gpu"
+    if iters is None:
         print(json.dumps({"impl": "reference", "unavailable":
-                          f"no stored oracle iteration count for {args.workload}"}))
+                          f"no iteration count to scale the oracle's sample for {args.workload}"}))
         return
-    k = max(2, args.cpu_sample_iters // 4)
+    k = max(1, args.cpu_sample_iters)
     for _ in range(args.warmup):
-        oracle_rate(wl, c, omega, w, iters, 1)
-    times = []
+        oracle_rate(args.workload, wl, iters, 1)
+    walls, solves = [], []
     for _ in range(args.steps):
-        times.append(oracle_rate(wl, c, omega, w, iters, k)["solve_s"])
-    total = sum(times)
-    value = args.steps / total
+        o = oracle_rate(args.workload, wl, iters, k)
+        walls.append(o["wall_s"])
+        solves.append(o["solve_s"])
+    value = args.steps / sum(solves)
     cores = cpu_cores()
-    sample = (f"{k} FGMRES iterations of the FP64 numpy oracle per step, scaled to the "
-              f"oracle's {iters}-iteration solve")
+    sample = (f"{k} FGMRES iterations per step of the FP64 numpy oracle on the recipe at "
+              f"{o['n_sample']}^{wl['dim']}, scaled by the node ratio {o['scale']:.0f} and to a "
+              f"{iters}-iteration solve ({'oracle count' if src == 'oracle' else 'GPU count'})")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * sum(walls) / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
-        "config": {"workload": args.workload, "grid": [wl["n"]] * wl["dim"],
-                   "levels": wl["levels"], "channels": wl["channels"]},
+        "config": dict(config_of(args, wl, wl["restart"]), parallelism=f"replicas{args.gpus}"),
+        "value_from": "solves/s extrapolated from the sampled iterations; ms_per_step is the "
+                      "wall time of one sampled step",
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
@@ -444,7 +522,7 @@ def main():
     from paper_2606_30495_b300 import mcmg
 
     wl, c, omega, w = setup_workload(args.workload, args.n)
-    if args.precision:
+    if args.precision != "native":
         wl["precision"] = args.precision
     sp = dict(restart=wl["restart"], max_iters=args.max_iters or MAX_ITERS[args.workload])
     prec = {"fp32": mcmg.FP32, "bf16": mcmg.BF16, "fp32tc": mcmg.FP32_TC}[wl["precision"]]
@@ -452,6 +530,8 @@ def main():
     t0 = time.perf_counter()
     h = mcmg.Handle(ctx, c, omega, wl["sponge"], wl["gamma_max"], w, precision=prec)
     t_setup = time.perf_counter() - t0
+    if args.profile_launch:
+        return profile_launch(args, h, wl, torch, mcmg, ctx)
     if args.shapes:
         for l, ops in enumerate(json.loads(args.shapes)):
             for op, sh in enumerate(ops):
@@ -526,27 +606,34 @@ def main():
     v1.synchronize()
     vc_s = v0.elapsed_time(v1) / 1e3 / nv
 
-    # dominant kernel family of the smoothing steps and residuals of one V-cycle
+    # the dominant launch class of the smoothing steps and residuals of one V-cycle
     fams, detail = time_smoothing(h, wl, torch, stream)
     pk, pk_src = peaks()
-    sm_mhz = pk.get("sm_max_mhz", 2032.0)
-    alu_peak = pk.get("fp32_tflops") or NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    alu_src = ("measured FFMA loop" if pk.get("fp32_tflops")
-               else f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz")
-    dom = max(fams, key=lambda k: fams[k]["s"])
-    fd = fams[dom]
-    if dom == "cuda":
-        roof = {"bound": "alu", "kernel": "CUDA-core FP32 smoothing step / residual (FFMA)",
-                "achieved": fd["flops"] / fd["s"] / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-                "peak_source": alu_src}
+    ffma_peak = mcmg.fp32_ffma_tflops(stream)          # measured live, this GPU, this run
+    dom = max(detail, key=lambda x: x["count"] * x["us"])
+    t_launch = dom["us"] * 1e-6
+    if dom["family"] == "cuda":
+        roof = {"bound": "alu", "achieved": dom["tflops"], "peak": ffma_peak, "unit": "TFLOP/s",
+                "peak_source": "measured FFMA loop (mcmg_fp32_ffma_tflops), this run",
+                "kernel": "CUDA-core FP32 smoothing step / residual"}
+    elif dom["family"] in ("ts", "tc") and dom["C"] <= 16:
+        roof = {"bound": "hbm", "achieved": dom["gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "peak_source": f"measured copy bandwidth ({pk_src})",
+                "kernel": "k_smooth_ts (tcgen05, A operands in tensor memory)"}
     else:
-        name = {"ts": "k_smooth_ts (tcgen05, A operands in TMEM)",
-                "tc": "k_smooth_tc (tcgen05 BF16, shared-memory operands)"}[dom]
-        roof = {"bound": "hbm", "kernel": name, "achieved": fd["bytes"] / fd["s"] / 1e9,
-                "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "peak_source": f"measured copy bandwidth ({pk_src})"}
+        # a contraction: executed tensor flops against the peak of its own operand type
+        tf = wl["precision"] == "fp32tc"
+        mult = 3.0 if tf else 1.0
+        peak = pk["bf16_tflops"] * (1.1 / 2.25 if tf else 1.0)
+        roof = {"bound": "tensor", "achieved": dom["tflops"] * mult, "peak": peak,
+                "unit": "TFLOP/s",
+                "peak_source": (f"measured cuBLAS BF16 burst ({pk_src})"
+                                + (" x nominal TF32/BF16 ratio 1.1/2.25" if tf else "")),
+                "kernel": "k_smooth_tsb (tcgen05, streamed weights)" + (", 3 TF32 products"
+                                                                         if tf else "")}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["launch"] = {k: dom[k] for k in ("level", "C", "kind", "count", "us")}
+    roof["traffic"] = NCU_TRAFFIC.get((args.workload, wl["precision"], dom["level"], dom["kind"]))
     roof["families"] = {k: dict(v, share=v["s"] / sum(x["s"] for x in fams.values()))
                         for k, v in fams.items()}
     roof["detail"] = detail
@@ -563,16 +650,43 @@ def main():
         e2e_times.append(time.perf_counter() - t1)
     e2e_value = job_rate(len(e2e_times), world, replica_total(sum(e2e_times), world, "cuda"))
 
+    # the same solve with BF16 channel mixing (reported beside the headline)
+    bf16 = None
+    if not args.no_bf16 and prec != mcmg.BF16:
+        hb = mcmg.Handle(ctx, c, omega, wl["sponge"], wl["gamma_max"], w, precision=mcmg.BF16)
+        bt, bi = [], []
+        for k in range(3):
+            with torch.cuda.stream(stream):
+                u.zero_()
+                flush.fill_(k & 0xFF)
+            b0 = torch.cuda.Event(enable_timing=True)
+            b1 = torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            stb, ib = hb.solve(f, u, tol=wl["tol"], restart_m=sp["restart"],
+                               max_iters=sp["max_iters"], stream=stream)
+            b1.record(stream)
+            b1.synchronize()
+            if k > 0:                                   # the first one warms up
+                bt.append(b0.elapsed_time(b1) / 1e3)
+                bi.append(ib)
+        bf16 = {"value": len(bt) / sum(bt), "unit": "solves/s",
+                "iters_per_solve": [i["iters"] for i in bi],
+                "rel_residual_fp64": max(i["rel_residual"] for i in bi),
+                "converged": all(i["converged"] for i in bi),
+                "timed_solves": len(bt)}
+        hb.close()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         it_o, src = golden_iters(args.workload)
         it_o = it_o or int(statistics.median(iters))
-        o = oracle_rate(wl, c, omega, w, it_o, args.cpu_sample_iters)
+        o = oracle_rate(args.workload, wl, it_o, args.cpu_sample_iters)
         cpu = {"value": 1.0 / o["solve_s"], "unit": "solves/s", "cores": cpu_cores(),
                "kind": "oracle",
                "sample": (f"{args.cpu_sample_iters} FGMRES iterations of the FP64 numpy oracle "
-                          f"({o['wall_s']:.1f} s), scaled to a {it_o}-iteration solve"
-                          f" ({'oracle count' if src else 'GPU count'})")}
+                          f"on the recipe at {o['n_sample']}^{wl['dim']} ({o['wall_s']:.1f} s), "
+                          f"scaled by the node ratio {o['scale']:.0f} and to a {it_o}-iteration "
+                          f"solve ({'oracle count' if src else 'GPU count'})")}
 
     lat = sorted(times)
     p50 = lat[len(lat) // 2]
@@ -583,12 +697,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {mcmg.FP32: "f32", mcmg.BF16: "bf16/f32",
                   mcmg.FP32_TC: "f32 (tf32x3 tensor-core mixing)"}[prec], "data": "synthetic",
-        "config": {"workload": args.workload, "grid": [wl["n"]] * wl["dim"],
-                   "levels": wl["levels"], "channels": wl["channels"],
-                   "nu_pre": wl["nu_pre"], "nu_post": wl["nu_post"],
-                   "fgmres_restart": sp["restart"], "tol": wl["tol"],
-                   "precision": wl["precision"],
-                   "l2": "flushed between solves (256 MiB write)", "parallelism": f"replicas{world}"},
+        "config": dict(config_of(args, wl, sp["restart"]), parallelism=f"replicas{world}"),
         "vcycles_per_s": sum(iters) * world / total,
         "vcycles_per_s_standalone": 1.0 / vc_s,
         "iters_per_solve": iters, "rel_residual_fp64": res, "true_rel_residual_oracle": true_res,
@@ -601,8 +710,11 @@ def main():
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 16 * n * 2,
                 "d2h_bytes_per_step": 16 * n},
         "peaks_source": pk_src,
+        "fp32_ffma_tflops_measured": ffma_peak,
         "kernel_shapes": kernel_shapes,
     }
+    if bf16:
+        out["bf16"] = bf16
     if cpu:
         out["cpu_baseline"] = cpu
     if rank == 0:

@@ -320,6 +320,12 @@ int mcmg_kernel_shape_count(int op);
 mcmg_status mcmg_get_kernel_shape(mcmg_handle h, int level, int op, int* shape);
 mcmg_status mcmg_set_kernel_shape(mcmg_handle h, int level, int op, int shape);
 
+/* Measurement aid (the paper has no counterpart): the FP32 fused
+ * multiply-add rate of the current device in TFLOP/s, timed with CUDA events
+ * on `stream` over a loop of independent FFMA chains (about 5 ms of work).
+ * It is the roofline denominator of the CUDA-core FP32 kernels.  Synchronous. */
+mcmg_status mcmg_fp32_ffma_tflops(void* stream, double* tflops);
+
 /* Number of kernel launches the library has issued in this process (a
  * captured graph counts as its kernel nodes).  For launch accounting.        */
 uint64_t mcmg_kernel_launches(void);

@@ -89,25 +89,26 @@ namespace ts {
 // between 16-byte K chunks, SBO = 128 B between 8-row groups).
 template <int K2, int P>
 __device__ __forceinline__ void gemm(uint32_t d, uint32_t a_slot, uint32_t b, bool accumulate) {
-  const uint32_t lbo = K2 * 16;
+  // one descriptor per matrix, stepped along K by adding the byte offset >> 4
+  // to its start-address field (the shared-memory addresses stay below 256 KB)
+  constexpr uint32_t lbo = K2 * 16;
+  constexpr uint64_t kstep = (2 * lbo) >> 4;
   if constexpr (P == 0) {
     constexpr uint32_t idesc = tc::make_idesc(M, K2);
+    const uint64_t b0 = tc::make_desc(b, lbo, 128);
 #pragma unroll
-    for (int s = 0; s < K2 / 16; ++s) {
-      const uint64_t bd = tc::make_desc(b + 2 * s * lbo, lbo, 128);
-      tc::mma_bf16_ts(d, a_slot + 8 * s, bd, idesc, (accumulate || s > 0) ? 1u : 0u);
-    }
+    for (int s = 0; s < K2 / 16; ++s)
+      tc::mma_bf16_ts(d, a_slot + 8 * s, b0 + s * kstep, idesc, (accumulate || s > 0) ? 1u : 0u);
   } else {
     constexpr uint32_t idesc = tc::make_idesc_tf32(M, K2);
-    const uint32_t blo = b + Cfg<K2, P>::HALF;
+    const uint64_t bh0 = tc::make_desc(b, lbo, 128);
+    const uint64_t bl0 = bh0 + (Cfg<K2, P>::HALF >> 4);
 #pragma unroll
     for (int s = 0; s < K2 / 8; ++s) {
-      const uint64_t bh = tc::make_desc(b + 2 * s * lbo, lbo, 128);
-      const uint64_t bl = tc::make_desc(blo + 2 * s * lbo, lbo, 128);
       const uint32_t ahi = a_slot + 8 * s, alo = a_slot + K2 + 8 * s;
-      tc::mma_tf32_ts(d, alo, bh, idesc, (accumulate || s > 0) ? 1u : 0u);
-      tc::mma_tf32_ts(d, ahi, bl, idesc, 1u);
-      tc::mma_tf32_ts(d, ahi, bh, idesc, 1u);
+      tc::mma_tf32_ts(d, alo, bh0 + s * kstep, idesc, (accumulate || s > 0) ? 1u : 0u);
+      tc::mma_tf32_ts(d, ahi, bl0 + s * kstep, idesc, 1u);
+      tc::mma_tf32_ts(d, ahi, bh0 + s * kstep, idesc, 1u);
     }
   }
 }
@@ -772,6 +773,409 @@ fail:
   }
 }
 
+// ---------------------------------------------------------------------------
+// Large channel counts (K2 = 64 with TF32x3, K2 = 128 with either precision):
+// the weights no longer fit shared memory, so they stream through it.  One
+// CTA per SM (its TMEM columns fill the SM) of 256 threads: thread t owns row
+// 32 (w % 4) + lane of warp w and every other 16-column chunk of it (warps
+// 0-3 the even chunks, 4-7 the odd ones).  Each stencil tap is one A stage
+// (two K-halves for TF32x3 at K2 = 128, so that two A slots fit beside X and
+// Y); the weight matrices arrive per (matrix, K-half) unit in a ring of RB
+// shared-memory buffers filled by bulk asynchronous copies (thread 0,
+// transaction-count mbarriers); a buffer is refilled once the MMAs that read
+// it have committed.  The arithmetic and the phases are those above.
+// ---------------------------------------------------------------------------
+namespace ts {
+
+template <int K2, int P>
+struct Big {
+  static constexpr int NH = (P == 1 && K2 == 128) ? 2 : 1;   // K-halves per tap
+  static constexpr int KU = K2 / NH;                          // K of one stage
+  static constexpr int AW = P ? 2 * KU : KU / 2;              // TMEM columns per A slot
+  static constexpr int COLS = 512;
+  static_assert(2 * K2 + 2 * AW <= COLS, "TMEM");
+  static constexpr int SUB = KU * K2 * (P ? 4 : 2);           // bytes of one K-half (hi or bf16)
+  static constexpr int UNIT = P ? 2 * SUB : SUB;              // bytes of one streamed unit
+  static constexpr int MATB = P ? 2 * K2 * K2 * 4 : K2 * K2 * 2;
+  static constexpr int RB = (192 * 1024) / UNIT;              // ring buffers
+  static constexpr int THREADS = 256;
+  static constexpr int CPT = KU / 32;                         // 16-column chunks per thread per stage
+};
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(dst), "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tc::smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// The MMAs of one streamed unit: D (+)= A B^T over the unit's K range, A in
+// TMEM at a (hi at a, lo at a + KU for TF32x3), B at b in shared memory.
+template <int K2, int P>
+__device__ __forceinline__ void gemm_unit(uint32_t d, uint32_t a, uint32_t b, bool accumulate) {
+  using B = Big<K2, P>;
+  constexpr uint32_t lbo = K2 * 16;
+  constexpr uint64_t kstep = (2 * lbo) >> 4;
+  if constexpr (P == 0) {
+    constexpr uint32_t idesc = tc::make_idesc(M, K2);
+    const uint64_t b0 = tc::make_desc(b, lbo, 128);
+#pragma unroll
+    for (int s = 0; s < B::KU / 16; ++s)
+      tc::mma_bf16_ts(d, a + 8 * s, b0 + s * kstep, idesc, (accumulate || s > 0) ? 1u : 0u);
+  } else {
+    constexpr uint32_t idesc = tc::make_idesc_tf32(M, K2);
+    const uint64_t bh0 = tc::make_desc(b, lbo, 128);
+    const uint64_t bl0 = bh0 + (B::SUB >> 4);
+#pragma unroll
+    for (int s = 0; s < B::KU / 8; ++s) {
+      const uint32_t ahi = a + 8 * s, alo = a + B::KU + 8 * s;
+      tc::mma_tf32_ts(d, alo, bh0 + s * kstep, idesc, (accumulate || s > 0) ? 1u : 0u);
+      tc::mma_tf32_ts(d, ahi, bl0 + s * kstep, idesc, 1u);
+      tc::mma_tf32_ts(d, ahi, bh0 + s * kstep, idesc, 1u);
+    }
+  }
+}
+
+}  // namespace ts
+
+template <int K2, int D, int P, int MODE>
+__global__ void __launch_bounds__(256, 1) k_smooth_tsb(TsParams p) {
+  using B = ts::Big<K2, P>;
+  constexpr int C = K2 / 2;
+  constexpr int NT = 2 * D + 1;
+  constexpr int NH = B::NH, KU = B::KU, RB = B::RB, CPT = B::CPT;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t abar[2];        // A slot s free again (its MMAs done)
+  __shared__ uint64_t pbar;           // the MMAs of an epilogue phase done
+  __shared__ uint64_t fullb[RB];      // unit landed in ring buffer b
+  __shared__ uint64_t emptyb[RB];     // MMAs reading ring buffer b done
+  __shared__ uint32_t tmem_base_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lanei = tid & 31;
+  const int row = 32 * (warp & 3) + lanei;
+  const int grp = warp >> 2;          // owns chunks q with q % 2 == grp
+  const bool has_e = p.e_in != nullptr;
+  const int UPT = has_e ? (NT + 1) * NH + (MODE == 0 ? 2 * NH : 0) : 2 * NH;   // units per tile
+
+  if (tid == 0) {
+    tc::bar_init(&abar[0], 1);
+    tc::bar_init(&abar[1], 1);
+    tc::bar_init(&pbar, 1);
+    for (int b = 0; b < RB; ++b) {
+      tc::bar_init(&fullb[b], 1);
+      tc::bar_init(&emptyb[b], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     tc::smem_u32(&tmem_base_sh)),
+                 "r"((uint32_t)B::COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const uint32_t lane = (uint32_t)(32 * (warp & 3)) << 16;
+  const uint32_t tX = tmem, tY = tmem + K2;
+  const uint32_t slot0 = tmem + 2 * K2, slot1 = slot0 + B::AW;
+  const uint32_t ring_s = tc::smem_u32(smem);
+  uint32_t aph[2] = {0, 0}, pph = 0;
+  bool ok = true;
+  auto wait_a = [&](int s) {
+    ok = tc::bar_wait(&abar[s], aph[s], p.err) && ok;
+    aph[s] ^= 1;
+  };
+  auto wait_p = [&]() {
+    ok = tc::bar_wait(&pbar, pph, p.err) && ok;
+    pph ^= 1;
+  };
+  const long long nxny = (long long)p.nx * p.ny;
+  const int my_tiles = blockIdx.x < p.items ? (p.items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  // ---- the weight stream (thread 0): units in order, RB - 1 ahead
+  const int u_total = my_tiles * UPT;
+  int u_issued = 0, u_done = 0, ui_idx = 0;   // ui_idx: index of the next issue within its tile
+  auto unit_of = [&](int idx, int& m, int& h) {
+    if (!has_e) {
+      m = idx < NH ? NT + 1 : NT + 2;
+      h = idx < NH ? idx : idx - NH;
+      return;
+    }
+    if (idx < 2 * NH) {                 // tap 0 with K_A, per K-half
+      m = (idx & 1) ? NT : 0;
+      h = idx >> 1;
+      return;
+    }
+    const int r = idx - 2 * NH;
+    if (r < (NT - 1) * NH) {
+      m = 1 + r / NH;
+      h = r % NH;
+      return;
+    }
+    const int r2 = r - (NT - 1) * NH;
+    m = r2 < NH ? NT + 1 : NT + 2;
+    h = r2 < NH ? r2 : r2 - NH;
+  };
+  auto issue_unit = [&]() {            // thread 0
+    const int b = u_issued % RB;
+    if (u_issued >= RB) {              // the MMAs of unit u_issued - RB have read buffer b
+      ok = tc::bar_wait(&emptyb[b], (uint32_t)(((u_issued / RB) - 1) & 1), p.err) && ok;
+    }
+    int m, h;
+    unit_of(ui_idx, m, h);
+    const int gm = m == NT + 2 ? p.wi : m;
+    const uint8_t* src = reinterpret_cast<const uint8_t*>(p.mats) + (size_t)gm * B::MATB;
+    const uint32_t dst = ring_s + (uint32_t)(b * B::UNIT);
+    ts::expect_tx(&fullb[b], (uint32_t)B::UNIT);
+    if constexpr (P == 1) {
+      ts::bulk_copy(dst, src + (size_t)h * B::SUB, B::SUB, &fullb[b]);
+      ts::bulk_copy(dst + B::SUB, src + (size_t)K2 * K2 * 4 + (size_t)h * B::SUB, B::SUB, &fullb[b]);
+    } else {
+      ts::bulk_copy(dst, src + (size_t)h * B::SUB, B::SUB, &fullb[b]);
+    }
+    ++u_issued;
+    if (++ui_idx == UPT) ui_idx = 0;
+  };
+  auto top_up = [&]() {                // thread 0
+    while (ok && u_issued < u_total && u_issued < u_done + RB - 1) issue_unit();
+  };
+  // MMAs of the next unit (thread 0): A at a, target d
+  auto run_unit = [&](uint32_t d, uint32_t a, bool acc) {
+    const int b = u_done % RB;
+    ok = tc::bar_wait(&fullb[b], (uint32_t)((u_done / RB) & 1), p.err) && ok;
+    if (ok) {
+      tc::fence_after();
+      ts::gemm_unit<K2, P>(d, a, ring_s + (uint32_t)(b * B::UNIT), acc);
+      tc::mma_commit(&emptyb[b]);
+    }
+    ++u_done;
+    top_up();
+  };
+  if (tid == 0) top_up();
+
+  for (int k = 0; k < my_tiles; ++k) {
+    const int item = blockIdx.x + k * gridDim.x;
+    const int field = item / p.tiles;
+    const int tile = item - field * p.tiles;
+    const size_t off = (size_t)field * (size_t)p.nodes * C;
+    const float2* r = p.r + off;
+    const float2* ein = has_e ? p.e_in + off : nullptr;
+    float2* out = p.out + off;
+    const long long n = (long long)tile * ts::M + row;
+    const bool row_ok = n < p.nodes;
+    const long long nc = row_ok ? n : p.nodes - 1;
+    int x, y, z;
+    node_xyz(nc, p.nx, p.ny, x, y, z);
+    auto nbr = [&](int j, long long& nb) -> bool {
+      if (j == 0) { nb = nc; return row_ok; }
+      const int axis = (j - 1) >> 1;
+      const int sgn = (j & 1) ? -1 : 1;
+      const int c = axis == 0 ? x : (axis == 1 ? y : z);
+      const int ext = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
+      const long long stride = axis == 0 ? 1 : (axis == 1 ? p.nx : nxny);
+      nb = nc + sgn * stride;
+      return row_ok && c + sgn >= 0 && c + sgn < ext;
+    };
+    // this thread's chunks of stage (tap j, half h): columns h KU + 32 i + 16 grp
+    auto load_stage = [&](float (&v)[CPT * 16], int j, int h) {
+      long long nb;
+      const bool ok_n = nbr(j, nb);
+#pragma unroll
+      for (int i = 0; i < CPT; ++i) {
+        const int c0 = h * KU + 32 * i + 16 * grp;
+        const float4* q = reinterpret_cast<const float4*>(ein + nb * C + c0 / 2);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const float4 w = ok_n ? __ldg(q + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+          v[16 * i + 4 * t] = w.x;
+          v[16 * i + 4 * t + 1] = w.y;
+          v[16 * i + 4 * t + 2] = w.z;
+          v[16 * i + 4 * t + 3] = w.w;
+        }
+      }
+    };
+    // 16 columns at absolute column c of an epilogue operand -> its A slot
+    auto put_abs = [&](bool second, int c, const float* v) {
+      const int h = c / KU;
+      const uint32_t slot = NH == 2 ? (h ? slot1 : slot0) : (second ? slot1 : slot0);
+      if constexpr (P == 1) {
+        uint32_t hi[16], lo[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          hi[i] = tc::to_tf32(v[i]);
+          lo[i] = tc::to_tf32(v[i] - __uint_as_float(hi[i]));
+        }
+        tc::tmem_st16(slot + lane + (c - h * KU), hi);
+        tc::tmem_st16(slot + lane + KU + (c - h * KU), lo);
+      } else {
+        uint32_t pk[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) pk[i] = tc::pack_bf16(v[2 * i], v[2 * i + 1]);
+        tc::tmem_st8(slot + lane + (c - h * KU) / 2, pk);
+      }
+    };
+
+    if (has_e) {
+      // ---- phase 1: stages q = (tap j, half h)
+      constexpr int Q = NT * NH;
+      float va[CPT * 16], vb[CPT * 16];
+      load_stage(va, 0, 0);
+      load_stage(vb, (1 / NH), 1 % NH);
+#pragma unroll 1
+      for (int q = 0; q < Q; ++q) {
+        float(&cur)[CPT * 16] = (q & 1) ? vb : va;
+        const int j = q / NH, h = q % NH;
+        const uint32_t slot = (q & 1) ? slot1 : slot0;
+        if (q >= 2) wait_a(q & 1);                 // MMAs of stage q-2 have read this slot
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) ts::put16<KU, P>(slot + lane, 32 * i + 16 * grp, cur + 16 * i);
+        tc::tmem_st_wait();
+        if (q + 2 < Q) load_stage(cur, (q + 2) / NH, (q + 2) % NH);
+        tc::fence_before();
+        ok = __syncthreads_and(ok);
+        if (!ok) goto fail;
+        if (tid == 0) {
+          tc::fence_after();
+          run_unit(tX, slot, q > 0);
+          if (j == 0) run_unit(tY, slot, h > 0);
+          tc::mma_commit(&abar[q & 1]);
+        }
+      }
+      wait_a(Q >= 2 ? ((Q - 2) & 1) : 0);
+      wait_a((Q - 1) & 1);
+      tc::fence_after();
+      // ---- epilogue 1: t = r - X - a (.) Y
+#pragma unroll
+      for (int i = 0; i < K2 / 32; ++i) {
+        const int c0 = 32 * i + 16 * grp;
+        float xv[16], yv[16], rv[16], av[16], t[16];
+        tc::tmem_ld16(tX + lane + c0, xv);
+        tc::tmem_ld16(tY + lane + c0, yv);
+        ts::load16(rv, r, C, nc, c0);
+        ts::load16(av, p.a, C, nc, c0);
+#pragma unroll
+        for (int qq = 0; qq < 8; ++qq) {
+          t[2 * qq] = rv[2 * qq] - xv[2 * qq] - (av[2 * qq] * yv[2 * qq] - av[2 * qq + 1] * yv[2 * qq + 1]);
+          t[2 * qq + 1] = rv[2 * qq + 1] - xv[2 * qq + 1] -
+                          (av[2 * qq] * yv[2 * qq + 1] + av[2 * qq + 1] * yv[2 * qq]);
+        }
+        if constexpr (MODE == 1) {
+          if (row_ok) ts::store16(out, C, n, c0, t);
+        } else {
+          if (!row_ok) {
+#pragma unroll
+            for (int qq = 0; qq < 16; ++qq) t[qq] = 0.f;
+          }
+          put_abs(false, c0, t);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < K2 / 32; ++i) {
+        const int c0 = 32 * i + 16 * grp;
+        float rv[16];
+        ts::load16(rv, r, C, nc, c0);
+        if (!row_ok) {
+#pragma unroll
+          for (int qq = 0; qq < 16; ++qq) rv[qq] = 0.f;
+        }
+        put_abs(false, c0, rv);
+      }
+    }
+
+    if constexpr (MODE == 0) {
+      // ---- phase 2: Z = T K~_S^T; epilogue 2: z = s (.) Z
+      tc::tmem_st_wait();
+      tc::fence_before();
+      ok = __syncthreads_and(ok);
+      if (!ok) goto fail;
+      if (tid == 0) {
+        tc::fence_after();
+        for (int h = 0; h < NH; ++h) run_unit(tX, (NH == 2 && h) ? slot1 : slot0, h > 0);
+        tc::mma_commit(&pbar);
+      }
+      wait_p();
+      tc::fence_after();
+#pragma unroll
+      for (int i = 0; i < K2 / 32; ++i) {
+        const int c0 = 32 * i + 16 * grp;
+        float zv[16], sv[16], zz[16];
+        tc::tmem_ld16(tX + lane + c0, zv);
+        ts::load16(sv, p.s, C, nc, c0);
+#pragma unroll
+        for (int qq = 0; qq < 8; ++qq) {
+          zz[2 * qq] = sv[2 * qq] * zv[2 * qq] - sv[2 * qq + 1] * zv[2 * qq + 1];
+          zz[2 * qq + 1] = sv[2 * qq] * zv[2 * qq + 1] + sv[2 * qq + 1] * zv[2 * qq];
+        }
+        if (!row_ok) {
+#pragma unroll
+          for (int qq = 0; qq < 16; ++qq) zz[qq] = 0.f;
+        }
+        put_abs(true, c0, zz);
+      }
+      // ---- phase 3: U = Z W~_i^T; epilogue 3: e' = e + U
+      tc::tmem_st_wait();
+      tc::fence_before();
+      ok = __syncthreads_and(ok);
+      if (!ok) goto fail;
+      if (tid == 0) {
+        tc::fence_after();
+        for (int h = 0; h < NH; ++h) run_unit(tY, NH == 2 ? (h ? slot1 : slot0) : slot1, h > 0);
+        tc::mma_commit(&pbar);
+      }
+      wait_p();
+      tc::fence_after();
+#pragma unroll
+      for (int i = 0; i < K2 / 32; ++i) {
+        const int c0 = 32 * i + 16 * grp;
+        float uv[16];
+        tc::tmem_ld16(tY + lane + c0, uv);
+        if (has_e) {
+          float ev[16];
+          ts::load16(ev, ein, C, nc, c0);
+#pragma unroll
+          for (int qq = 0; qq < 16; ++qq) uv[qq] += ev[qq];
+        }
+        if (row_ok) ts::store16(out, C, n, c0, uv);
+      }
+    }
+    tc::fence_before();
+  }
+  ok = __syncthreads_and(ok);
+  if (!ok) goto fail;
+  if (warp == 0) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"((uint32_t)B::COLS));
+  }
+  return;
+
+fail:
+  // a bounded wait ran out: record it; thread 0 lets its weight copies land
+  // and its MMAs finish (bounded), then the tensor memory is released
+  if (p.err && tid == 0) atomicOr(p.err, 1);
+  if (tid == 0) {
+    for (int u = u_done; u < u_issued; ++u)
+      tc::bar_wait(&fullb[u % RB], (uint32_t)((u / RB) & 1), nullptr);
+    if (u_done > 0)
+      tc::bar_wait(&emptyb[(u_done - 1) % RB], (uint32_t)(((u_done - 1) / RB) & 1), nullptr);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"((uint32_t)B::COLS));
+  }
+}
+
 namespace {
 
 int sm_count() {
@@ -814,6 +1218,25 @@ mcmg_status tsr_launch(TsParams p, int nrhs, cudaStream_t st) {
 }
 
 template <int K2, int D, int P, int MODE>
+mcmg_status tsb_launch(TsParams p, int nrhs, cudaStream_t st) {
+  using B = ts::Big<K2, P>;
+  auto kern = k_smooth_tsb<K2, D, P, MODE>;
+  static bool attr = false;
+  const size_t smem = (size_t)B::RB * B::UNIT;
+  if (!attr) {
+    MCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    attr = true;
+  }
+  p.tiles = (int)((p.nodes + ts::M - 1) / ts::M);
+  p.items = p.tiles * nrhs;
+  const int grid = std::min(p.items, sm_count());
+  kern<<<grid, B::THREADS, smem, st>>>(p);
+  MCMG_CHECK_LAUNCH("smooth_tsb");
+  return MCMG_OK;
+}
+
+template <int K2, int D, int P, int MODE>
 mcmg_status ts_launch(TsParams p, int nrhs, cudaStream_t st) {
   using G = ts::Cfg<K2, P>;
   constexpr int NT = 2 * D + 1;
@@ -852,7 +1275,8 @@ mcmg_status ts_dispatch(int C, const TsParams& p, int nrhs, cudaStream_t st) {
       else return ts_launch<32, D, P, MODE>(p, nrhs, st);
     case 32:
       if constexpr (P == 0) return ts_launch<64, D, P, MODE>(p, nrhs, st);
-      break;
+      else return tsb_launch<64, D, P, MODE>(p, nrhs, st);
+    case 64: return tsb_launch<128, D, P, MODE>(p, nrhs, st);
     default: break;
   }
   set_error("tensor-core step: no variant for C = %d", C);
@@ -862,8 +1286,7 @@ mcmg_status ts_dispatch(int C, const TsParams& p, int nrhs, cudaStream_t st) {
 }  // namespace
 
 bool ts_supported(int C, int prec) {
-  if (prec == MCMG_BF16) return C == 8 || C == 16 || C == 32;
-  if (prec == MCMG_FP32_TC) return C == 8 || C == 16;
+  if (prec == MCMG_BF16 || prec == MCMG_FP32_TC) return C == 8 || C == 16 || C == 32 || C == 64;
   return false;
 }
 

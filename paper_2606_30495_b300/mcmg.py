@@ -90,6 +90,7 @@ _SIGS = {
     "mcmg_kernel_shape_count": [C.c_int],
     "mcmg_get_kernel_shape": [_P, C.c_int, C.c_int, C.POINTER(C.c_int)],
     "mcmg_set_kernel_shape": [_P, C.c_int, C.c_int, C.c_int],
+    "mcmg_fp32_ffma_tflops": [_P, C.POINTER(C.c_double)],
     "mcmg_kernel_launches": [],
     "mcmg_last_error": [],
     "mcmg_version": [],
@@ -202,6 +203,13 @@ def pack_weights(w: dict):
 
 
 # ---------------------------------------------------------------- objects ---
+
+def fp32_ffma_tflops(stream=None) -> float:
+    """Measured FP32 FFMA rate of the current device (TFLOP/s)."""
+    v = C.c_double()
+    _check(load().mcmg_fp32_ffma_tflops(_stream(stream), C.byref(v)))
+    return v.value
+
 
 def cgs2_noalloc(V, w, stream=None):
     """mcmg_cgs2_noalloc: CGS2 of w against the rows of V with no device

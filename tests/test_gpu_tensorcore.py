@@ -9,7 +9,9 @@ FP64 oracle.
 * BF16 mixing: 1e-2 per step, 2e-2 per V-cycle (the BF16 bound).
 
 The large cases have more 128-node tiles than the grid has CTAs, so every
-CTA walks several tiles, and node counts that are not a multiple of 128.
+CTA walks several tiles, and node counts that are not a multiple of 128; the
+C = 32 / 64 cases run the variant that streams its weights through shared
+memory (one CTA per SM).
 Every bounded wait inside the kernels must have finished (error word 0).
 """
 import numpy as np
@@ -65,8 +67,13 @@ CASES = [
     ("fp32tc", (34, 30), [8, 16], "structured"),
     ("fp32tc", (6, 8, 10), [8, 16], "random"),
     ("fp32tc", (10, 6, 14), [16, 16], "random"),
+    ("fp32tc", (16, 12), [32, 64], "random"),
+    ("fp32tc", (4, 6, 8), [64, 64], "random"),
+    ("fp32tc", (8, 6, 10), [32, 32], "structured"),
     ("bf16", (22, 18), [8, 32], "random"),
     ("bf16", (6, 10, 14), [32, 32], "random"),
+    ("bf16", (16, 12), [64, 64], "random"),
+    ("bf16", (4, 6, 8), [64, 64], "random"),
 ]
 IDS = [f"{p}-{'x'.join(map(str, s))}-C{'-'.join(map(str, c))}-{m}" for p, s, c, m in CASES]
 
@@ -140,6 +147,9 @@ def test_vcycle(case):
     ("fp32tc", (254, 162), [16, 16]),       # 322 tiles over 2 CTAs per SM
     ("fp32tc", (60, 66, 42), [8, 8]),       # 1300 tiles over 4 CTAs per SM, ragged
     ("bf16", (60, 66, 42), [8, 8]),         # 1300 tiles over 8 CTAs per SM, ragged
+    ("fp32tc", (160, 130), [64, 64]),       # 163 tiles over one CTA per SM, ragged
+    ("fp32tc", (34, 32, 30), [32, 32]),     # 255 tiles over one CTA per SM, ragged
+    ("bf16", (160, 130), [64, 64]),
 ])
 def test_persistent_multi_tile(ctx, prec, shape, channels):
     """More tiles than CTAs: each persistent CTA walks several tiles."""
