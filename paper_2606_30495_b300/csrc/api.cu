@@ -435,33 +435,30 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
         (s = dev_alloc(h, h->arena, (void**)&lv.s, sizeof(float2) * lv.g.nodes() * C)))
       return cleanup(), s;
     lv.err = h->err_dev;
-    if (w->precision == MCMG_BF16 && tc_supported(C)) {
-      // BF16 tiles: taps, K_A, K_S, W^(i)
+    if (w->precision == MCMG_BF16 && ts_supported(C, MCMG_BF16)) {
+      // BF16 block forms of every matrix: taps, K_A, K_S, W^(i)
       const int K2 = 2 * C;
-      const size_t tile = (size_t)K2 * K2;          // bf16 elements per tile
+      const size_t tile = (size_t)K2 * K2;          // bf16 elements per matrix
       const int ntile = T + 2 + ns;
       std::vector<uint16_t> host(tile * ntile);
       std::vector<float2> mat((size_t)C * C);
       auto put = [&](const double* src, int t) {
         for (size_t i = 0; i < (size_t)C * C; ++i)
           mat[i] = make_float2((float)src[2 * i], (float)src[2 * i + 1]);
-        pack_tc_tile(mat.data(), C, host.data() + tile * t);
+        pack_ts_bf16(mat.data(), C, host.data() + tile * t);
       };
       for (int t = 0; t < T; ++t) put(lb[l].W + (size_t)2 * t * C * C, t);
       put(lb[l].KA, T);
       put(lb[l].KS, T + 1);
       for (int i = 0; i < ns; ++i) put(lb[l].Ws + (size_t)2 * i * C * C, T + 2 + i);
-      if ((s = dev_alloc(h, h->arena, (void**)&lv.tcw.tiles, host.size() * sizeof(uint16_t))))
+      uint4* dst = nullptr;
+      if ((s = dev_alloc(h, h->arena, (void**)&dst, host.size() * sizeof(uint16_t))))
         return cleanup(), s;
-      MCMG_CUDA(cudaMemcpy(lv.tcw.tiles, host.data(), host.size() * sizeof(uint16_t),
+      MCMG_CUDA(cudaMemcpy(dst, host.data(), host.size() * sizeof(uint16_t),
                            cudaMemcpyHostToDevice));
-      if (ts_supported(C, MCMG_BF16)) {      // TMEM-operand kernels, same tile layout
-        lv.use_ts = true;
-        lv.ts_prec = MCMG_BF16;
-        lv.ts_mats = lv.tcw.tiles;
-      } else {
-        lv.use_tc = true;
-      }
+      lv.use_ts = true;
+      lv.ts_prec = MCMG_BF16;
+      lv.ts_mats = dst;
     }
     if (w->precision == MCMG_FP32_TC && ts_supported(C, MCMG_FP32_TC)) {
       // TF32 hi / lo halves of every matrix: taps, K_A, K_S, W^(i)

@@ -1319,6 +1319,24 @@ mcmg_status launch_smooth_ts(const Level& L, int step, const float2* r, const fl
   return d3 ? ts_dispatch<3, 0, 1>(L.C, p, nrhs, st) : ts_dispatch<2, 0, 1>(L.C, p, nrhs, st);
 }
 
+// Host: a complex C x C matrix M[co][ci] (float2, row-major) -> its real
+// 2C x 2C block form as BF16 in the no-swizzle K-major core-matrix layout of
+// a B operand (row n = output index, K = input index, 16-byte chunks of 8
+// elements, chunk-major).
+void pack_ts_bf16(const float2* Mc, int C, uint16_t* out) {
+  const int K2 = 2 * C;
+  for (int n = 0; n < K2; ++n)
+    for (int k = 0; k < K2; ++k) {
+      const float2 m = Mc[(size_t)(n >> 1) * C + (k >> 1)];
+      float v;
+      if ((n & 1) == 0) v = (k & 1) == 0 ? m.x : -m.y;   // re out: Mr re_in - Mi im_in
+      else v = (k & 1) == 0 ? m.y : m.x;                 // im out: Mi re_in + Mr im_in
+      __nv_bfloat16 b = __float2bfloat16_rn(v);
+      const size_t pos = ((size_t)(k >> 3) * K2 + n) * 8 + (k & 7);
+      std::memcpy(out + pos, &b, 2);
+    }
+}
+
 // Host: FP32 -> TF32 bit pattern, round to nearest, ties away from zero
 // (the same rounding as the device's cvt.rna.tf32.f32 on finite values).
 static float host_tf32(float v) {

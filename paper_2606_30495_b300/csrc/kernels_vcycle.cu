@@ -598,8 +598,6 @@ mcmg_status launch_smooth(const Level& L, int step, const float2* r, const float
                           float2* e_out, int mode, int nrhs, cudaStream_t st) {
   if (L.use_ts && (mode == 0 || e_in))
     return launch_smooth_ts(L, step, r, e_in, e_out, mode, nrhs, st);
-  if (mode == 0 && L.use_tc)
-    return launch_smooth_tc(L, L.tcw, step, r, e_in, e_out, nrhs, L.err, st);
   const SmoothParams p = smooth_params(L, step, r, e_in, e_out, mode);
   int shape = L.shape[mode];
   if (shape < 0 || !shape_ok(shape, L.C, L.g.d)) shape = pick_shape(p.nodes, L.C, nrhs);
@@ -618,7 +616,7 @@ mcmg_status autotune_smooth(Level& L, float2* r, float2* e, float2* out, cudaStr
   MCMG_CUDA(cudaEventCreate(&e1));
   mcmg_status status = MCMG_OK;
   for (int mode = 0; mode < 2 && status == MCMG_OK; ++mode) {
-    if ((mode == 0 && L.use_tc) || L.use_ts) continue;
+    if (L.use_ts) continue;
     const SmoothParams p = smooth_params(L, 0, r, e, out, mode);
     float best_ms[kNumShapes];
     for (int s = 0; s < kNumShapes; ++s) best_ms[s] = 1e30f;

@@ -69,13 +69,6 @@ struct Grid {
   __host__ __device__ Grid coarse() const { return Grid{d, nx / 2, ny / 2, d == 3 ? nz / 2 : 1}; }
 };
 
-// BF16 weight tiles of one level for the tensor-core smoothing step: the real
-// 2C x 2C block form of every mixing matrix, in the shared-memory core-matrix
-// layout, stored [stencil taps][K_A][K_S][W^(i) per step].
-struct TcWeights {
-  uint4* tiles = nullptr;
-};
-
 // Read-only per-level state: features and weights.  Mixing matrices are
 // stored transposed, M^T[ci][co], so consecutive output channels are
 // contiguous.
@@ -91,7 +84,6 @@ struct Level {
   float2* Wsmt = nullptr;     // [nsteps][C][C]
   float2* Rt = nullptr;       // [T3][C][Cn]
   float2* Pt = nullptr;       // [T3][Cn][C]
-  bool use_tc = false;        // smoothing step on tcgen05 (BF16 mixing), SMEM operands
   bool use_ts = false;        // smoothing step and residual on tcgen05, TMEM A operands
   int ts_prec = -1;           // MCMG_BF16 or MCMG_FP32_TC when use_ts
   const uint4* ts_mats = nullptr;  // weight matrices in the operand layout of ts_prec
@@ -99,23 +91,17 @@ struct Level {
   // 2 restriction, 3 prolongation) and the autotuner's choice
   int shape[4] = {-1, -1, -1, -1};
   int tuned[4] = {-1, -1, -1, -1};
-  TcWeights tcw;
   int* err = nullptr;         // device view of the handle's error word
 };
-
-// tensor-core smoothing (kernels_tc.cu)
-bool tc_supported(int C);
-mcmg_status launch_smooth_tc(const Level& L, const TcWeights& W, int step, const float2* r,
-                             const float2* e_in, float2* e_out, int nrhs, int* err,
-                             cudaStream_t st);
-void pack_tc_tile(const float2* Mc, int C, uint16_t* out);
 
 // tensor-core smoothing step and residual with A operands in tensor memory
 // (kernels_ts.cu); mode as launch_smooth
 bool ts_supported(int C, int prec);
 mcmg_status launch_smooth_ts(const Level& L, int step, const float2* r, const float2* e_in,
                              float2* out, int mode, int nrhs, cudaStream_t st);
-// complex C x C matrix -> TF32 hi and lo halves of its real block form (2 * 4C^2 floats)
+// complex C x C matrix -> its real 2C x 2C block form as a B operand: BF16
+// (4C^2 values), or TF32 hi and lo halves (2 * 4C^2 floats)
+void pack_ts_bf16(const float2* Mc, int C, uint16_t* out);
 void pack_ts_tf32(const float2* Mc, int C, float* out);
 
 // Launchers used by the V-cycle (kernels_vcycle.cu), asynchronous on `st`.

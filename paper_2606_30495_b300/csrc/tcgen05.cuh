@@ -1,6 +1,6 @@
 // Inline-PTX wrappers for the 5th-generation tensor cores (tcgen05), the
 // shared-memory matrix descriptors and the bounded mbarrier waits, shared by
-// the tensor-core smoothing kernels (kernels_tc.cu, kernels_ts.cu).
+// the tensor-core smoothing kernels (kernels_ts.cu).
 #pragma once
 #include <cuda_bf16.h>
 #include <cstdint>
