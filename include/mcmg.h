@@ -130,7 +130,11 @@ typedef struct {
   int nrhs;          /* right-hand sides solved together (independent systems)*/
   int flags;         /* MCMG_SOLVE_* bits                                     */
   void* stream;      /* cudaStream_t the solve runs on (NULL = the handle's
-                        own stream); the call still returns only when done   */
+                        own stream); the call still returns only when done.
+                        The solve reads f and u only after all work enqueued
+                        on this stream (NULL: on the legacy default stream)
+                        before the call; mcmg_submit marks that point at
+                        submission and the server orders the request after it */
 } mcmg_solve_opts;
 
 #define MCMG_SOLVE_STATIONARY 1  /* u <- u + MG(f - A u) instead of FGMRES

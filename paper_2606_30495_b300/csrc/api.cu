@@ -25,6 +25,10 @@ struct Request {
   mcmg_status status = MCMG_PENDING;
   mcmg_solve_info info{};
   std::string err;                   // message of a failure on the server thread
+  cudaEvent_t ready = nullptr;       // recorded on the caller's stream at submit
+  ~Request() {
+    if (ready) cudaEventDestroy(ready);
+  }
 };
 
 struct mcmg_ctx_s {
@@ -643,6 +647,20 @@ static mcmg_status check_opts(const mcmg_solve_opts* o) {
   return MCMG_OK;
 }
 
+// Order `work` after everything enqueued so far on the caller's stream
+// (NULL: the legacy default stream), so that f and u written there before the
+// call are what the solve reads.
+static mcmg_status order_after(cudaStream_t caller, cudaStream_t work) {
+  if (caller == work) return MCMG_OK;
+  cudaEvent_t ev;
+  MCMG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ev, caller);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(work, ev, 0);
+  cudaEventDestroy(ev);
+  if (e != cudaSuccess) return cuda_fail(e, "order after the caller's stream");
+  return MCMG_OK;
+}
+
 mcmg_status mcmg_solve(mcmg_handle h, const void* f, void* u, const mcmg_solve_opts* o,
                        mcmg_solve_info* info) {
   if (!h || !f || !u) { set_error("NULL argument"); return MCMG_ERR_ARG; }
@@ -671,11 +689,13 @@ mcmg_status mcmg_solve(mcmg_handle h, const void* f, void* u, const mcmg_solve_o
       h->blk = nullptr;
     }
     if (!h->blk) MCMG_TRY(block_create(h, o->restart_m, o->nrhs, &h->blk));
+    MCMG_TRY(order_after((cudaStream_t)o->stream, block_stream(h->blk)));
     MCMG_TRY(block_begin(h->blk, (const double2*)f, (double2*)u, *o));
     int done = 0;
     while (!done) MCMG_TRY(block_advance(h->blk, true, &done));
     block_info(h->blk, &agg, &worst);
   } else {
+    if (!o->stream) MCMG_TRY(order_after(nullptr, h->stream));
     for (int k = 0; k < o->nrhs; ++k) {
       cudaStream_t st = o->stream ? (cudaStream_t)o->stream : h->stream;
       mcmg_solve_info one;
@@ -920,6 +940,17 @@ static bool try_admit(mcmg_ctx_s* c, Request* r) {
     cudaGetLastError();
     return false;
   }
+  // the request reads f and u only after the caller's work before the submit
+  if (r->ready) {
+    cudaError_t e = cudaStreamWaitEvent(block_stream(r->blk), r->ready, 0);
+    cudaEventDestroy(r->ready);
+    r->ready = nullptr;
+    if (e != cudaSuccess) {
+      r->status = cuda_fail(e, "wait for the caller's stream");
+      r->err = mcmg_last_error();
+      return true;
+    }
+  }
   s = block_begin(r->blk, r->f, r->u, r->o);
   if (s != MCMG_OK) {
     r->status = s;
@@ -1031,6 +1062,16 @@ mcmg_status mcmg_submit(mcmg_ctx c, mcmg_handle h, const void* f, void* u,
   r->f = (const double2*)f;
   r->u = (double2*)u;
   r->o = *o;
+  {
+    // mark the caller's stream now; the server orders the request after it
+    cudaError_t e = cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(r->ready, (cudaStream_t)o->stream);
+    if (e != cudaSuccess) {
+      if (r->ready) cudaEventDestroy(r->ready);
+      delete r;
+      return cuda_fail(e, "record the caller's stream");
+    }
+  }
   r->bytes_needed = request_bytes(h, *o);
   r->t_submit = std::chrono::steady_clock::now();
   {

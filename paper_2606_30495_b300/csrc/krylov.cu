@@ -805,6 +805,8 @@ struct KrylovBlock {
   double t_solve = 0.0;
 };
 
+cudaStream_t block_stream(const KrylovBlock* b) { return b->st; }
+
 int block_size(const KrylovBlock* b) { return b->nb; }
 int block_m(const KrylovBlock* b) { return b->m; }
 

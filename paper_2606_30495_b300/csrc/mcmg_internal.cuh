@@ -222,6 +222,7 @@ mcmg_status block_begin(KrylovBlock* b, const double2* f, double2* u, const mcmg
 mcmg_status block_advance(KrylovBlock* b, bool blocking, int* done);
 void block_info(const KrylovBlock* b, mcmg_solve_info* info, mcmg_status* final_status);
 int block_size(const KrylovBlock* b);
+cudaStream_t block_stream(const KrylovBlock* b);   // the block solve's private stream
 int block_m(const KrylovBlock* b);
 // CGS2 on caller buffers (used by mcmg_cgs2).
 mcmg_status cgs2_once(mcmg_handle_s* h, const float2* V, int k, long long n, float2* w,

@@ -245,8 +245,14 @@ class Context:
         _check(self.lib.mcmg_ctx_memory(self.h, C.byref(v)))
         return v.value
 
-    def submit(self, handle, f, u, tol=1e-6, restart_m=20, max_iters=0, nrhs=1, flags=0) -> int:
-        o = SolveOpts(tol, restart_m, max_iters, nrhs, flags)
+    def submit(self, handle, f, u, tol=1e-6, restart_m=20, max_iters=0, nrhs=1, flags=0,
+               stream=None) -> int:
+        """Queue a solve; it reads f and u after the work enqueued so far on
+        `stream` (default: torch's current stream), which wrote them."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        o = SolveOpts(tol, restart_m, max_iters, nrhs, flags, _stream(stream))
         t = C.c_uint64()
         _check(self.lib.mcmg_submit(self.h, handle.h, ptr(f), ptr(u), C.byref(o), C.byref(t)))
         return t.value

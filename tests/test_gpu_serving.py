@@ -112,3 +112,51 @@ def test_admission_under_a_small_budget_and_refusal():
         for h in hs:
             h.close()
         ctx.close()
+
+
+def test_solve_and_submit_read_inputs_after_the_callers_stream():
+    """f and u written on the caller's stream just before the call are what
+    the solve reads: u is first filled with NaN, then zeroed on torch's
+    current stream behind a GPU sleep of about 0.1 s, and the solve is
+    issued at once (a single solve, a batched solve and a server request).
+    Without the ordering the first residual would read the NaN."""
+    from paper_2606_30495_b300 import mcmg
+    ctx = mcmg.Context(0)
+    reqs = _requests()
+    req, c, om, w, f = reqs[0]                   # 64^2, two right-hand sides
+    h = mcmg.Handle(ctx, c, om, 16, 1.0, w, precision=mcmg.BF16)
+    try:
+        fd = torch.from_numpy(f).cuda()
+        ref = torch.zeros_like(fd)
+        st, info = h.solve(fd, ref, tol=1e-6, restart_m=30, max_iters=3000, nrhs=req["nrhs"])
+        assert st == 0 and info["converged"]
+        want = ref.cpu().numpy()
+
+        def poisoned():
+            u = torch.full_like(fd, float("nan"))
+            torch.cuda.synchronize()
+            torch.cuda._sleep(200_000_000)        # ~0.1 s of device time on this stream
+            u.zero_()
+            return u
+
+        u = poisoned()
+        st, info = h.solve(fd, u, tol=1e-6, restart_m=30, max_iters=3000, nrhs=req["nrhs"])
+        assert st == 0 and info["converged"], info
+        assert np.allclose(u.cpu().numpy(), want, rtol=0, atol=1e-12 * np.abs(want).max())
+        u1 = poisoned()[0].contiguous()
+        st, info = h.solve(fd[0].contiguous(), u1, tol=1e-6, restart_m=30, max_iters=3000)
+        assert st == 0 and info["converged"], info
+        assert np.all(np.isfinite(u1.cpu().numpy()))
+        u = poisoned()
+        t = ctx.submit(h, fd, u, tol=1e-6, restart_m=30, max_iters=3000, nrhs=req["nrhs"])
+        t0 = time.time()
+        while True:
+            st, info = ctx.poll(t)
+            if st != mcmg.MCMG_PENDING or time.time() - t0 > 60:
+                break
+            time.sleep(0.002)
+        assert st == 0 and info["converged"], (st, info)
+        assert np.allclose(u.cpu().numpy(), want, rtol=0, atol=1e-12 * np.abs(want).max())
+    finally:
+        h.close()
+        ctx.close()
