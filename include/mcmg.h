@@ -268,6 +268,17 @@ mcmg_status mcmg_residual_restrict(mcmg_handle h, int level, const void* r_dev,
 mcmg_status mcmg_prolong_add(mcmg_handle h, int level, const void* e_coarse_dev,
                              void* e_dev, int nrhs, void* stream);
 
+/* The background Green operator of the Born-series variant (Appendix, the
+ * discrete Green operator; Eq. discrete_symbol), in place:
+ *   x <- IDFT( DFT(x) / (sum_a 4 sin^2(pi m_a / N_a) - q0) ),
+ * the discrete Laplacian's symbol on periodic modes, q0 = (k0 h)^2 with
+ * Re q0 halfway between the extremes of Re q and Im q0 = -max|q - Re q0|.
+ * x: dev c128 [nodes_0] (grid order, x fastest).  The DFT is this library's
+ * own FFT, so every axis must be a power of two of at most 4096 cells
+ * (else MCMG_ERR_SHAPE).  Enqueued on `stream`; the first call on a handle
+ * prepares the symbols (synchronous).                                        */
+mcmg_status mcmg_apply_G(mcmg_handle h, void* x_dev, void* stream);
+
 /* Raw coarse-basis response (Eq. coarse_basis, Section 3.4):
  *   Psi = g_proj(P_1 P_2 ... P_level (delta_alpha)),
  * delta_alpha the one-hot latent field at node `node` (linear index on that

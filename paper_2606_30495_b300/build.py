@@ -18,7 +18,6 @@ LIB = os.path.join(HERE, "libmcmg.so")
 BUILD_DIR = os.path.join(os.path.dirname(HERE), "_build")
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-CUDA_LIB = os.path.join(os.path.dirname(os.path.dirname(NVCC)), "lib64")   # cuFFT at run time
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE]
@@ -83,8 +82,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
     tmp = LIB + ".tmp"
-    cmd = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lcufft",
-           "-Xlinker", "-rpath", "-Xlinker", CUDA_LIB, "-lpthread", "-ldl", "-lrt"]
+    cmd = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs,
+           "-lpthread", "-ldl", "-lrt"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)

@@ -255,16 +255,17 @@ struct mcmg_handle_s {
   int* err_host = nullptr;      // error word, mapped pinned (bounded waits that ran out)
   int* err_dev = nullptr;
   unsigned shape_gen = 0;       // bumped when a smoothing shape is overridden
-  // Born-series variant (born.cu): FFT plan, per-axis Laplacian symbols, q0
+  // Born-series variant (born.cu): per-axis Laplacian symbols and FFT
+  // twiddles, q0
   bool born_ready = false;
-  int born_plan = 0;
   double* born_sym[3] = {};
+  double2* born_tw[3] = {};
   double born_q0r = 0.0, born_q0i = 0.0;
 };
 
 namespace mcmg {
-// Green operator of the Born-series variant (born.cu): plan, symbols and q0
-// once per handle; x <- G x in place (x: c128 [nodes_0]) on st.
+// Green operator of the Born-series variant (born.cu): symbols, twiddles and
+// q0 once per handle; x <- G x in place (x: c128 [nodes_0]) on st.
 mcmg_status born_prepare(mcmg_handle_s* h);
 mcmg_status born_apply_G(mcmg_handle_s* h, double2* x, cudaStream_t st);
 void born_release(mcmg_handle_s* h);

@@ -84,6 +84,7 @@ _SIGS = {
     "mcmg_residual_restrict": [_P, C.c_int, _P, _P, _P, C.c_int, _P],
     "mcmg_prolong_add": [_P, C.c_int, _P, _P, C.c_int, _P],
     "mcmg_coarse_basis": [_P, C.c_int, C.c_longlong, C.c_int, _P, _P],
+    "mcmg_apply_G": [_P, _P, _P],
     "mcmg_cgs2": [_P, _P, C.c_int, C.c_size_t, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "mcmg_cgs2_noalloc": [_P, C.c_int, C.c_size_t, _P, C.POINTER(C.c_double),
                           C.POINTER(C.c_double), _P],
@@ -366,6 +367,10 @@ class Handle:
 
     def prolong_add(self, level, ec, e, nrhs=1, stream=None):
         _check(self.lib.mcmg_prolong_add(self.h, level, ptr(ec), ptr(e), nrhs, _stream(stream)))
+
+    def apply_G(self, x, stream=None):
+        """x <- G x in place (the Born-series Green operator; x complex128)."""
+        _check(self.lib.mcmg_apply_G(self.h, ptr(x), _stream(stream)))
 
     def coarse_basis(self, level, node, channel, out, stream=None):
         """Raw coarse-basis response of (level, node, channel) into `out`
