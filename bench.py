@@ -395,10 +395,11 @@ def run_serving(args):
     """Serving stream: requests with their own media and 1-8 point sources.
 
     Plain form: every right-hand side solved one after another with mcmg_solve
-    (one right-hand side per call, no batching) on FP32 handles.  Served form: BF16 handles set up at each request's
-    arrival and submitted to the context's server (admission against the HBM
-    budget, every solve on its own stream, stages of all admitted solves
-    overlapping).  Arrivals are Poisson at 1.5x the plain form's request rate.
+    (one right-hand side per call, no batching) on FP32 handles.  Served form:
+    BF16 handles set up at each request's arrival and submitted to the
+    context's server (admission against the HBM budget, every request on its
+    own stream, the V-cycles due in the same round batched across requests
+    into one tensor-core launch per level and step).  Arrivals are Poisson at 1.5x the plain form's request rate.
     Reports solves/s (right-hand sides per second of makespan), p50/p99 request
     latency (completion - arrival, setup included) and the speedup."""
     import numpy as np
@@ -466,6 +467,7 @@ def run_serving(args):
         time.sleep(0.0005)
     makespan = max(v[0] for v in done.values())
     launches = mcmg.kernel_launches() - launches0
+    cohort_rounds, cohort_members = ctx.batching()
     lat = sorted(done[k][0] - t_arr[k] for k in range(len(reqs)))
     conv = all(done[k][1] == 0 for k in range(len(reqs)))
     served_rate = nrhs_total / makespan
@@ -498,6 +500,8 @@ def run_serving(args):
         "served_status": [mcmg.STATUS.get(done[k][1], done[k][1]) for k in range(len(reqs))],
         "served_device_error": dev_err,
         "converged": conv, "worst_true_rel_residual": worst, "gpu_launches": int(launches),
+        "cross_request_batching": {"cohort_vcycles": cohort_rounds,
+                                   "requests_in_cohorts": cohort_members},
     }
     print(json.dumps(out))
 

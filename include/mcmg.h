@@ -216,6 +216,16 @@ mcmg_status mcmg_solve_host(mcmg_handle h, const void* f_host_c128, void* u_host
  * Returns MCMG_ERR_BUSY when the queue is full.  Thread-safe.                */
 mcmg_status mcmg_submit(mcmg_ctx ctx, mcmg_handle h, const void* f_dev_c128,
                         void* u_dev_c128, const mcmg_solve_opts* opts, uint64_t* ticket);
+/* Cross-request batching of the server (not in the paper; serving): with it
+ * on (the default), the requests whose V-cycles are due in the same round and
+ * whose handles share weights and level layout run those V-cycles as one
+ * cohort, every smoothing step and residual of a level one tensor-core launch
+ * over all their fields (each field with its own grid and medium); results
+ * are the same as alone.  enable: 1 on, 0 off, -1 unchanged.  rounds /
+ * members (may be NULL): cohort V-cycles run so far and the requests they
+ * held, summed.  Thread-safe.                                               */
+mcmg_status mcmg_server_batching(mcmg_ctx ctx, int enable, uint64_t* rounds, uint64_t* members);
+
 /* MCMG_PENDING until the request finished; then its final status, with info
  * filled.  A finished ticket is forgotten after the first non-pending poll.  */
 mcmg_status mcmg_poll(mcmg_ctx ctx, uint64_t ticket, mcmg_solve_info* info);

@@ -46,6 +46,15 @@ struct mcmg_ctx_s {
   bool stop = false;
   bool running = false;
   size_t max_queue = 4096;
+  // cross-request batching (server thread): its stream, and the descriptors
+  // of batched launches, staged in pinned memory and uploaded once per round
+  cudaStream_t sst = nullptr;
+  mcmg::TsField* fd_h = nullptr;
+  mcmg::TsField* fd_d = nullptr;
+  int fd_cap = 0;
+  cudaEvent_t fd_ev = nullptr;       // the last upload has been read
+  unsigned long long cohort_rounds = 0, cohort_members = 0;   // for reporting
+  bool batching = true;              // cross-request batching of V-cycles
 };
 
 namespace mcmg {
@@ -350,6 +359,9 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
   h->g0 = g0;
   h->L = L;
   h->precision = w->precision;
+  // batching key (coarse; every batched launch also checks the level
+  // signatures below)
+  h->wsig = ((uint64_t)w->precision << 8) | (uint64_t)d;
   // shapes
   Grid g = g0;
   for (int l = 0; l < L; ++l) {
@@ -424,6 +436,22 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
   for (int l = 0; l < L; ++l) {
     Level& lv = h->lv[l];
     const int C = lv.C, ns = lv.nu_pre + lv.nu_post;
+    {
+      auto fnv = [](uint64_t x, const void* data, size_t bytes) {
+        const unsigned char* b = (const unsigned char*)data;
+        for (size_t i = 0; i < bytes; ++i) x = (x ^ b[i]) * 1099511628211ull;
+        return x;
+      };
+      uint64_t base = 1469598103934665603ull;
+      base = fnv(base, &w->precision, sizeof(int));
+      base = fnv(base, &C, sizeof(int));
+      base = fnv(base, lb[l].W, sizeof(double) * 2 * T * C * C);
+      base = fnv(base, lb[l].KA, sizeof(double) * 2 * C * C);
+      lv.rsig = base;
+      base = fnv(base, lb[l].KS, sizeof(double) * 2 * C * C);
+      for (int i = 0; i < ns && i < 2 * 8 + 1; ++i)
+        lv.ssig[i] = fnv(base, lb[l].Ws + (size_t)2 * i * C * C, sizeof(double) * 2 * C * C);
+    }
     if ((s = upload(h, h->arena, transpose_blocks(lb[l].W, T, C, C), &lv.Wt)) ||
         (s = upload(h, h->arena, transpose_blocks(lb[l].KA, 1, C, C), &lv.KAt)) ||
         (s = upload(h, h->arena, transpose_blocks(lb[l].KS, 1, C, C), &lv.KSt)) ||
@@ -959,6 +987,259 @@ static bool try_admit(mcmg_ctx_s* c, Request* r) {
   return true;
 }
 
+// ---- cross-request batching --------------------------------------------
+// One V-cycle (Algorithm 2) for the pending right-hand sides of several
+// requests whose handles share weights and level layout (wsig), each with its
+// own medium (features) and grid.  Per level, every smoothing step and the
+// residual of all members is one tensor-core launch over all their fields
+// (field descriptors: pointers, features, grid); lift, restriction,
+// prolongation and projection run per member.  Every field goes through the
+// same arithmetic as in a V-cycle of its own, so results are unchanged by the
+// company a request keeps.  The launches run on the server's stream, ordered
+// after each member's stream and back.
+struct CohortMember {
+  mcmg_handle_s* h;
+  VWork* w;
+  const float2* const* srcs;
+  float2* const* dsts;
+  int count;
+  cudaStream_t st;
+  float2* ecur[MCMG_MAX_LEVELS];
+};
+
+namespace {
+
+struct CohortOp {
+  enum Kind { TS, SMOOTH, RESTRICT, PROLONG, MEMSET } kind;
+  int member = -1, level = 0, step = 0, mode = 0;
+  int f0 = 0, nf = 0;                 // TS: descriptors [f0, f0 + nf)
+  bool has_e = false;
+  const float2* r = nullptr;          // SMOOTH (one member, CUDA cores)
+  const float2* e_in = nullptr;
+  float2* out = nullptr;
+};
+
+}  // namespace
+
+static mcmg_status cohort_vcycle(mcmg_ctx_s* c, std::vector<CohortMember>& ms, bool* planned) {
+  *planned = false;
+  // ---- plan: the level sequence of every member, batched per level
+  std::vector<CohortOp> ops;
+  std::vector<TsField> fd;
+  int Lmax = 0;
+  for (auto& m : ms) Lmax = std::max(Lmax, m.h->L);
+  auto fields_of = [&](int l, const std::vector<int>& who, const float2* const* eins,
+                       float2* const* outs, bool use_t_out) {
+    // one descriptor per (member, right-hand side)
+    const int f0 = (int)fd.size();
+    int first = 0;
+    for (size_t q = 0; q < who.size(); ++q) {
+      const CohortMember& m = ms[who[q]];
+      const Level& lv = m.h->lv[l];
+      const long long nl = lv.g.nodes();
+      const size_t stride = (size_t)nl * lv.C;
+      for (int k = 0; k < m.count; ++k) {
+        TsField f{};
+        f.r = m.w->r[l] + k * stride;
+        f.e_in = eins[q] ? eins[q] + k * stride : nullptr;
+        f.out = (use_t_out ? m.w->t[l] : outs[q]) + k * stride;
+        f.a = lv.a;
+        f.s = lv.s;
+        f.nodes = nl;
+        f.nx = lv.g.nx;
+        f.ny = lv.g.ny;
+        f.nz = lv.g.nz;
+        f.tiles = (int)((nl + 127) / 128);
+        f.first = first;
+        first += f.tiles;
+        fd.push_back(f);
+      }
+    }
+    return std::make_pair(f0, (int)fd.size() - f0);
+  };
+  bool same = true;                   // every batched launch's arithmetic agrees
+  auto steps = [&](int l, const std::vector<int>& who, int step0, int nsteps, bool from_zero) {
+    const Level& L0 = ms[who[0]].h->lv[l];
+    for (int q : who)
+      for (int i = 0; i < nsteps; ++i)
+        if (step0 + i > 2 * 8 || ms[q].h->lv[l].ssig[step0 + i] != L0.ssig[step0 + i] ||
+            ms[q].h->lv[l].use_ts != L0.use_ts)
+          same = false;
+    for (int i = 0; i < nsteps; ++i) {
+      std::vector<const float2*> eins(who.size());
+      std::vector<float2*> outs(who.size());
+      for (size_t q = 0; q < who.size(); ++q) {
+        CohortMember& m = ms[who[q]];
+        float2* cur = (from_zero && i == 0) ? nullptr : m.ecur[l];
+        eins[q] = cur;
+        outs[q] = (cur == m.w->e[l]) ? m.w->e2[l] : m.w->e[l];
+      }
+      if (L0.use_ts) {
+        auto fr = fields_of(l, who, eins.data(), outs.data(), false);
+        CohortOp op{CohortOp::TS};
+        op.level = l;
+        op.step = step0 + i;
+        op.mode = 0;
+        op.f0 = fr.first;
+        op.nf = fr.second;
+        op.has_e = eins[0] != nullptr;
+        op.member = who[0];
+        ops.push_back(op);
+      } else {
+        for (size_t q = 0; q < who.size(); ++q) {
+          CohortOp op{CohortOp::SMOOTH};
+          op.member = who[q];
+          op.level = l;
+          op.step = step0 + i;
+          op.mode = 0;
+          op.r = ms[who[q]].w->r[l];
+          op.e_in = eins[q];
+          op.out = outs[q];
+          ops.push_back(op);
+        }
+      }
+      for (size_t q = 0; q < who.size(); ++q) ms[who[q]].ecur[l] = outs[q];
+    }
+  };
+  for (int l = 0; l < Lmax; ++l) {                   // down cycle
+    std::vector<int> who, res;
+    for (int q = 0; q < (int)ms.size(); ++q)
+      if (ms[q].h->L > l) who.push_back(q);
+    const int nu = ms[who[0]].h->lv[l].nu_pre;
+    for (int q : who)
+      if (ms[q].h->lv[l].nu_pre != nu) return MCMG_OK;   // not batchable: caller runs them apart
+    if (nu > 0) {
+      steps(l, who, 0, nu, true);
+    } else {
+      for (int q : who) {
+        CohortOp op{CohortOp::MEMSET};
+        op.member = q;
+        op.level = l;
+        ops.push_back(op);
+        ms[q].ecur[l] = ms[q].w->e[l];
+      }
+    }
+    for (int q : who)
+      if (l < ms[q].h->L - 1) res.push_back(q);
+    if (!res.empty()) {
+      const Level& L0 = ms[res[0]].h->lv[l];
+      for (int q : res)
+        if (ms[q].h->lv[l].rsig != L0.rsig || ms[q].h->lv[l].use_ts != L0.use_ts) same = false;
+      std::vector<const float2*> eins(res.size());
+      for (size_t q = 0; q < res.size(); ++q) eins[q] = ms[res[q]].ecur[l];
+      if (L0.use_ts) {
+        auto fr = fields_of(l, res, eins.data(), nullptr, true);
+        CohortOp op{CohortOp::TS};
+        op.level = l;
+        op.mode = 1;
+        op.f0 = fr.first;
+        op.nf = fr.second;
+        op.has_e = true;
+        op.member = res[0];
+        ops.push_back(op);
+      } else {
+        for (size_t q = 0; q < res.size(); ++q) {
+          CohortOp op{CohortOp::SMOOTH};
+          op.member = res[q];
+          op.level = l;
+          op.mode = 1;
+          op.r = ms[res[q]].w->r[l];
+          op.e_in = eins[q];
+          op.out = ms[res[q]].w->t[l];
+          ops.push_back(op);
+        }
+      }
+      for (int q : res) {
+        CohortOp op{CohortOp::RESTRICT};
+        op.member = q;
+        op.level = l;
+        ops.push_back(op);
+      }
+    }
+  }
+  for (int l = Lmax - 2; l >= 0; --l) {              // up cycle
+    std::vector<int> who;
+    for (int q = 0; q < (int)ms.size(); ++q)
+      if (l < ms[q].h->L - 1) who.push_back(q);
+    if (who.empty()) continue;
+    const int nu = ms[who[0]].h->lv[l].nu_post, nu1 = ms[who[0]].h->lv[l].nu_pre;
+    for (int q : who)
+      if (ms[q].h->lv[l].nu_post != nu || ms[q].h->lv[l].nu_pre != nu1) return MCMG_OK;
+    for (int q : who) {
+      CohortOp op{CohortOp::PROLONG};
+      op.member = q;
+      op.level = l;
+      op.e_in = ms[q].ecur[l + 1];      // the pointers as they are at this point of the cycle
+      op.out = ms[q].ecur[l];
+      ops.push_back(op);
+    }
+    if (nu > 0) steps(l, who, nu1, nu, false);
+  }
+  if (!same || (int)fd.size() > c->fd_cap) return MCMG_OK;   // run the members apart
+  *planned = true;
+
+  // ---- lift on each member's stream; the server stream follows all of them
+  for (auto& m : ms) {
+    const Level& l0 = m.h->lv[0];
+    MCMG_TRY(launch_lift_gather(m.srcs, m.h->lift, m.w->r[0], l0.C, l0.g.nodes(), m.count, m.st));
+    MCMG_TRY(order_after(m.st, c->sst));
+  }
+  // ---- descriptors: one upload (the staging is rewritten only once the
+  // previous upload has been read)
+  if (!fd.empty()) {
+    MCMG_CUDA(cudaEventSynchronize(c->fd_ev));
+    std::memcpy(c->fd_h, fd.data(), sizeof(TsField) * fd.size());
+    MCMG_CUDA(cudaMemcpyAsync(c->fd_d, c->fd_h, sizeof(TsField) * fd.size(),
+                              cudaMemcpyHostToDevice, c->sst));
+    MCMG_CUDA(cudaEventRecord(c->fd_ev, c->sst));
+  }
+  for (const CohortOp& op : ops) {
+    CohortMember& m = ms[op.member];
+    const Level& lv = m.h->lv[op.level];
+    switch (op.kind) {
+      case CohortOp::TS:
+        MCMG_TRY(launch_smooth_ts_fields(lv, op.step, c->fd_d + op.f0, fd.data() + op.f0, op.nf,
+                                         op.has_e, op.mode, c->sst));
+        break;
+      case CohortOp::SMOOTH:
+        MCMG_TRY(launch_smooth(lv, op.step, op.r, op.e_in, op.out, op.mode, m.count, c->sst));
+        break;
+      case CohortOp::RESTRICT:
+        MCMG_TRY(launch_restrict(lv, m.w->t[op.level], m.w->r[op.level + 1], m.count, c->sst));
+        break;
+      case CohortOp::PROLONG:
+        MCMG_TRY(launch_prolong_add(lv, op.e_in, op.out, m.count, c->sst));
+        break;
+      case CohortOp::MEMSET:
+        MCMG_CUDA(cudaMemsetAsync(m.w->e[op.level], 0,
+                                  sizeof(float2) * lv.g.nodes() * lv.C * m.count, c->sst));
+        break;
+    }
+  }
+  // ---- projection on each member's stream, after the server stream
+  for (auto& m : ms) {
+    const Level& l0 = m.h->lv[0];
+    MCMG_TRY(order_after(c->sst, m.st));
+    MCMG_TRY(launch_project_scatter(m.ecur[0], m.h->proj, m.dsts, l0.C, l0.g.nodes(), m.count,
+                                    m.st));
+  }
+  c->cohort_rounds += 1;
+  c->cohort_members += ms.size();
+  return MCMG_OK;
+}
+
+// The server thread's stream and descriptor staging, made on first use.
+static mcmg_status server_resources(mcmg_ctx_s* c) {
+  if (c->sst) return MCMG_OK;
+  const int cap = 16384;
+  MCMG_CUDA(cudaStreamCreateWithFlags(&c->sst, cudaStreamNonBlocking));
+  MCMG_CUDA(cudaEventCreateWithFlags(&c->fd_ev, cudaEventDisableTiming));
+  MCMG_CUDA(cudaHostAlloc((void**)&c->fd_h, sizeof(TsField) * cap, cudaHostAllocDefault));
+  MCMG_CUDA(cudaMalloc((void**)&c->fd_d, sizeof(TsField) * cap));
+  c->fd_cap = cap;
+  return MCMG_OK;
+}
+
 static void server_loop(mcmg_ctx_s* c) {
   cudaSetDevice(c->device);
   std::unique_lock<std::mutex> lk(c->mu);
@@ -983,18 +1264,72 @@ static void server_loop(mcmg_ctx_s* c) {
       c->cv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
       continue;
     }
+    const bool batch = c->batching;
     lk.unlock();
     bool progressed = false;
-    std::vector<Request*> fin;
+    std::vector<Request*> fin, ready;
+    std::vector<int> counts;
     for (Request* r : c->active) {
       bool all = r->status != MCMG_PENDING;
       if (!all) {
-        int d = 0;
-        mcmg_status s = block_advance(r->blk, false, &d);
+        int d = 0, cnt = -1;
+        mcmg_status s = block_poll(r->blk, false, &d, &cnt);
         if (s != MCMG_OK) { r->status = s; r->err = mcmg_last_error(); d = 1; }
-        if (d) { all = true; progressed = true; }
+        if (d) {
+          all = true;
+          progressed = true;
+        } else if (cnt >= 0) {                 // its round finished: a new one starts now
+          ready.push_back(r);
+          counts.push_back(cnt);
+          progressed = true;
+        }
       }
       if (all) fin.push_back(r);
+    }
+    // the V-cycles of this round: requests that share weights and level
+    // layout run as one cohort (one launch per level and step for all of
+    // them), the others each on its own stream
+    if (!ready.empty()) {
+      std::map<uint64_t, std::vector<int>> groups;
+      for (int i = 0; i < (int)ready.size(); ++i)
+        if (counts[i] > 0) groups[batch ? ready[i]->h->wsig : (uint64_t)i].push_back(i);
+      for (auto& g : groups) {
+        bool done_g = false;
+        if (g.second.size() >= 2 && server_resources(c) == MCMG_OK) {
+          std::vector<CohortMember> ms;
+          for (int i : g.second) {
+            CohortMember m{};
+            m.h = ready[i]->h;
+            block_vcycle_io(ready[i]->blk, &m.w, &m.srcs, &m.dsts);
+            m.count = counts[i];
+            m.st = block_stream(ready[i]->blk);
+            ms.push_back(m);
+          }
+          bool planned = false;
+          mcmg_status s = cohort_vcycle(c, ms, &planned);
+          if (s != MCMG_OK) {
+            for (int i : g.second) { ready[i]->status = s; ready[i]->err = mcmg_last_error(); }
+            planned = true;
+          }
+          done_g = planned;
+        }
+        if (!done_g) {
+          for (int i : g.second) {
+            VWork* w;
+            const float2* const* srcs;
+            float2* const* dsts;
+            block_vcycle_io(ready[i]->blk, &w, &srcs, &dsts);
+            mcmg_status s = vcycle_run_batch(ready[i]->h, w, srcs, dsts, counts[i],
+                                             block_stream(ready[i]->blk));
+            if (s != MCMG_OK) { ready[i]->status = s; ready[i]->err = mcmg_last_error(); }
+          }
+        }
+      }
+      for (Request* r : ready) {
+        if (r->status != MCMG_PENDING) continue;
+        mcmg_status s = block_after_vcycle(r->blk);
+        if (s != MCMG_OK) { r->status = s; r->err = mcmg_last_error(); }
+      }
     }
     for (Request* r : fin) {
       mcmg_solve_info agg{};
@@ -1044,6 +1379,16 @@ static void server_stop(mcmg_ctx_s* c) {
   for (Request* r : c->queue) delete r;
   c->active.clear();
   c->queue.clear();
+  cudaSetDevice(c->device);
+  if (c->sst) {
+    cudaStreamSynchronize(c->sst);
+    cudaStreamDestroy(c->sst);
+    c->sst = nullptr;
+  }
+  if (c->fd_ev) { cudaEventDestroy(c->fd_ev); c->fd_ev = nullptr; }
+  if (c->fd_h) { cudaFreeHost(c->fd_h); c->fd_h = nullptr; }
+  if (c->fd_d) { cudaFree(c->fd_d); c->fd_d = nullptr; }
+  c->fd_cap = 0;
 }
 
 mcmg_status mcmg_submit(mcmg_ctx c, mcmg_handle h, const void* f, void* u,
@@ -1087,6 +1432,15 @@ mcmg_status mcmg_submit(mcmg_ctx c, mcmg_handle h, const void* f, void* u,
     server_start(c);
   }
   c->cv.notify_all();
+  return MCMG_OK;
+}
+
+mcmg_status mcmg_server_batching(mcmg_ctx c, int enable, uint64_t* rounds, uint64_t* members) {
+  if (!c) { set_error("NULL context"); return MCMG_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (enable >= 0) c->batching = enable != 0;
+  if (rounds) *rounds = c->cohort_rounds;
+  if (members) *members = c->cohort_members;
   return MCMG_OK;
 }
 

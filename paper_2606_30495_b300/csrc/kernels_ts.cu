@@ -78,8 +78,14 @@ struct TsParams {
   int nx, ny, nz;
   long long nodes;        // per field
   int tiles;              // per field
-  int items;              // tiles * fields
+  int items;              // tiles * fields (or the descriptors' tiles in total)
   int* err;               // error word (mapped host memory), may be null
+  // batched launch over fields of different grids and features: when set,
+  // item i belongs to the last descriptor whose `first` <= i, and the fields
+  // above (r, e_in, out, a, s, nx, ny, nz, nodes, tiles) are not used, except
+  // that e_in is non-null exactly when every descriptor's e_in is
+  const TsField* fields;
+  int nfields;
 };
 
 namespace ts {
@@ -161,6 +167,54 @@ __device__ __forceinline__ void load16(float* v, const float2* __restrict__ src,
     v[4 * i + 2] = t.z;
     v[4 * i + 3] = t.w;
   }
+}
+
+// One tile's field: its pointers (field offsets applied), grid and first node.
+struct Tile {
+  const float2* r;
+  const float2* e_in;
+  float2* out;
+  const float2* a;
+  const float2* s;
+  long long nodes, n0;
+  int nx, ny, nz;
+};
+
+__device__ __forceinline__ Tile tile_of(const TsParams& p, int item, int C) {
+  Tile t;
+  if (!p.fields) {
+    const int field = item / p.tiles, tile = item - field * p.tiles;
+    const size_t off = (size_t)field * (size_t)p.nodes * C;
+    t.r = p.r + off;
+    t.e_in = p.e_in ? p.e_in + off : nullptr;
+    t.out = p.out + off;
+    t.a = p.a;
+    t.s = p.s;
+    t.nodes = p.nodes;
+    t.nx = p.nx;
+    t.ny = p.ny;
+    t.nz = p.nz;
+    t.n0 = (long long)tile * M;
+  } else {
+    int lo = 0, hi = p.nfields - 1;       // the last descriptor with first <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.fields[mid].first <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const TsField& d = p.fields[lo];
+    t.r = d.r;
+    t.e_in = d.e_in;
+    t.out = d.out;
+    t.a = d.a;
+    t.s = d.s;
+    t.nodes = d.nodes;
+    t.nx = d.nx;
+    t.ny = d.ny;
+    t.nz = d.nz;
+    t.n0 = (long long)(item - d.first) * M;
+  }
+  return t;
 }
 
 __device__ __forceinline__ void store16(float2* dst, int C, long long n, int c0, const float* v) {
@@ -294,25 +348,23 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Cfg<K2, P>::PER_SM) k_smooth_
   };
 
   for (int item = blockIdx.x; item < p.items; item += gridDim.x) {
-    const int field = item / p.tiles;
-    const int tile = item - field * p.tiles;
-    const size_t off = (size_t)field * (size_t)p.nodes * C;
-    const float2* r = p.r + off;
-    const float2* ein = p.e_in ? p.e_in + off : nullptr;
-    float2* out = p.out + off;
-    const long long n = (long long)tile * ts::M + tid;
-    const bool row_ok = n < p.nodes;
-    const long long nc = row_ok ? n : p.nodes - 1;
+    const ts::Tile tv = ts::tile_of(p, item, C);
+    const float2* r = tv.r;
+    const float2* ein = tv.e_in;
+    float2* out = tv.out;
+    const long long n = tv.n0 + tid;
+    const bool row_ok = n < tv.nodes;
+    const long long nc = row_ok ? n : tv.nodes - 1;
     int x, y, z;
-    node_xyz(nc, p.nx, p.ny, x, y, z);
+    node_xyz(nc, tv.nx, tv.ny, x, y, z);
     // neighbour of node n along tap j (centre, -x, +x, -y, +y, -z, +z)
     auto nbr = [&](int j, long long& nb) -> bool {
       if (j == 0) { nb = nc; return row_ok; }
       const int axis = (j - 1) >> 1;
       const int sgn = (j & 1) ? -1 : 1;
       const int c = axis == 0 ? x : (axis == 1 ? y : z);
-      const int ext = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
-      const long long stride = axis == 0 ? 1 : (axis == 1 ? p.nx : (long long)p.nx * p.ny);
+      const int ext = axis == 0 ? tv.nx : (axis == 1 ? tv.ny : tv.nz);
+      const long long stride = axis == 0 ? 1 : (axis == 1 ? tv.nx : (long long)tv.nx * tv.ny);
       nb = nc + sgn * stride;
       return row_ok && c + sgn >= 0 && c + sgn < ext;
     };
@@ -360,7 +412,7 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Cfg<K2, P>::PER_SM) k_smooth_
         tc::tmem_ld16(tX + lane + c0, xv);
         tc::tmem_ld16(tY + lane + c0, yv);
         ts::load16(rv, r, C, nc, c0);
-        ts::load16(av, p.a, C, nc, c0);
+        ts::load16(av, tv.a, C, nc, c0);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           t[2 * k] = rv[2 * k] - xv[2 * k] - (av[2 * k] * yv[2 * k] - av[2 * k + 1] * yv[2 * k + 1]);
@@ -408,7 +460,7 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Cfg<K2, P>::PER_SM) k_smooth_
       for (int c0 = 0; c0 < K2; c0 += 16) {
         float zv[16], sv[16], zz[16];
         tc::tmem_ld16(tX + lane + c0, zv);
-        ts::load16(sv, p.s, C, nc, c0);
+        ts::load16(sv, tv.s, C, nc, c0);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           zz[2 * k] = sv[2 * k] * zv[2 * k] - sv[2 * k + 1] * zv[2 * k + 1];
@@ -535,7 +587,6 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Ring<K2, P>::PER_SM) k_smooth
     phase[b] ^= 1;
     return w;
   };
-  const long long nxny = (long long)p.nx * p.ny;
   const int my_tiles = blockIdx.x < p.items ? (p.items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int g_total = my_tiles * NSEG;
   // the next segment to issue, as (tile of this CTA, index within the tile)
@@ -544,27 +595,25 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Ring<K2, P>::PER_SM) k_smooth
   // issue the next segment of this CTA's sequence into ring buffer g_issued % R
   auto issue_next = [&]() {
     const int item = blockIdx.x + is_k * gridDim.x;
-    const int field = item / p.tiles, tile = item - field * p.tiles;
-    const size_t off = (size_t)field * (size_t)p.nodes * C;
-    const long long n0 = (long long)tile * ts::M;
+    const ts::Tile tv = ts::tile_of(p, item, C);
     const int idx = is_idx;
     const float2* base;
-    long long start = n0;
+    long long start = tv.n0;
     if (MODE == 0 && !has_e) {
-      base = idx == 0 ? p.r + off : p.s;
+      base = idx == 0 ? tv.r : tv.s;
     } else if (idx < NT) {
-      base = p.e_in + off;
+      base = tv.e_in;
       if (idx > 0) {
         const int axis = (idx - 1) >> 1;
-        const long long stride = axis == 0 ? 1 : (axis == 1 ? p.nx : nxny);
-        start = n0 + ((idx & 1) ? -stride : stride);
+        const long long stride = axis == 0 ? 1 : (axis == 1 ? tv.nx : (long long)tv.nx * tv.ny);
+        start = tv.n0 + ((idx & 1) ? -stride : stride);
       }
     } else {
       const int e = idx - NT;    // 0 r, 1 a, 2 s, 3 e
-      base = e == 0 ? p.r + off : e == 1 ? p.a : e == 2 ? p.s : p.e_in + off;
+      base = e == 0 ? tv.r : e == 1 ? tv.a : e == 2 ? tv.s : tv.e_in;
     }
     const int b = g_issued % R;
-    ts::copy_segment<K2, P>(ring_s + (uint32_t)(b * RG::SEG), base, start, p.nodes, tid);
+    ts::copy_segment<K2, P>(ring_s + (uint32_t)(b * RG::SEG), base, start, tv.nodes, tid);
     ts::cp_async_arrive(&full[b]);
     ++g_issued;
     if (++is_idx == NSEG) { is_idx = 0; ++is_k; }
@@ -582,22 +631,20 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Ring<K2, P>::PER_SM) k_smooth
 
   for (int k = 0; k < my_tiles; ++k) {
     const int item = blockIdx.x + k * gridDim.x;
-    const int field = item / p.tiles;
-    const int tile = item - field * p.tiles;
-    const size_t off = (size_t)field * (size_t)p.nodes * C;
-    float2* out = p.out + off;
-    const long long n = (long long)tile * ts::M + tid;
-    const bool row_ok = n < p.nodes;
-    const long long nc = row_ok ? n : p.nodes - 1;
+    const ts::Tile tv = ts::tile_of(p, item, C);
+    float2* out = tv.out;
+    const long long n = tv.n0 + tid;
+    const bool row_ok = n < tv.nodes;
+    const long long nc = row_ok ? n : tv.nodes - 1;
     const int gt = k * NSEG;        // first segment of this tile
     int x, y, z;
-    node_xyz(nc, p.nx, p.ny, x, y, z);
+    node_xyz(nc, tv.nx, tv.ny, x, y, z);
     auto tap_ok = [&](int j) -> bool {
       if (j == 0) return row_ok;
       const int axis = (j - 1) >> 1;
       const int sgn = (j & 1) ? -1 : 1;
       const int c = axis == 0 ? x : (axis == 1 ? y : z);
-      const int ext = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
+      const int ext = axis == 0 ? tv.nx : (axis == 1 ? tv.ny : tv.nz);
       return row_ok && c + sgn >= 0 && c + sgn < ext;
     };
 
@@ -897,7 +944,6 @@ __global__ void __launch_bounds__(256, 1) k_smooth_tsb(TsParams p) {
     ok = tc::bar_wait(&pbar, pph, p.err) && ok;
     pph ^= 1;
   };
-  const long long nxny = (long long)p.nx * p.ny;
   const int my_tiles = blockIdx.x < p.items ? (p.items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   // ---- the weight stream (thread 0): units in order, RB - 1 ahead
   const int u_total = my_tiles * UPT;
@@ -962,24 +1008,22 @@ __global__ void __launch_bounds__(256, 1) k_smooth_tsb(TsParams p) {
 
   for (int k = 0; k < my_tiles; ++k) {
     const int item = blockIdx.x + k * gridDim.x;
-    const int field = item / p.tiles;
-    const int tile = item - field * p.tiles;
-    const size_t off = (size_t)field * (size_t)p.nodes * C;
-    const float2* r = p.r + off;
-    const float2* ein = has_e ? p.e_in + off : nullptr;
-    float2* out = p.out + off;
-    const long long n = (long long)tile * ts::M + row;
-    const bool row_ok = n < p.nodes;
-    const long long nc = row_ok ? n : p.nodes - 1;
+    const ts::Tile tv = ts::tile_of(p, item, C);
+    const float2* r = tv.r;
+    const float2* ein = has_e ? tv.e_in : nullptr;
+    float2* out = tv.out;
+    const long long n = tv.n0 + row;
+    const bool row_ok = n < tv.nodes;
+    const long long nc = row_ok ? n : tv.nodes - 1;
     int x, y, z;
-    node_xyz(nc, p.nx, p.ny, x, y, z);
+    node_xyz(nc, tv.nx, tv.ny, x, y, z);
     auto nbr = [&](int j, long long& nb) -> bool {
       if (j == 0) { nb = nc; return row_ok; }
       const int axis = (j - 1) >> 1;
       const int sgn = (j & 1) ? -1 : 1;
       const int c = axis == 0 ? x : (axis == 1 ? y : z);
-      const int ext = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
-      const long long stride = axis == 0 ? 1 : (axis == 1 ? p.nx : nxny);
+      const int ext = axis == 0 ? tv.nx : (axis == 1 ? tv.ny : tv.nz);
+      const long long stride = axis == 0 ? 1 : (axis == 1 ? tv.nx : (long long)tv.nx * tv.ny);
       nb = nc + sgn * stride;
       return row_ok && c + sgn >= 0 && c + sgn < ext;
     };
@@ -1059,7 +1103,7 @@ __global__ void __launch_bounds__(256, 1) k_smooth_tsb(TsParams p) {
         tc::tmem_ld16(tX + lane + c0, xv);
         tc::tmem_ld16(tY + lane + c0, yv);
         ts::load16(rv, r, C, nc, c0);
-        ts::load16(av, p.a, C, nc, c0);
+        ts::load16(av, tv.a, C, nc, c0);
 #pragma unroll
         for (int qq = 0; qq < 8; ++qq) {
           t[2 * qq] = rv[2 * qq] - xv[2 * qq] - (av[2 * qq] * yv[2 * qq] - av[2 * qq + 1] * yv[2 * qq + 1]);
@@ -1108,7 +1152,7 @@ __global__ void __launch_bounds__(256, 1) k_smooth_tsb(TsParams p) {
         const int c0 = 32 * i + 16 * grp;
         float zv[16], sv[16], zz[16];
         tc::tmem_ld16(tX + lane + c0, zv);
-        ts::load16(sv, p.s, C, nc, c0);
+        ts::load16(sv, tv.s, C, nc, c0);
 #pragma unroll
         for (int qq = 0; qq < 8; ++qq) {
           zz[2 * qq] = sv[2 * qq] * zv[2 * qq] - sv[2 * qq + 1] * zv[2 * qq + 1];
@@ -1209,8 +1253,10 @@ mcmg_status tsr_launch(TsParams p, int nrhs, cudaStream_t st) {
     smem = s;
   }
   static_assert(RG::PER_SM >= 1, "ring does not fit");
-  p.tiles = (int)((p.nodes + ts::M - 1) / ts::M);
-  p.items = p.tiles * nrhs;
+  if (!p.fields) {
+    p.tiles = (int)((p.nodes + ts::M - 1) / ts::M);
+    p.items = p.tiles * nrhs;
+  }
   const int grid = std::min(p.items, sm_count() * RG::PER_SM);
   kern<<<grid, ts::THREADS, smem, st>>>(p);
   MCMG_CHECK_LAUNCH("smooth_tsr");
@@ -1228,8 +1274,10 @@ mcmg_status tsb_launch(TsParams p, int nrhs, cudaStream_t st) {
     MCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     attr = true;
   }
-  p.tiles = (int)((p.nodes + ts::M - 1) / ts::M);
-  p.items = p.tiles * nrhs;
+  if (!p.fields) {
+    p.tiles = (int)((p.nodes + ts::M - 1) / ts::M);
+    p.items = p.tiles * nrhs;
+  }
   const int grid = std::min(p.items, sm_count());
   kern<<<grid, B::THREADS, smem, st>>>(p);
   MCMG_CHECK_LAUNCH("smooth_tsb");
@@ -1257,8 +1305,10 @@ mcmg_status ts_launch(TsParams p, int nrhs, cudaStream_t st) {
     smem = s;
     per_sm = G::PER_SM;
   }
-  p.tiles = (int)((p.nodes + ts::M - 1) / ts::M);
-  p.items = p.tiles * nrhs;
+  if (!p.fields) {
+    p.tiles = (int)((p.nodes + ts::M - 1) / ts::M);
+    p.items = p.tiles * nrhs;
+  }
   const int grid = std::min(p.items, sm_count() * per_sm);
   kern<<<grid, ts::THREADS, smem, st>>>(p);
   MCMG_CHECK_LAUNCH("smooth_ts");
@@ -1317,6 +1367,33 @@ mcmg_status launch_smooth_ts(const Level& L, int step, const float2* r, const fl
   }
   if (tf) return d3 ? ts_dispatch<3, 1, 1>(L.C, p, nrhs, st) : ts_dispatch<2, 1, 1>(L.C, p, nrhs, st);
   return d3 ? ts_dispatch<3, 0, 1>(L.C, p, nrhs, st) : ts_dispatch<2, 0, 1>(L.C, p, nrhs, st);
+}
+
+mcmg_status launch_smooth_ts_fields(const Level& L, int step, const TsField* fields_dev,
+                                    const TsField* fields_host, int nf, bool has_e, int mode,
+                                    cudaStream_t st) {
+  if (nf < 1) return MCMG_OK;
+  if (mode == 1 && !has_e) {
+    set_error("tensor-core residual needs e");
+    return MCMG_ERR_ARG;
+  }
+  TsParams p{};
+  p.fields = fields_dev;
+  p.nfields = nf;
+  p.items = fields_host[nf - 1].first + fields_host[nf - 1].tiles;
+  // e_in only marks whether the fields carry e (the descriptors hold the pointers)
+  p.e_in = has_e ? fields_host[0].e_in : nullptr;
+  p.mats = L.ts_mats;
+  p.wi = 2 * L.g.d + 1 + 2 + step;
+  p.err = L.err;
+  const bool d3 = L.g.d == 3;
+  const bool tf = L.ts_prec == MCMG_FP32_TC;
+  if (mode == 0) {
+    if (tf) return d3 ? ts_dispatch<3, 1, 0>(L.C, p, 1, st) : ts_dispatch<2, 1, 0>(L.C, p, 1, st);
+    return d3 ? ts_dispatch<3, 0, 0>(L.C, p, 1, st) : ts_dispatch<2, 0, 0>(L.C, p, 1, st);
+  }
+  if (tf) return d3 ? ts_dispatch<3, 1, 1>(L.C, p, 1, st) : ts_dispatch<2, 1, 1>(L.C, p, 1, st);
+  return d3 ? ts_dispatch<3, 0, 1>(L.C, p, 1, st) : ts_dispatch<2, 0, 1>(L.C, p, 1, st);
 }
 
 // Host: a complex C x C matrix M[co][ci] (float2, row-major) -> its real

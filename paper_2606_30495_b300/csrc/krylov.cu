@@ -913,8 +913,9 @@ static mcmg_status member_process(Krylov* k) {
   return MCMG_OK;
 }
 
-mcmg_status block_advance(KrylovBlock* b, bool blocking, int* done) {
+mcmg_status block_poll(KrylovBlock* b, bool blocking, int* done, int* count) {
   *done = 0;
+  *count = -1;                         // -1: the last round is still running
   if (blocking) {
     MCMG_CUDA(cudaEventSynchronize(b->ev));
   } else {
@@ -924,33 +925,50 @@ mcmg_status block_advance(KrylovBlock* b, bool blocking, int* done) {
   }
   for (Krylov* k : b->ks)
     if (k->phase == Krylov::WAIT_RES || k->phase == Krylov::WAIT_STEP) MCMG_TRY(member_process(k));
-  // batch the V-cycles of every member that needs one
-  int count = 0;
+  // the members that need a V-cycle this round, in member order
+  int n = 0;
   for (Krylov* k : b->ks)
     if (k->phase == Krylov::NEED_STEP) {
-      b->ptr_h[count] = k->V + (size_t)k->j * k->n;
-      b->ptr_h[b->nb + count] = k->Z + (size_t)k->j * k->n;
-      ++count;
+      b->ptr_h[n] = k->V + (size_t)k->j * k->n;
+      b->ptr_h[b->nb + n] = k->Z + (size_t)k->j * k->n;
+      ++n;
     }
-  if (count > 0) {
-    MCMG_CUDA(cudaMemcpyAsync(b->ptr_d, b->ptr_h, sizeof(float2*) * count, cudaMemcpyHostToDevice,
+  if (n > 0) {
+    MCMG_CUDA(cudaMemcpyAsync(b->ptr_d, b->ptr_h, sizeof(float2*) * n, cudaMemcpyHostToDevice,
                               b->st));
-    MCMG_CUDA(cudaMemcpyAsync(b->ptr_d + b->nb, b->ptr_h + b->nb, sizeof(float2*) * count,
+    MCMG_CUDA(cudaMemcpyAsync(b->ptr_d + b->nb, b->ptr_h + b->nb, sizeof(float2*) * n,
                               cudaMemcpyHostToDevice, b->st));
-    MCMG_TRY(vcycle_run_batch(b->h, b->vw, b->ptr_d, b->ptr_d + b->nb, count, b->st));
-    for (Krylov* k : b->ks)
-      if (k->phase == Krylov::NEED_STEP) MCMG_TRY(enqueue_arnoldi(k, k->j));
   }
+  *count = n;
   bool all = true;
   for (Krylov* k : b->ks) all = all && k->phase == Krylov::DONE;
   if (all) {
     MCMG_CUDA(cudaStreamSynchronize(b->st));
     b->t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - b->t0).count();
     *done = 1;
-    return MCMG_OK;
   }
+  return MCMG_OK;
+}
+
+mcmg_status block_after_vcycle(KrylovBlock* b) {
+  for (Krylov* k : b->ks)
+    if (k->phase == Krylov::NEED_STEP) MCMG_TRY(enqueue_arnoldi(k, k->j));
   MCMG_CUDA(cudaEventRecord(b->ev, b->st));
   return MCMG_OK;
+}
+
+void block_vcycle_io(KrylovBlock* b, VWork** w, const float2* const** srcs, float2* const** dsts) {
+  *w = b->vw;
+  *srcs = b->ptr_d;
+  *dsts = b->ptr_d + b->nb;
+}
+
+mcmg_status block_advance(KrylovBlock* b, bool blocking, int* done) {
+  int count = 0;
+  MCMG_TRY(block_poll(b, blocking, done, &count));
+  if (*done || count < 0) return MCMG_OK;
+  if (count > 0) MCMG_TRY(vcycle_run_batch(b->h, b->vw, b->ptr_d, b->ptr_d + b->nb, count, b->st));
+  return block_after_vcycle(b);
 }
 
 void block_info(const KrylovBlock* b, mcmg_solve_info* info, mcmg_status* final_status) {

@@ -87,6 +87,11 @@ struct Level {
   bool use_ts = false;        // smoothing step and residual on tcgen05, TMEM A operands
   int ts_prec = -1;           // MCMG_BF16 or MCMG_FP32_TC when use_ts
   const uint4* ts_mats = nullptr;  // weight matrices in the operand layout of ts_prec
+  // signatures of the arithmetic of one smoothing step (stencil, K_A, K_S,
+  // W^(i)) and of the residual (stencil, K_A), with precision and C: launches
+  // of different handles may be batched when these agree
+  uint64_t ssig[2 * 8 + 1] = {};
+  uint64_t rsig = 0;
   // CUDA-core kernel shape per operation in use (0 smoothing step, 1 residual,
   // 2 restriction, 3 prolongation) and the autotuner's choice
   int shape[4] = {-1, -1, -1, -1};
@@ -94,11 +99,30 @@ struct Level {
   int* err = nullptr;         // device view of the handle's error word
 };
 
+// One field of a batched tensor-core launch: its own grid and features
+// (fields of several requests at the same level, same weights).  first: the
+// first tile (item) of the field in the launch, a prefix sum of tiles.
+struct TsField {
+  const float2* r;
+  const float2* e_in;
+  float2* out;
+  const float2* a;
+  const float2* s;
+  long long nodes;
+  int nx, ny, nz, tiles, first;
+};
+
 // tensor-core smoothing step and residual with A operands in tensor memory
 // (kernels_ts.cu); mode as launch_smooth
 bool ts_supported(int C, int prec);
 mcmg_status launch_smooth_ts(const Level& L, int step, const float2* r, const float2* e_in,
                              float2* out, int mode, int nrhs, cudaStream_t st);
+// The same over nf fields given by descriptors in device memory (fields_dev,
+// their host copy fields_host for the shapes): L supplies the weights, C and
+// the dimension; every field's e_in is null exactly when has_e is false.
+mcmg_status launch_smooth_ts_fields(const Level& L, int step, const TsField* fields_dev,
+                                    const TsField* fields_host, int nf, bool has_e, int mode,
+                                    cudaStream_t st);
 // complex C x C matrix -> its real 2C x 2C block form as a B operand: BF16
 // (4C^2 values), or TF32 hi and lo halves (2 * 4C^2 floats)
 void pack_ts_bf16(const float2* Mc, int C, uint16_t* out);
@@ -220,6 +244,15 @@ void block_destroy(mcmg_handle_s* h, KrylovBlock* b);
 mcmg_status block_begin(KrylovBlock* b, const double2* f, double2* u, const mcmg_solve_opts& o);
 // As krylov_advance, for the whole block (one round per call).
 mcmg_status block_advance(KrylovBlock* b, bool blocking, int* done);
+// The same round in two halves around a V-cycle run by the caller:
+// block_poll reads the last round's results (once its work has finished;
+// *count = -1 while it runs) and stages, on the block's stream, the device
+// pointer arrays of the *count members that need a V-cycle; after the caller
+// has run that V-cycle (block_vcycle_io: workspace, source and destination
+// arrays), block_after_vcycle enqueues their Arnoldi steps.
+mcmg_status block_poll(KrylovBlock* b, bool blocking, int* done, int* count);
+mcmg_status block_after_vcycle(KrylovBlock* b);
+void block_vcycle_io(KrylovBlock* b, VWork** w, const float2* const** srcs, float2* const** dsts);
 void block_info(const KrylovBlock* b, mcmg_solve_info* info, mcmg_status* final_status);
 int block_size(const KrylovBlock* b);
 cudaStream_t block_stream(const KrylovBlock* b);   // the block solve's private stream
@@ -255,6 +288,7 @@ struct mcmg_handle_s {
   int* err_host = nullptr;      // error word, mapped pinned (bounded waits that ran out)
   int* err_dev = nullptr;
   unsigned shape_gen = 0;       // bumped when a smoothing shape is overridden
+  uint64_t wsig = 0;            // signature of the weights and level layout (batching key)
   // Born-series variant (born.cu): per-axis Laplacian symbols and FFT
   // twiddles, q0
   bool born_ready = false;

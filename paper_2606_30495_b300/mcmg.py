@@ -88,6 +88,7 @@ _SIGS = {
     "mcmg_cgs2": [_P, _P, C.c_int, C.c_size_t, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "mcmg_cgs2_noalloc": [_P, C.c_int, C.c_size_t, _P, C.POINTER(C.c_double),
                           C.POINTER(C.c_double), _P],
+    "mcmg_server_batching": [_P, C.c_int, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)],
     "mcmg_kernel_shape_count": [C.c_int],
     "mcmg_get_kernel_shape": [_P, C.c_int, C.c_int, C.POINTER(C.c_int)],
     "mcmg_set_kernel_shape": [_P, C.c_int, C.c_int, C.c_int],
@@ -257,6 +258,14 @@ class Context:
         t = C.c_uint64()
         _check(self.lib.mcmg_submit(self.h, handle.h, ptr(f), ptr(u), C.byref(o), C.byref(t)))
         return t.value
+
+    def batching(self, enable=None):
+        """Switch cross-request batching (True / False, None: unchanged);
+        returns (cohort V-cycles run, requests they held)."""
+        r, m = C.c_uint64(), C.c_uint64()
+        e = -1 if enable is None else int(bool(enable))
+        _check(self.lib.mcmg_server_batching(self.h, e, C.byref(r), C.byref(m)))
+        return r.value, m.value
 
     def poll(self, ticket: int):
         """(status, info dict); status MCMG_PENDING while running."""

@@ -28,7 +28,35 @@ def _handles(ctx, reqs, precision):
     return [mcmg.Handle(ctx, c, om, 16, 1.0, w, precision=precision) for (_, c, om, w, _) in reqs]
 
 
+def _run_mix(ctx, hs, reqs):
+    from paper_2606_30495_b300 import mcmg
+    fs = [torch.from_numpy(f).cuda() for (_, _, _, _, f) in reqs]
+    us = [torch.zeros_like(x) for x in fs]
+    tickets = [ctx.submit(h, fd, u, tol=1e-6, restart_m=30, max_iters=3000, nrhs=r[0]["nrhs"])
+               for h, fd, u, r in zip(hs, fs, us, reqs)]
+    done = {}
+    t0 = time.time()
+    while len(done) < len(tickets) and time.time() - t0 < 120:
+        for t in tickets:
+            if t not in done:
+                st, info = ctx.poll(t)
+                if st != mcmg.MCMG_PENDING:
+                    done[t] = (st, info)
+        time.sleep(0.002)
+    assert len(done) == len(tickets)
+    out = []
+    for k, t in enumerate(tickets):
+        st, info = done[t]
+        assert st == 0 and info["converged"]
+        out.append(us[k].cpu().numpy())
+    return out
+
+
 def test_server_results_equal_alone_and_in_the_mix():
+    """Each request's solution is the same alone (mcmg_solve), in the mix with
+    cross-request batching (the V-cycles of requests on 64^2 and 128^2 grids,
+    3 and 4 levels of one model, run as cohorts: one tensor-core launch per
+    level and step for all of them) and in the mix without it."""
     from paper_2606_30495_b300 import mcmg
     ctx = mcmg.Context(0)
     reqs = _requests()
@@ -41,30 +69,21 @@ def test_server_results_equal_alone_and_in_the_mix():
             st, info = h.solve(fd, u, tol=1e-6, restart_m=30, max_iters=3000, nrhs=req["nrhs"])
             assert st == 0 and info["converged"], info
             alone.append(u.cpu().numpy())
-        # in the mix: all submitted at once, overlapping on the device
-        fs = [torch.from_numpy(f).cuda() for (_, _, _, _, f) in reqs]
-        us = [torch.zeros_like(x) for x in fs]
-        tickets = [ctx.submit(h, fd, u, tol=1e-6, restart_m=30, max_iters=3000, nrhs=r[0]["nrhs"])
-                   for h, fd, u, r in zip(hs, fs, us, reqs)]
-        done = {}
-        t0 = time.time()
-        while len(done) < len(tickets) and time.time() - t0 < 120:
-            for t in tickets:
-                if t not in done:
-                    st, info = ctx.poll(t)
-                    if st != mcmg.MCMG_PENDING:
-                        done[t] = (st, info)
-            time.sleep(0.002)
-        assert len(done) == len(tickets)
-        for k, t in enumerate(tickets):
-            st, info = done[t]
-            assert st == 0 and info["converged"]
-            mix = us[k].cpu().numpy()
-            assert np.max(np.abs(mix - alone[k])) <= 1e-12 * np.max(np.abs(alone[k]))
+        r0, m0 = ctx.batching(True)
+        batched = _run_mix(ctx, hs, reqs)
+        r1, m1 = ctx.batching()
+        assert r1 > r0 and m1 - m0 >= 2 * (r1 - r0), (r0, m0, r1, m1)   # cohorts were formed
+        ctx.batching(False)
+        apart = _run_mix(ctx, hs, reqs)
+        assert ctx.batching()[0] == r1                                  # and none without it
+        ctx.batching(True)
+        for k in range(len(reqs)):
+            for mix in (batched[k], apart[k]):
+                assert np.max(np.abs(mix - alone[k])) <= 1e-12 * np.max(np.abs(alone[k]))
             req, c, om, w, f = reqs[k]
             q = O.wavenumber_coef(c, om, 16, 1.0)
             for j in range(req["nrhs"]):
-                res = np.linalg.norm(f[j] - O.apply_A(q, mix[j])) / np.linalg.norm(f[j])
+                res = np.linalg.norm(f[j] - O.apply_A(q, batched[k][j])) / np.linalg.norm(f[j])
                 assert res <= 1e-6
     finally:
         for h in hs:
