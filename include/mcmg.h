@@ -312,7 +312,7 @@ mcmg_status mcmg_cgs2(mcmg_handle h, const void* V_dev, int k, size_t n, void* w
  * cudaMalloc: code running under another framework's fixed memory budget or
  * allocator, and call sites that cannot afford the device-wide
  * synchronisation that cudaMalloc / cudaFree can cause.  It allocates nothing:
- * its scratch (about 0.6 MB) is a static device array that every GPU which
+ * its scratch (about 1.2 MB) is a static device array that every GPU which
  * loads this library holds until the process exits.  Same arguments and
  * results as mcmg_cgs2, with k at most 64 (larger k returns MCMG_ERR_ARG), no
  * handle, and the caller's stream (NULL = legacy default stream).  V and w

@@ -100,15 +100,16 @@ __global__ void __launch_bounds__(RED_T) k_multidot(const float2* __restrict__ V
   DF ar[KV], ai[KV];
 #pragma unroll
   for (int i = 0; i < KV; ++i) ar[i] = ai[i] = DF{0.f, 0.f};
-  for (long long p = (long long)blockIdx.x * RED_T + threadIdx.x; p < n;
-       p += (long long)gridDim.x * RED_T) {
-    const WT wv = w[p];
+  // two elements per iteration, every load issued before the arithmetic, so
+  // that twice as many loads are in flight per thread
+  const long long stride = (long long)gridDim.x * RED_T;
+  auto accumulate = [&](const WT wv, const float2 (&vv)[KV]) {
     const DF wx = df_from(wv.x), wy = df_from(wv.y);
 #pragma unroll
     for (int i = 0; i < KV; ++i) {
       const int ii = i0 + i;
       if (ii < k) {
-        const float2 v = V[(long long)ii * ldv + p];
+        const float2 v = vv[i];
         // conj(v) w = (vx wx + vy wy) + i (vx wy - vy wx)
         df_add(ar[i], df_mul(v.x, wx.hi, wx.lo));
         df_add(ar[i], df_mul(v.y, wy.hi, wy.lo));
@@ -119,6 +120,29 @@ __global__ void __launch_bounds__(RED_T) k_multidot(const float2* __restrict__ V
         df_add(ar[i], df_sq(wy));
       }
     }
+  };
+  long long p = (long long)blockIdx.x * RED_T + threadIdx.x;
+  for (; p + stride < n; p += 2 * stride) {
+    const WT wa = w[p], wb = w[p + stride];
+    float2 va[KV], vb[KV];
+#pragma unroll
+    for (int i = 0; i < KV; ++i) {
+      const int ii = i0 + i < k ? i0 + i : 0;
+      va[i] = V[(long long)ii * ldv + p];
+      vb[i] = V[(long long)ii * ldv + p + stride];
+    }
+    accumulate(wa, va);
+    accumulate(wb, vb);
+  }
+  if (p < n) {
+    const WT wa = w[p];
+    float2 va[KV];
+#pragma unroll
+    for (int i = 0; i < KV; ++i) {
+      const int ii = i0 + i < k ? i0 + i : 0;
+      va[i] = V[(long long)ii * ldv + p];
+    }
+    accumulate(wa, va);
   }
   // 2 KV values per thread: through shared memory, warp q sums values 2q, 2q+1
   static_assert(2 * KV == 2 * (RED_T / 32), "one warp per pair of values");
@@ -196,15 +220,24 @@ __global__ void __launch_bounds__(RED_T) k_update(const float2* __restrict__ V, 
   for (long long p = (long long)blockIdx.x * RED_T + threadIdx.x; p < n;
        p += (long long)gridDim.x * RED_T) {
     DF sr{0.f, 0.f}, si{0.f, 0.f};
-    for (int i = 0; i < k; ++i) {
-      const float2 v = V[(long long)i * ldv + p];
+    // h v = (hx vx - hy vy) + i (hx vy + hy vx); four basis vectors loaded
+    // before their arithmetic (same order of accumulation as one at a time)
+    auto acc = [&](const float2 v, int i) {
       const DF hx = hs[2 * i], hy = hs[2 * i + 1];
-      // h v = (hx vx - hy vy) + i (hx vy + hy vx)
       df_add(sr, df_mul(v.x, hx.hi, hx.lo));
       df_add(sr, df_mul(-v.y, hy.hi, hy.lo));
       df_add(si, df_mul(v.y, hx.hi, hx.lo));
       df_add(si, df_mul(v.x, hy.hi, hy.lo));
+    };
+    int i = 0;
+    for (; i + 4 <= k; i += 4) {
+      float2 v4[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v4[q] = V[(long long)(i + q) * ldv + p];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc(v4[q], i + q);
     }
+    for (; i < k; ++i) acc(V[(long long)i * ldv + p], i);
     const double2 wd = to_d2(w[p]);
     store_w(w + p, wd.x - df_to(sr), wd.y - df_to(si));
     const double2 o = to_d2(w[p]);
@@ -267,10 +300,28 @@ __global__ void __launch_bounds__(RED_T) k_reduce_res(const double* __restrict__
 }
 
 // v0 = r / beta (to complex64)
+// The scalar of a scaling kernel, computed once per block (FP64 square roots
+// and divisions run at a small fraction of the FP32 rate on this part).
+__device__ __forceinline__ double block_inv_sqrt(const double* v) {
+  __shared__ double inv;
+  if (threadIdx.x == 0) {
+    const double b = sqrt(*v);
+    inv = b > 0.0 ? 1.0 / b : 0.0;
+  }
+  __syncthreads();
+  return inv;
+}
+
+__device__ __forceinline__ double block_sqrt(const double* v) {
+  __shared__ double root;
+  if (threadIdx.x == 0) root = sqrt(*v);
+  __syncthreads();
+  return root;
+}
+
 __global__ void k_start_cycle(const double2* __restrict__ r, const double* __restrict__ dsc,
                               float2* __restrict__ v0, long long n) {
-  const double beta = sqrt(dsc[0]);
-  const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+  const double inv = block_inv_sqrt(dsc);
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p < n) {
     const double2 v = r[p];
@@ -285,10 +336,9 @@ struct Stat {
 // v_{j+1} = w / sqrt(nrm2)
 __global__ void k_scale(const double2* __restrict__ w, const double* __restrict__ dsc,
                         float2* __restrict__ v, long long n) {
+  const double inv = block_inv_sqrt(dsc + 3);
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
-  const double hn = sqrt(dsc[3]);
-  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
   const double2 x = w[p];
   v[p] = make_float2((float)(x.x * inv), (float)(x.y * inv));
 }
@@ -296,9 +346,9 @@ __global__ void k_scale(const double2* __restrict__ w, const double* __restrict_
 // Stationary step: u += beta * z, beta = ||r|| (the V-cycle ran on r / beta).
 __global__ void k_stationary_update(const float2* __restrict__ z, const double* __restrict__ dsc,
                                     double2* __restrict__ u, long long n) {
+  const double beta = block_sqrt(dsc);
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
-  const double beta = sqrt(dsc[0]);
   const float2 zz = z[p];
   const double2 o = u[p];
   u[p] = make_double2(o.x + beta * zz.x, o.y + beta * zz.y);
@@ -368,9 +418,9 @@ struct Krylov {
 };
 
 // Blocks of the grid-stride reductions: about one element per thread, at
-// most four blocks per SM (the update and multi-dot loops over the basis are
+// most eight blocks per SM (the update and multi-dot loops over the basis are
 // serial per element, so parallelism over elements hides their latency).
-constexpr int RED_MAX_BLK = 148 * 4;
+constexpr int RED_MAX_BLK = 148 * 8;
 
 static int red_blocks(long long n) {
   long long b = (n + RED_T - 1) / RED_T;
