@@ -836,17 +836,23 @@ namespace ts {
 
 template <int K2, int P>
 struct Big {
-  static constexpr int NH = (P == 1 && K2 == 128) ? 2 : 1;   // K-halves per tap
+  // K-halves per tap: with TF32x3 the two A slots of a whole tap would not
+  // leave room beside X and Y (K2 = 128) or would hold the SM's tensor memory
+  // for one CTA alone (K2 = 64); in halves two CTAs fit per SM at K2 = 64
+  static constexpr int NH = (P == 1 && K2 >= 64) ? 2 : 1;
   static constexpr int KU = K2 / NH;                          // K of one stage
   static constexpr int AW = P ? 2 * KU : KU / 2;              // TMEM columns per A slot
-  static constexpr int COLS = 512;
-  static_assert(2 * K2 + 2 * AW <= COLS, "TMEM");
+  static constexpr int NEED = 2 * K2 + 2 * AW;
+  static constexpr int COLS = NEED <= 128 ? 128 : NEED <= 256 ? 256 : 512;
+  static constexpr int PER_SM = 512 / COLS;                   // CTAs per SM
+  static_assert(NEED <= COLS, "TMEM");
   static constexpr int SUB = KU * K2 * (P ? 4 : 2);           // bytes of one K-half (hi or bf16)
   static constexpr int UNIT = P ? 2 * SUB : SUB;              // bytes of one streamed unit
   static constexpr int MATB = P ? 2 * K2 * K2 * 4 : K2 * K2 * 2;
-  static constexpr int RB = (192 * 1024) / UNIT;              // ring buffers
+  static constexpr int RB = (PER_SM == 1 ? 192 * 1024 : 96 * 1024) / UNIT;   // ring buffers
   static constexpr int THREADS = 256;
   static constexpr int CPT = KU / 32;                         // 16-column chunks per thread per stage
+  static_assert(RB >= 2 && CPT >= 1, "ring and stage shapes");
 };
 
 __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes,
@@ -893,7 +899,7 @@ __device__ __forceinline__ void gemm_unit(uint32_t d, uint32_t a, uint32_t b, bo
 }  // namespace ts
 
 template <int K2, int D, int P, int MODE>
-__global__ void __launch_bounds__(256, 1) k_smooth_tsb(TsParams p) {
+__global__ void __launch_bounds__(256, ts::Big<K2, P>::PER_SM) k_smooth_tsb(TsParams p) {
   using B = ts::Big<K2, P>;
   constexpr int C = K2 / 2;
   constexpr int NT = 2 * D + 1;
@@ -1278,7 +1284,7 @@ mcmg_status tsb_launch(TsParams p, int nrhs, cudaStream_t st) {
     p.tiles = (int)((p.nodes + ts::M - 1) / ts::M);
     p.items = p.tiles * nrhs;
   }
-  const int grid = std::min(p.items, sm_count());
+  const int grid = std::min(p.items, sm_count() * B::PER_SM);
   kern<<<grid, B::THREADS, smem, st>>>(p);
   MCMG_CHECK_LAUNCH("smooth_tsb");
   return MCMG_OK;
