@@ -325,12 +325,16 @@ mcmg_status mcmg_cgs2(mcmg_handle h, const void* V_dev, int k, size_t n, void* w
 mcmg_status mcmg_cgs2_noalloc(const void* V_dev, int k, size_t n, void* w_dev,
                               double* h_host, double* norm_host, void* stream);
 
-/* Kernel shapes of the CUDA-core V-cycle operations (tuning and test access;
- * the paper has no counterpart).  op: 0 smoothing step, 1 residual
- * r - A_l(e), 2 restriction R_l, 3 prolongation P_l (ops 2 and 3 exist for
+/* Kernel shapes of the V-cycle operations (tuning and test access; the
+ * paper has no counterpart).  op: 0 smoothing step, 1 residual r - A_l(e),
+ * 2 restriction R_l, 3 prolongation P_l (ops 2 and 3 exist for
  * level < levels-1).  Each has several interchangeable kernels and thread
  * shapes with the same results up to FP32 rounding order; setup times them
- * on every level and keeps the fastest.
+ * on every level and keeps the fastest.  The last shape of ops 2 and 3 is
+ * the tensor-core transfer, available on tensor-core handles (MCMG_BF16,
+ * MCMG_FP32_TC) where the transfer's input has 16, 32 or 64 channels and
+ * its output as many, half or twice as many; its results carry that
+ * handle's mixing precision.
  *   mcmg_kernel_shape_count: number of shapes of op (indices 0 .. count-1),
  *                            0 for an unknown op.
  *   mcmg_get_kernel_shape:   the shape `level` uses for op (*shape).

@@ -515,6 +515,32 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
       lv.ts_prec = MCMG_FP32_TC;
       lv.ts_mats = dst;
     }
+    if (lv.use_ts && l < L - 1) {
+      // restriction R_o (Cn x C) and prolongation P_o (C x Cn), every tap
+      const int Cn = lv.Cn;
+      const bool tf = lv.ts_prec == MCMG_FP32_TC;
+      const size_t per = (tf ? 2 * sizeof(float) : sizeof(uint16_t)) * (size_t)(2 * C) * (2 * Cn);
+      std::vector<unsigned char> hr(per * T3), hp(per * T3);
+      std::vector<float2> mat((size_t)C * Cn);
+      for (int t = 0; t < T3; ++t) {
+        const double* rs = lb[l].R + (size_t)2 * t * Cn * C;
+        for (size_t i = 0; i < (size_t)C * Cn; ++i)
+          mat[i] = make_float2((float)rs[2 * i], (float)rs[2 * i + 1]);
+        pack_ts_rect(mat.data(), Cn, C, tf, hr.data() + per * t);
+        const double* ps = lb[l].P + (size_t)2 * t * C * Cn;
+        for (size_t i = 0; i < (size_t)C * Cn; ++i)
+          mat[i] = make_float2((float)ps[2 * i], (float)ps[2 * i + 1]);
+        pack_ts_rect(mat.data(), C, Cn, tf, hp.data() + per * t);
+      }
+      uint4 *dr = nullptr, *dp = nullptr;
+      if ((s = dev_alloc(h, h->arena, (void**)&dr, hr.size())) ||
+          (s = dev_alloc(h, h->arena, (void**)&dp, hp.size())))
+        return cleanup(), s;
+      MCMG_CUDA(cudaMemcpy(dr, hr.data(), hr.size(), cudaMemcpyHostToDevice));
+      MCMG_CUDA(cudaMemcpy(dp, hp.data(), hp.size(), cudaMemcpyHostToDevice));
+      lv.ts_R = dr;
+      lv.ts_P = dp;
+    }
   }
   {
     std::vector<float2> vl(C0), vp(C0);

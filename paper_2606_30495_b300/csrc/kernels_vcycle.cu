@@ -782,6 +782,10 @@ struct TShape {
 static constexpr TShape kTShapes[] = {{0, 0, 0}, {1, 4, 4}, {2, 4, 4}, {1, 4, 8}, {2, 4, 8},
                                      {1, 4, 2}, {1, 2, -1}, {1, 4, -1}, {1, 8, -1}};
 static constexpr int kNumTShapes = sizeof(kTShapes) / sizeof(kTShapes[0]);
+// The shape after the table: the tensor-core transfer (kernels_xts.cu), on
+// tensor-core levels whose input side has at least 16 channels.
+static constexpr int kXtsShape = kNumTShapes;
+static constexpr int kNumXShapes = kNumTShapes + 1;
 
 // Register-tiled transfers are built for channel pairs (fine, coarse) with
 // the coarse count equal to or twice the fine one; other pairs use shape 0.
@@ -862,6 +866,7 @@ static TransferParams transfer_params(const Level& L, bool restrict_, const floa
 
 static bool xshape_ok(int s, const Level& L, bool restrict_) {
   if (s == 0) return true;
+  if (s == kXtsShape) return xts_supported(L, restrict_);
   if (!xt_pair(L.C, L.Cn)) return false;
   const TShape& k = kTShapes[s];
   const int CI = restrict_ ? L.C : L.Cn, CO = restrict_ ? L.Cn : L.C;
@@ -871,6 +876,7 @@ static bool xshape_ok(int s, const Level& L, bool restrict_) {
 
 static mcmg_status transfer_run(const Level& L, const TransferParams& p, bool restrict_, int shape,
                                 int nrhs, cudaStream_t st) {
+  if (shape == kXtsShape) return launch_transfer_ts(L, restrict_, p.src, p.dst, nrhs, st);
   if (shape > 0)
     return transfer_rt_launch(p, L.C, L.Cn, L.g.d, restrict_, kTShapes[shape].tn,
                               kTShapes[shape].cv, kTShapes[shape].kq, nrhs, st);
@@ -905,15 +911,15 @@ mcmg_status autotune_transfer(Level& L, float2* fine, float2* coarse, cudaStream
   for (int op = 2; op < 4 && status == MCMG_OK; ++op) {
     const bool r = op == 2;
     const TransferParams p = transfer_params(L, r, r ? fine : coarse, r ? coarse : fine);
-    float best_ms[kNumTShapes];
-    for (int s = 0; s < kNumTShapes; ++s) best_ms[s] = 1e30f;
+    float best_ms[kNumXShapes];
+    for (int s = 0; s < kNumXShapes; ++s) best_ms[s] = 1e30f;
     for (int pass = 0; pass < kTunePasses && status == MCMG_OK; ++pass) {
-      for (int s = 0; s < kNumTShapes; ++s) {
+      for (int s = 0; s < kNumXShapes; ++s) {
         if (!xshape_ok(s, L, r)) continue;
         // thread-per-node transfers time well alone but slowed the whole
         // V-cycle on grids with small coarse levels (measured on 256^2;
         // faster on 1024^2): candidates only from 2^16 coarse nodes on
-        if (kTShapes[s].kq < 0 && L.g.coarse().nodes() < (1 << 16)) continue;
+        if (s < kNumTShapes && kTShapes[s].kq < 0 && L.g.coarse().nodes() < (1 << 16)) continue;
         for (int rep = 0; rep < 2; ++rep)
           if ((status = transfer_run(L, p, r, s, 1, st)) != MCMG_OK) break;
         if (status != MCMG_OK) break;
@@ -930,7 +936,7 @@ mcmg_status autotune_transfer(Level& L, float2* fine, float2* coarse, cudaStream
       }
     }
     int best_s = 0;
-    for (int s = 0; s < kNumTShapes; ++s)
+    for (int s = 0; s < kNumXShapes; ++s)
       if (best_ms[s] < best_ms[best_s]) best_s = s;
     L.shape[op] = best_s;
     L.tuned[op] = best_s;
@@ -940,7 +946,7 @@ mcmg_status autotune_transfer(Level& L, float2* fine, float2* coarse, cudaStream
   return status;
 }
 
-int kernel_shape_count(int op) { return op < 2 ? kNumShapes : kNumTShapes; }
+int kernel_shape_count(int op) { return op < 2 ? kNumShapes : kNumXShapes; }
 bool kernel_shape_valid(const Level& L, int op, int shape) {
   if (shape < 0 || shape >= kernel_shape_count(op)) return false;
   return op < 2 ? shape_ok(shape, L.C, L.g.d) : xshape_ok(shape, L, op == 2);

@@ -1,0 +1,554 @@
+// Restriction and prolongation of the McMg V-cycle (Section 3.2, Algorithm 2)
+// on the tcgen05 tensor cores, for levels whose input side has at least 16
+// channels (BF16 or FP32-accurate 3xTF32 operands, FP32 accumulation).
+//
+// Both are sums over 3^d taps of a complex channel-mixing matrix applied to
+// a gathered row, i.e. GEMMs over tiles of M = 128 output nodes with
+// K = 2 C_in, N = 2 C_out in real block form:
+//
+//   restriction   r_c[J]  = sum_o R_o x[2J + o]                (27 / 9 taps)
+//   prolongation  e[2j+p] += sum_{(J, o): 2J + o = 2j + p} P_o e_c[J]
+//
+// The prolongation is taken output by output: a tile holds 128 fine nodes of
+// one parity class p (fine node 2j + p for 128 consecutive j of the coarse
+// lattice), whose taps are fixed: per axis one (J = j, o = 0) when p_a = 0,
+// two (J = j, o = +1) and (J = j + 1, o = -1) when p_a = 1.
+//
+// The structure is that of the streamed-weight smoothing step (kernels_ts.cu):
+// 256 threads, thread t owning row 32 (w % 4) + lane of warp w and every
+// other 16-column chunk of it; each (tap, K-part) is one A stage gathered
+// into registers two stages ahead, converted and written to one of two A
+// slots in tensor memory; the weight matrices stream per (tap, K-part) unit
+// through a ring of shared-memory buffers filled by bulk asynchronous copies;
+// one thread issues the MMAs into the accumulator D.  The epilogue stores D
+// (restriction) or adds it to the fine field (prolongation).  Every mbarrier
+// wait is bounded and the block votes on the outcome at its next barrier.
+#include <algorithm>
+#include <cstring>
+
+#include "mcmg_internal.cuh"
+#include "tcgen05.cuh"
+#include "vcycle_kernels.cuh"
+
+namespace mcmg {
+
+namespace xts {
+
+constexpr int M = 128;
+constexpr int THREADS = 256;
+
+template <int KI, int KO, int P>  // P: 0 BF16, 1 TF32x3
+struct Cfg {
+  // A stages of 32 K values (one 16-column chunk per thread)
+  static constexpr int KU = 32;
+  static constexpr int NH = KI / KU;                          // K parts per tap
+  static constexpr int AW = P ? 2 * KU : KU / 2;              // A slot columns
+  // two accumulators (taps alternate) and two A slots
+  static constexpr int NEED = 2 * KO + 2 * AW;
+  static constexpr int COLS = NEED <= 256 ? 256 : 512;
+  static constexpr int PER_SM = 512 / COLS;
+  static constexpr int SUB = KU * KO * (P ? 4 : 2);           // one K part of one matrix (hi or bf16)
+  static constexpr int UNIT = P ? 2 * SUB : SUB;
+  static constexpr int MATB = P ? 2 * KO * KI * 4 : KO * KI * 2;
+  static constexpr int RING = PER_SM == 1 ? 192 * 1024 : 96 * 1024;
+  static constexpr int RB = RING / UNIT;
+  static constexpr int NCH = (KO + 31) / 32;                  // output chunks per thread
+  static_assert(KI % KU == 0 && RB >= 2 && NEED <= COLS, "transfer shape");
+};
+
+struct XParams {
+  const float2* src;      // restriction: fine x; prolongation: coarse e_c
+  float2* dst;            // restriction: coarse r_c (written); prolongation: fine e (+=)
+  const uint4* mats;      // [3^d taps] matrices in the operand layout, MATB bytes each
+  int fx, fy, fz;         // fine grid
+  int cx, cy, cz;         // coarse grid
+  long long src_nodes, dst_nodes;   // per field
+  int tiles;              // coarse-lattice tiles per field (per parity class)
+  int items;
+  int* err;
+};
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(dst), "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tc::smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 16 FP32 values -> A slot columns c0 .. c0+15 (TF32 hi at c0, lo at KU + c0;
+// or 8 packed BF16 pairs at c0 / 2)
+template <int KU, int P>
+__device__ __forceinline__ void put16(uint32_t slot, int c0, const float* v) {
+  if constexpr (P == 1) {
+    uint32_t hi[16], lo[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      hi[i] = tc::to_tf32(v[i]);
+      lo[i] = tc::to_tf32(v[i] - __uint_as_float(hi[i]));
+    }
+    tc::tmem_st16(slot + c0, hi);
+    tc::tmem_st16(slot + KU + c0, lo);
+  } else {
+    uint32_t pk[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) pk[i] = tc::pack_bf16(v[2 * i], v[2 * i + 1]);
+    tc::tmem_st8(slot + c0 / 2, pk);
+  }
+}
+
+// The MMAs of one streamed unit: D (+)= A B^T over the unit's K range.
+template <int KI, int KO, int P>
+__device__ __forceinline__ void gemm_unit(uint32_t d, uint32_t a, uint32_t b, bool accumulate) {
+  using G = Cfg<KI, KO, P>;
+  constexpr uint32_t lbo = KO * 16;       // B rows are the KO outputs
+  constexpr uint64_t kstep = (2 * lbo) >> 4;
+  if constexpr (P == 0) {
+    constexpr uint32_t idesc = tc::make_idesc(M, KO);
+    const uint64_t b0 = tc::make_desc(b, lbo, 128);
+#pragma unroll
+    for (int s = 0; s < G::KU / 16; ++s)
+      tc::mma_bf16_ts(d, a + 8 * s, b0 + s * kstep, idesc, (accumulate || s > 0) ? 1u : 0u);
+  } else {
+    constexpr uint32_t idesc = tc::make_idesc_tf32(M, KO);
+    const uint64_t bh0 = tc::make_desc(b, lbo, 128);
+    const uint64_t bl0 = bh0 + (G::SUB >> 4);
+#pragma unroll
+    for (int s = 0; s < G::KU / 8; ++s) {
+      const uint32_t ahi = a + 8 * s, alo = a + G::KU + 8 * s;
+      tc::mma_tf32_ts(d, alo, bh0 + s * kstep, idesc, (accumulate || s > 0) ? 1u : 0u);
+      tc::mma_tf32_ts(d, ahi, bl0 + s * kstep, idesc, 1u);
+      tc::mma_tf32_ts(d, ahi, bh0 + s * kstep, idesc, 1u);
+    }
+  }
+}
+
+// Tap `idx` of an item: its weight index t (taps ((oz+1)*3+(oy+1))*3+(ox+1))
+// and the gather offsets.  Restriction: idx enumerates the 3^D offsets o and
+// the gathered fine node is 2J + o.  Prolongation of parity class p: the
+// odd axes of p take o = +1 (source J = j) or o = -1 (J = j + 1) by the bits
+// of idx; even axes take o = 0.
+template <int D, int DIR>
+__device__ __forceinline__ void tap_of(int cls, int idx, int& t, int (&o)[3], int (&dj)[3]) {
+  if constexpr (DIR == 0) {
+    int r = idx;
+    o[0] = r % 3 - 1;
+    r /= 3;
+    o[1] = r % 3 - 1;
+    r /= 3;
+    o[2] = D == 3 ? r - 1 : 0;
+    dj[0] = dj[1] = dj[2] = 0;
+  } else {
+    int bit = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dj[a] = 0;
+      o[a] = 0;
+      if (a < D && ((cls >> a) & 1)) {
+        const bool minus = (idx >> bit) & 1;
+        ++bit;
+        o[a] = minus ? -1 : 1;
+        dj[a] = minus ? 1 : 0;
+      }
+    }
+  }
+  t = D == 3 ? ((o[2] + 1) * 3 + (o[1] + 1)) * 3 + (o[0] + 1) : (o[1] + 1) * 3 + (o[0] + 1);
+}
+
+template <int D>
+__host__ __device__ constexpr int popc_cls(int cls) {
+  return (cls & 1) + ((cls >> 1) & 1) + (D == 3 ? ((cls >> 2) & 1) : 0);
+}
+
+}  // namespace xts
+
+template <int KI, int KO, int D, int P, int DIR>
+__global__ void __launch_bounds__(xts::THREADS, xts::Cfg<KI, KO, P>::PER_SM)
+    k_transfer_ts(xts::XParams p) {
+  using G = xts::Cfg<KI, KO, P>;
+  constexpr int CI = KI / 2, CO = KO / 2;
+  constexpr int NH = G::NH, KU = G::KU, RB = G::RB, NCH = G::NCH;
+  constexpr int T3 = D == 3 ? 27 : 9;
+  constexpr int NCLS = DIR == 1 ? (1 << D) : 1;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t abar[2];
+  __shared__ uint64_t fullb[RB];
+  __shared__ uint64_t emptyb[RB];
+  __shared__ uint32_t tmem_base_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lanei = tid & 31;
+  const int row = 32 * (warp & 3) + lanei;
+  const int grp = warp >> 2;
+
+  if (tid == 0) {
+    tc::bar_init(&abar[0], 1);
+    tc::bar_init(&abar[1], 1);
+    for (int b = 0; b < RB; ++b) {
+      tc::bar_init(&fullb[b], 1);
+      tc::bar_init(&emptyb[b], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     tc::smem_u32(&tmem_base_sh)),
+                 "r"((uint32_t)G::COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const uint32_t lane = (uint32_t)(32 * (warp & 3)) << 16;
+  // accumulators: tap t into column tmem + (t & 1) KO; A slots after them
+  const uint32_t slot0 = tmem + 2 * KO, slot1 = slot0 + G::AW;
+  const uint32_t ring_s = tc::smem_u32(smem);
+  uint32_t aph[2] = {0, 0};
+  bool ok = true;
+  auto wait_a = [&](int s) {
+    ok = tc::bar_wait(&abar[s], aph[s], p.err) && ok;
+    aph[s] ^= 1;
+  };
+  const int my_items = blockIdx.x < p.items ? (p.items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  // taps of an item: all 3^D for the restriction, 2^(odd axes) for a class
+  auto item_class = [&](int item) -> int {
+    if constexpr (DIR == 0) return 0;
+    else return (item / p.tiles) % NCLS;
+  };
+  auto item_taps = [&](int item) -> int {
+    if constexpr (DIR == 0) return T3;
+    else return 1 << xts::popc_cls<D>(item_class(item));
+  };
+  // ---- weight stream (thread 0): units (tap, K part) of every item in order
+  int u_issued = 0, u_done = 0;
+  int ui_k = 0, ui_idx = 0;           // next unit: item of this CTA, unit within it
+  int u_left = 0;                     // units of this CTA not yet issued
+  for (int k = 0; k < my_items; ++k) u_left += item_taps(blockIdx.x + k * gridDim.x) * NH;
+  const int u_total = u_left;
+  auto issue_unit = [&]() {
+    const int b = u_issued % RB;
+    if (u_issued >= RB)
+      ok = tc::bar_wait(&emptyb[b], (uint32_t)(((u_issued / RB) - 1) & 1), p.err) && ok;
+    const int item = blockIdx.x + ui_k * gridDim.x;
+    const int tap = ui_idx / NH, h = ui_idx % NH;
+    int t, o[3], dj[3];
+    xts::tap_of<D, DIR>(item_class(item), tap, t, o, dj);
+    const uint8_t* src = reinterpret_cast<const uint8_t*>(p.mats) + (size_t)t * G::MATB;
+    const uint32_t dst = ring_s + (uint32_t)(b * G::UNIT);
+    xts::expect_tx(&fullb[b], (uint32_t)G::UNIT);
+    xts::bulk_copy(dst, src + (size_t)h * G::SUB, G::SUB, &fullb[b]);
+    if constexpr (P == 1)
+      xts::bulk_copy(dst + G::SUB, src + (size_t)KO * KI * 4 + (size_t)h * G::SUB, G::SUB,
+                     &fullb[b]);
+    ++u_issued;
+    if (++ui_idx == item_taps(item) * NH) { ui_idx = 0; ++ui_k; }
+  };
+  auto top_up = [&]() {
+    while (ok && u_issued < u_total && u_issued < u_done + RB - 1) issue_unit();
+  };
+  auto run_unit = [&](uint32_t d, uint32_t a, bool acc) {   // thread 0
+    const int b = u_done % RB;
+    ok = tc::bar_wait(&fullb[b], (uint32_t)((u_done / RB) & 1), p.err) && ok;
+    if (ok) {
+      tc::fence_after();
+      xts::gemm_unit<KI, KO, P>(d, a, ring_s + (uint32_t)(b * G::UNIT), acc);
+      tc::mma_commit(&emptyb[b]);
+    }
+    ++u_done;
+    top_up();
+  };
+  if (tid == 0) top_up();
+
+  for (int k = 0; k < my_items; ++k) {
+    const int item = blockIdx.x + k * gridDim.x;
+    const int per_field = p.tiles * NCLS;
+    const int field = item / per_field;
+    const int within = item - field * per_field;
+    const int cls = DIR == 1 ? within / p.tiles : 0;
+    const int tile = within - cls * p.tiles;
+    const float2* src = p.src + (size_t)field * (size_t)p.src_nodes * CI;
+    float2* dst = p.dst + (size_t)field * (size_t)p.dst_nodes * CO;
+    const long long cnodes = (long long)p.cx * p.cy * p.cz;
+    const long long j = (long long)tile * xts::M + row;      // coarse-lattice node of this row
+    const bool row_ok = j < cnodes;
+    int jx, jy, jz;
+    node_xyz(row_ok ? j : 0, p.cx, p.cy, jx, jy, jz);
+    // the gathered source row of tap `tap`: fine 2J + o (restriction) or
+    // coarse j + dj (prolongation)
+    auto source = [&](int tap, long long& s) -> bool {
+      int t, o[3], dj[3];
+      xts::tap_of<D, DIR>(cls, tap, t, o, dj);
+      if constexpr (DIR == 0) {
+        const int fxx = 2 * jx + o[0], fyy = 2 * jy + o[1], fzz = 2 * jz + o[2];
+        s = ((long long)fzz * p.fy + fyy) * p.fx + fxx;
+        return row_ok && fxx >= 0 && fxx < p.fx && fyy >= 0 && fyy < p.fy && fzz >= 0 &&
+               fzz < p.fz;
+      } else {
+        const int cxx = jx + dj[0], cyy = jy + dj[1], czz = jz + dj[2];
+        s = ((long long)czz * p.cy + cyy) * p.cx + cxx;
+        return row_ok && cxx < p.cx && cyy < p.cy && czz < p.cz;
+      }
+    };
+    auto load_stage = [&](float (&v)[16], int q) {
+      long long s = 0;
+      const bool ok_n = source(q / NH, s);
+      const int c0 = (q % NH) * KU + 16 * grp;
+      const float4* qp = reinterpret_cast<const float4*>(src + s * CI + c0 / 2);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 w = ok_n ? __ldg(qp + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[4 * u] = w.x;
+        v[4 * u + 1] = w.y;
+        v[4 * u + 2] = w.z;
+        v[4 * u + 3] = w.w;
+      }
+    };
+    // The tensor cores accumulate in FP32 with truncation, an error that
+    // grows with the number of MMAs summed into one accumulator (27 taps x
+    // 3 KI / 8 of them would reach ~2e-5).  Each tap therefore sums into an
+    // accumulator of its own (taps alternate between two), and the tap
+    // partials are added here in FP32 with rounding to nearest.
+    float acc[NCH * 16];
+#pragma unroll
+    for (int i = 0; i < NCH * 16; ++i) acc[i] = 0.f;
+    auto fold = [&](int t) {
+      const uint32_t dcol = tmem + lane + (uint32_t)((t & 1) * KO);
+#pragma unroll
+      for (int i = 0; i < NCH; ++i) {
+        const int c0 = 32 * i + 16 * grp;
+        if (c0 < KO) {
+          float dv[16];
+          tc::tmem_ld16(dcol + c0, dv);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) acc[16 * i + u] += dv[u];
+        }
+      }
+    };
+    const int TAPS = item_taps(item);
+    const int Q = TAPS * NH;                // stages of this item (>= 1)
+    float va[16], vb[16];
+    load_stage(va, 0);
+    if (Q > 1) load_stage(vb, 1);
+#pragma unroll 1
+    for (int q = 0; q < Q; ++q) {
+      float(&cur)[16] = (q & 1) ? vb : va;
+      const uint32_t slot = (q & 1) ? slot1 : slot0;
+      const int tap = q / NH, h = q - tap * NH;
+      if (q >= 2) wait_a(q & 1);
+      // the MMAs of stage q - 2 and all before it are complete: tap - 2's
+      // accumulator is final and is about to be reused by this tap
+      if (h == 0 && tap >= 2) {
+        tc::fence_after();
+        fold(tap - 2);
+      }
+      xts::put16<KU, P>(slot + lane, 16 * grp, cur);
+      tc::tmem_st_wait();
+      if (q + 2 < Q) load_stage(cur, q + 2);
+      tc::fence_before();
+      ok = __syncthreads_and(ok);
+      if (!ok) goto fail;
+      if (tid == 0) {
+        tc::fence_after();
+        run_unit(tmem + (uint32_t)((tap & 1) * KO), slot, h > 0);
+        tc::mma_commit(&abar[q & 1]);
+      }
+    }
+    if (Q >= 2) wait_a((Q - 2) & 1);
+    wait_a((Q - 1) & 1);
+    tc::fence_after();
+    if (TAPS >= 2) fold(TAPS - 2);
+    fold(TAPS - 1);
+    // ---- epilogue: store the sum (restriction) or add it to the fine field
+    {
+      long long o_row;
+      if constexpr (DIR == 0) {
+        o_row = j;
+      } else {
+        const int px = cls & 1, py = (cls >> 1) & 1, pz = D == 3 ? (cls >> 2) & 1 : 0;
+        o_row = ((long long)(2 * jz + pz) * p.fy + (2 * jy + py)) * p.fx + (2 * jx + px);
+      }
+#pragma unroll
+      for (int i = 0; i < NCH; ++i) {
+        const int c0 = 32 * i + 16 * grp;
+        if (c0 < KO && row_ok) {
+          float4* op = reinterpret_cast<float4*>(dst + o_row * CO + c0 / 2);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            float4 w = make_float4(acc[16 * i + 4 * u], acc[16 * i + 4 * u + 1],
+                                   acc[16 * i + 4 * u + 2], acc[16 * i + 4 * u + 3]);
+            if constexpr (DIR == 1) {
+              const float4 e = op[u];
+              w.x += e.x;
+              w.y += e.y;
+              w.z += e.z;
+              w.w += e.w;
+            }
+            op[u] = w;
+          }
+        }
+      }
+    }
+    tc::fence_before();
+  }
+  ok = __syncthreads_and(ok);
+  if (!ok) goto fail;
+  if (warp == 0) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"((uint32_t)G::COLS));
+  }
+  return;
+
+fail:
+  if (p.err && tid == 0) atomicOr(p.err, 1);
+  if (tid == 0) {
+    for (int u = u_done; u < u_issued; ++u)
+      tc::bar_wait(&fullb[u % RB], (uint32_t)((u / RB) & 1), nullptr);
+    if (u_done > 0)
+      tc::bar_wait(&emptyb[(u_done - 1) % RB], (uint32_t)(((u_done - 1) / RB) & 1), nullptr);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"((uint32_t)G::COLS));
+  }
+}
+
+namespace {
+
+int xsm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+template <int KI, int KO, int D, int P, int DIR>
+mcmg_status xts_launch(xts::XParams p, int nrhs, cudaStream_t st) {
+  using G = xts::Cfg<KI, KO, P>;
+  auto kern = k_transfer_ts<KI, KO, D, P, DIR>;
+  static bool attr = false;
+  // ring; at most PER_SM CTAs on one SM so that their tensor memory fits
+  const size_t guard = (size_t)(228 * 1024) / (G::PER_SM + 1) + 16 - 2048;
+  size_t smem = std::max((size_t)G::RB * G::UNIT, guard);
+  smem = (smem + 127) & ~(size_t)127;
+  if (!attr) {
+    MCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    attr = true;
+  }
+  const long long cn = (long long)p.cx * p.cy * p.cz;
+  p.tiles = (int)((cn + xts::M - 1) / xts::M);
+  p.items = p.tiles * (DIR == 1 ? (1 << D) : 1) * nrhs;
+  const int grid = std::min(p.items, xsm_count() * G::PER_SM);
+  kern<<<grid, xts::THREADS, smem, st>>>(p);
+  MCMG_CHECK_LAUNCH(DIR == 0 ? "restrict_ts" : "prolong_ts");
+  return MCMG_OK;
+}
+
+template <int D, int P, int DIR>
+mcmg_status xts_pair(int CI, int CO, const xts::XParams& p, int nrhs, cudaStream_t st) {
+  // (input channels, output channels): restriction C -> C', prolongation C' -> C
+#define XTS_CASE(ci, co)                                          \
+  if (CI == ci && CO == co) return xts_launch<2 * ci, 2 * co, D, P, DIR>(p, nrhs, st);
+  if constexpr (DIR == 0) {
+    XTS_CASE(16, 32) XTS_CASE(16, 16) XTS_CASE(32, 64) XTS_CASE(32, 32) XTS_CASE(64, 64)
+  } else {
+    XTS_CASE(16, 8) XTS_CASE(16, 16) XTS_CASE(32, 16) XTS_CASE(32, 32) XTS_CASE(64, 32)
+    XTS_CASE(64, 64)
+  }
+#undef XTS_CASE
+  set_error("tensor-core transfer: no variant for %d -> %d channels", CI, CO);
+  return MCMG_ERR_SHAPE;
+}
+
+}  // namespace
+
+bool xts_supported(const Level& L, bool restrict_) {
+  if (!L.use_ts || !L.ts_R || !L.ts_P) return false;
+  const int CI = restrict_ ? L.C : L.Cn, CO = restrict_ ? L.Cn : L.C;
+  if (restrict_)
+    return (CI == 16 && (CO == 32 || CO == 16)) || (CI == 32 && (CO == 64 || CO == 32)) ||
+           (CI == 64 && CO == 64);
+  return (CI == 16 && (CO == 8 || CO == 16)) || (CI == 32 && (CO == 16 || CO == 32)) ||
+         (CI == 64 && (CO == 32 || CO == 64));
+}
+
+mcmg_status launch_transfer_ts(const Level& L, bool restrict_, const float2* src, float2* dst,
+                               int nrhs, cudaStream_t st) {
+  if (!xts_supported(L, restrict_)) {
+    set_error("tensor-core transfer not available on this level");
+    return MCMG_ERR_SHAPE;
+  }
+  const Grid gc = L.g.coarse();
+  xts::XParams p{};
+  p.src = src;
+  p.dst = dst;
+  p.mats = restrict_ ? L.ts_R : L.ts_P;
+  p.fx = L.g.nx;
+  p.fy = L.g.ny;
+  p.fz = L.g.nz;
+  p.cx = gc.nx;
+  p.cy = gc.ny;
+  p.cz = gc.nz;
+  p.src_nodes = restrict_ ? L.g.nodes() : gc.nodes();
+  p.dst_nodes = restrict_ ? gc.nodes() : L.g.nodes();
+  p.err = L.err;
+  const int CI = restrict_ ? L.C : L.Cn, CO = restrict_ ? L.Cn : L.C;
+  const bool d3 = L.g.d == 3, tf = L.ts_prec == MCMG_FP32_TC;
+  if (restrict_) {
+    if (tf) return d3 ? xts_pair<3, 1, 0>(CI, CO, p, nrhs, st) : xts_pair<2, 1, 0>(CI, CO, p, nrhs, st);
+    return d3 ? xts_pair<3, 0, 0>(CI, CO, p, nrhs, st) : xts_pair<2, 0, 0>(CI, CO, p, nrhs, st);
+  }
+  if (tf) return d3 ? xts_pair<3, 1, 1>(CI, CO, p, nrhs, st) : xts_pair<2, 1, 1>(CI, CO, p, nrhs, st);
+  return d3 ? xts_pair<3, 0, 1>(CI, CO, p, nrhs, st) : xts_pair<2, 0, 1>(CI, CO, p, nrhs, st);
+}
+
+// Host: a complex Cout x Cin matrix M[co][ci] (float2, row-major) -> its real
+// block form (N = 2 Cout rows, K = 2 Cin) as a B operand in the no-swizzle
+// K-major core-matrix layout: BF16 (chunks of 8 K-elements) or TF32 hi and lo
+// halves (chunks of 4), [hi][lo].
+void pack_ts_rect(const float2* Mc, int Cout, int Cin, bool tf32, void* out) {
+  const int N = 2 * Cout, K = 2 * Cin;
+  auto rna = [](float v) {
+    uint32_t b;
+    std::memcpy(&b, &v, 4);
+    b = (b + 0x1000u) & 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
+  };
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < K; ++k) {
+      const float2 m = Mc[(size_t)(n >> 1) * Cin + (k >> 1)];
+      float v;
+      if ((n & 1) == 0) v = (k & 1) == 0 ? m.x : -m.y;
+      else v = (k & 1) == 0 ? m.y : m.x;
+      if (tf32) {
+        float* hi = static_cast<float*>(out);
+        float* lo = hi + (size_t)N * K;
+        const size_t pos = ((size_t)(k >> 2) * N + n) * 4 + (k & 3);
+        const float h = rna(v);
+        hi[pos] = h;
+        lo[pos] = rna(v - h);
+      } else {
+        uint16_t* o = static_cast<uint16_t*>(out);
+        const __nv_bfloat16 bv = __float2bfloat16_rn(v);
+        const size_t pos = ((size_t)(k >> 3) * N + n) * 8 + (k & 7);
+        std::memcpy(o + pos, &bv, 2);
+      }
+    }
+}
+
+}  // namespace mcmg

@@ -87,6 +87,10 @@ struct Level {
   bool use_ts = false;        // smoothing step and residual on tcgen05, TMEM A operands
   int ts_prec = -1;           // MCMG_BF16 or MCMG_FP32_TC when use_ts
   const uint4* ts_mats = nullptr;  // weight matrices in the operand layout of ts_prec
+  // restriction (Cn x C) and prolongation (C x Cn) tap matrices in the same
+  // layout, for the tensor-core transfers (null where those do not apply)
+  const uint4* ts_R = nullptr;
+  const uint4* ts_P = nullptr;
   // signatures of the arithmetic of one smoothing step (stencil, K_A, K_S,
   // W^(i)) and of the residual (stencil, K_A), with precision and C: launches
   // of different handles may be batched when these agree
@@ -127,6 +131,16 @@ mcmg_status launch_smooth_ts_fields(const Level& L, int step, const TsField* fie
 // (4C^2 values), or TF32 hi and lo halves (2 * 4C^2 floats)
 void pack_ts_bf16(const float2* Mc, int C, uint16_t* out);
 void pack_ts_tf32(const float2* Mc, int C, float* out);
+
+// tensor-core restriction (restrict_ true: r_c = R t) and prolongation
+// (e += P e_c) of level L (kernels_xts.cu): available on tensor-core levels
+// whose input side has at least 16 channels.  src, dst: nrhs fields each.
+bool xts_supported(const Level& L, bool restrict_);
+mcmg_status launch_transfer_ts(const Level& L, bool restrict_, const float2* src, float2* dst,
+                               int nrhs, cudaStream_t st);
+// complex Cout x Cin matrix [co][ci] -> real block form (2 Cout x 2 Cin) as
+// a B operand: BF16 (4 Cout Cin values) or TF32 hi and lo (2 * 4 Cout Cin)
+void pack_ts_rect(const float2* Mc, int Cout, int Cin, bool tf32, void* out);
 
 // Launchers used by the V-cycle (kernels_vcycle.cu), asynchronous on `st`.
 // mode 0: e_out = e_in + S^(step)(r - A e_in); mode 1: e_out = r - A e_in.

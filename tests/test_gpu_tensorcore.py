@@ -12,6 +12,9 @@ The large cases have more 128-node tiles than the grid has CTAs, so every
 CTA walks several tiles, and node counts that are not a multiple of 128; the
 C = 32 / 64 cases run the variant that streams its weights through shared
 memory (one CTA per SM).
+The tensor-core restriction and prolongation (the last transfer shape, on
+levels whose transfer input has 16 or more channels) are held to the same
+bounds, alone, with many items per CTA, and inside V-cycles.
 Every bounded wait inside the kernels must have finished (error word 0).
 """
 import numpy as np
@@ -132,6 +135,122 @@ def test_residual_restrict(case):
         h.residual_restrict(l, dev(r), dev(e), rc, nrhs=2)
         want = np.stack([O.restrict(lv["R"], r[k] - O.op_A(lv, a, e[k])) for k in range(2)])
         assert relerr(host(rc), want) < tol, l
+
+
+def _xts_supported(C, Cn, restrict_):
+    """Channel pairs of the tensor-core transfer: input side >= 16 channels,
+    output equal to or half / twice the input (the library's model family)."""
+    ci, co = (C, Cn) if restrict_ else (Cn, C)
+    if restrict_:
+        return (ci, co) in {(16, 32), (16, 16), (32, 64), (32, 32), (64, 64)}
+    return (ci, co) in {(16, 8), (16, 16), (32, 16), (32, 32), (64, 32), (64, 64)}
+
+
+def test_transfer_every_shape(case):
+    """Restriction R_l and prolongation P_l in every kernel shape, the
+    tensor-core one (the last shape) included where the level's channels
+    allow it, against the oracle; then V-cycles with the tensor-core
+    transfers forced on every level that has them."""
+    from paper_2606_30495_b300 import mcmg
+    prec, m, h = case
+    w = m["w"]
+    L = w["levels"]
+    tol = _tols(prec)[0]
+    xts = mcmg.kernel_shape_count(mcmg.OP_RESTRICT) - 1
+    assert xts == mcmg.kernel_shape_count(mcmg.OP_PROLONG) - 1
+    ran_xts = 0
+    try:
+        for l in range(L - 1):
+            C, Cn = w["channels"][l], w["channels"][l + 1]
+            shp = tuple(n >> l for n in m["shape"])
+            cshp = tuple(n >> (l + 1) for n in m["shape"])
+            lv = w["lvl"][l]
+            r = I.complex_normal((2,) + shp + (C,), rng(70))
+            zero = torch.zeros(r.shape, dtype=torch.complex64, device="cuda")
+            want_r = np.stack([O.restrict(lv["R"], r[k]) for k in range(2)])
+            ec = I.complex_normal((2,) + cshp + (Cn,), rng(71))
+            e = I.complex_normal((2,) + shp + (C,), rng(72))
+            want_p = np.stack([e[k] + O.prolong(lv["P"], ec[k], shp) for k in range(2)])
+            for op, want in ((mcmg.OP_RESTRICT, want_r), (mcmg.OP_PROLONG, want_p)):
+                ok_xts = _xts_supported(C, Cn, op == mcmg.OP_RESTRICT)
+                for sh in range(mcmg.kernel_shape_count(op)):
+                    ran = h.set_kernel_shape(l, op, sh)
+                    if sh == xts:
+                        assert ran == ok_xts, (l, op, C, Cn)
+                    if not ran:
+                        continue
+                    if op == mcmg.OP_RESTRICT:
+                        rc = torch.zeros((2,) + cshp + (Cn,), dtype=torch.complex64, device="cuda")
+                        h.residual_restrict(l, dev(r), zero, rc, nrhs=2)
+                        got = host(rc)
+                    else:
+                        ef = dev(e)
+                        h.prolong_add(l, dev(ec), ef, nrhs=2)
+                        got = host(ef)
+                    assert relerr(got, want) < tol, (l, op, sh)
+                    ran_xts += sh == xts
+                h.set_kernel_shape(l, op, -1)
+        if any(_xts_supported(w["channels"][l], w["channels"][l + 1], rr)
+               for l in range(L - 1) for rr in (True, False)):
+            assert ran_xts > 0
+            for l in range(L - 1):
+                for op in (mcmg.OP_RESTRICT, mcmg.OP_PROLONG):
+                    h.set_kernel_shape(l, op, xts)   # False where not available
+            rv = I.complex_normal((2,) + m["shape"], rng(73))
+            want_v = np.stack([O.vcycle(w, m["feats"], ri) for ri in rv])
+            ev = torch.zeros(rv.shape, dtype=torch.complex64, device="cuda")
+            h.vcycle(dev(rv), ev, nrhs=2)
+            assert relerr(host(ev), want_v) < _tols(prec)[1]
+        assert h.device_error() == 0
+    finally:
+        for l in range(L - 1):
+            for op in (mcmg.OP_RESTRICT, mcmg.OP_PROLONG):
+                h.set_kernel_shape(l, op, -1)
+
+
+@pytest.mark.parametrize("prec,shape,channels", [
+    ("fp32tc", (94, 80, 70), [16, 32]),     # restriction 514.1 tiles, prolongation 8 classes
+    ("bf16", (94, 80, 70), [32, 32]),
+    ("fp32tc", (62, 48, 40), [64, 64]),     # four K parts per tap (TF32)
+    ("fp32tc", (500, 330), [16, 32]),       # 2D: 322.3 tiles, 4 classes
+    ("bf16", (500, 330), [16, 16]),
+])
+def test_transfer_ts_many_items(ctx, prec, shape, channels):
+    """The tensor-core transfers with more items than CTAs (each persistent
+    CTA walks several tiles and parity classes) and a ragged last tile,
+    nrhs = 2, against the oracle.  Setup features are not needed: the
+    restriction is taken through the residual with e = 0."""
+    from paper_2606_30495_b300 import mcmg
+    d = len(shape)
+    pre, post = I.nu_schedule(2)
+    w = I.make_weights(d, list(channels), pre, post, mode="random", seed=9)
+    c = I.grf(shape, 4.0, 1.0, 3.0, rng(109))
+    omega = I.omega_for_ppw(c.min(), 8.0, shape[0])
+    h = mcmg.Handle(ctx, c, omega, 4, 1.0, w, precision=_prec(prec))
+    xts = mcmg.kernel_shape_count(mcmg.OP_RESTRICT) - 1
+    try:
+        C, Cn = channels
+        lv = w["lvl"][0]
+        cshp = tuple(n >> 1 for n in shape)
+        tol = _tols(prec)[0]
+        if _xts_supported(C, Cn, True):
+            assert h.set_kernel_shape(0, mcmg.OP_RESTRICT, xts)
+            r = I.complex_normal((2,) + shape + (C,), rng(80))
+            rc = torch.zeros((2,) + cshp + (Cn,), dtype=torch.complex64, device="cuda")
+            h.residual_restrict(0, dev(r), torch.zeros(r.shape, dtype=torch.complex64,
+                                                       device="cuda"), rc, nrhs=2)
+            want = np.stack([O.restrict(lv["R"], r[k]) for k in range(2)])
+            assert relerr(host(rc), want) < tol
+        assert h.set_kernel_shape(0, mcmg.OP_PROLONG, xts)
+        ec = I.complex_normal((2,) + cshp + (Cn,), rng(81))
+        e = I.complex_normal((2,) + shape + (C,), rng(82))
+        ef = dev(e)
+        h.prolong_add(0, dev(ec), ef, nrhs=2)
+        want = np.stack([e[k] + O.prolong(lv["P"], ec[k], shape) for k in range(2)])
+        assert relerr(host(ef), want) < tol
+        assert h.device_error() == 0
+    finally:
+        h.close()
 
 
 def test_vcycle(case):
