@@ -257,6 +257,52 @@ def time_smoothing(h, wl, torch, stream, reps=20):
     return fams, detail
 
 
+def time_transfers(h, wl, torch, stream, reps=20):
+    """CUDA-event time of the restriction and prolongation of every level, as
+    the V-cycle runs them (setup's kernel shapes), through the C ABI on
+    `stream`: the prolongation alone (mcmg_prolong_add), the restriction as
+    residual + restriction less the residual.  Algorithmic bytes: the input
+    read once and the output written (and, prolongation, read) once;
+    flops: 8 flops per complex MAC over the 3^d taps of every coarse node."""
+    d = wl["dim"]
+    T3 = 3 ** d
+    out = []
+    for l in range(wl["levels"] - 1):
+        C, Cn = wl["channels"][l], wl["channels"][l + 1]
+        shp = tuple(n >> l for n in (wl["n"],) * d)
+        cshp = tuple(n >> (l + 1) for n in (wl["n"],) * d)
+        nf, nc = math.prod(shp), math.prod(cshp)
+        r = torch.randn(shp + (C,), dtype=torch.complex64, device="cuda")
+        e = torch.randn(shp + (C,), dtype=torch.complex64, device="cuda")
+        t = torch.empty_like(e)
+        rc = torch.empty(cshp + (Cn,), dtype=torch.complex64, device="cuda")
+        ec = torch.randn(cshp + (Cn,), dtype=torch.complex64, device="cuda")
+
+        def timed(run):
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    run()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    run()
+                e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / 1e3 / reps
+
+        t_res = timed(lambda: h.residual(l, r, e, t, stream=stream))
+        t_rr = timed(lambda: h.residual_restrict(l, r, e, rc, stream=stream))
+        t_p = timed(lambda: h.prolong_add(l, ec, e, stream=stream))
+        fl = 8.0 * T3 * C * Cn * nc
+        for kind, sec, by, op in (("restrict", max(t_rr - t_res, 1e-9), 8.0 * (C * nf + Cn * nc), 2),
+                                  ("prolong", t_p, 8.0 * (Cn * nc + 2 * C * nf), 3)):
+            sh = h.kernel_shape(l, op)
+            out.append(dict(level=l, C=C, Cn=Cn, kind=kind, shape=sh, us=sec * 1e6,
+                            tflops=fl / sec / 1e12, gbs=by / sec / 1e9))
+    return out
+
+
 def sample_size(wl):
     """Grid size of the oracle's sample: the workload's own up to 2^18 nodes,
     else a 4x coarser copy of the same recipe."""
@@ -641,6 +687,9 @@ def main():
     roof["families"] = {k: dict(v, share=v["s"] / sum(x["s"] for x in fams.values()))
                         for k, v in fams.items()}
     roof["detail"] = detail
+    transfers = time_transfers(h, wl, torch, stream)
+    t_smooth = sum(x["us"] * x["count"] for x in detail) * 1e-6
+    t_xfer = sum(x["us"] for x in transfers) * 1e-6
 
     # end to end through the C ABI with host buffers (copies inside the call)
     f_pin = torch.from_numpy(f_host).pin_memory()
@@ -716,6 +765,15 @@ def main():
         "peaks_source": pk_src,
         "fp32_ffma_tflops_measured": ffma_peak,
         "kernel_shapes": kernel_shapes,
+        "transfers": transfers,
+        # one V-cycle, warm, each class timed alone: smoothing steps and
+        # residuals, restrictions and prolongations, the rest (lift,
+        # projection, launch gaps); and the FGMRES work per iteration beside it
+        "breakdown_ms": {"vcycle": 1e3 * vc_s, "smoothing": 1e3 * t_smooth,
+                         "transfers": 1e3 * t_xfer,
+                         "vcycle_other": 1e3 * (vc_s - t_smooth - t_xfer),
+                         "iteration": 1e3 * total / max(1, sum(iters)),
+                         "krylov_and_A": 1e3 * (total / max(1, sum(iters)) - vc_s)},
     }
     if bf16:
         out["bf16"] = bf16

@@ -822,15 +822,20 @@ fail:
 
 // ---------------------------------------------------------------------------
 // Large channel counts (K2 = 64 with TF32x3, K2 = 128 with either precision):
-// the weights no longer fit shared memory, so they stream through it.  One
-// CTA per SM (its TMEM columns fill the SM) of 256 threads: thread t owns row
-// 32 (w % 4) + lane of warp w and every other 16-column chunk of it (warps
-// 0-3 the even chunks, 4-7 the odd ones).  Each stencil tap is one A stage
-// (two K-halves for TF32x3 at K2 = 128, so that two A slots fit beside X and
-// Y); the weight matrices arrive per (matrix, K-half) unit in a ring of RB
-// shared-memory buffers filled by bulk asynchronous copies (thread 0,
-// transaction-count mbarriers); a buffer is refilled once the MMAs that read
-// it have committed.  The arithmetic and the phases are those above.
+// the weights no longer fit shared memory, so they stream through it.  CTAs
+// of 256 threads, as many per SM as their TMEM columns allow (two at K2 = 64,
+// one at K2 = 128): thread t owns row 32 (w % 4) + lane of warp w and every
+// other 16-column chunk of it (warps 0-3 the even chunks, 4-7 the odd ones).
+// Each stencil tap is one A stage, or two K-halves for TF32x3 so that two A
+// slots fit beside X and Y.  The stage loop handles two stages per iteration
+// so that the two register buffers are named statically: a buffer's loads,
+// issued two stages ahead, stay in flight until it is converted (a buffer
+// chosen at run time made the compiler wait for each load at once).  The
+// weight matrices arrive per (matrix, K-half) unit in a ring of RB
+// shared-memory buffers filled by bulk asynchronous copies with
+// transaction-count mbarriers; thread 32 issues them after each block
+// barrier, beside thread 0's MMAs, and a buffer is refilled once the MMAs
+// that read it have committed.  The arithmetic and the phases are those above.
 // ---------------------------------------------------------------------------
 namespace ts {
 
@@ -995,22 +1000,33 @@ __global__ void __launch_bounds__(256, ts::Big<K2, P>::PER_SM) k_smooth_tsb(TsPa
     ++u_issued;
     if (++ui_idx == UPT) ui_idx = 0;
   };
-  auto top_up = [&]() {                // thread 0
-    while (ok && u_issued < u_total && u_issued < u_done + RB - 1) issue_unit();
+  // Thread 32 issues the copies, right after each block barrier, so that
+  // thread 0 only waits for weights and issues MMAs.  u_seen counts the
+  // units consumed before that barrier; a refill waits for the MMAs of unit
+  // u_issued - RB <= u_seen - 2, which thread 0 issued before the barrier.
+  int u_seen = 0;
+  auto produce = [&](int consumed_now) {   // every thread; only thread 32 acts
+    if (tid == 32)
+      while (ok && u_issued < u_total && u_issued < u_seen + RB - 1) issue_unit();
+    u_seen += consumed_now;
   };
   // MMAs of the next unit (thread 0): A at a, target d
+  int u_fail = -1;                     // a unit whose arrival thread 0 gave up on
   auto run_unit = [&](uint32_t d, uint32_t a, bool acc) {
     const int b = u_done % RB;
-    ok = tc::bar_wait(&fullb[b], (uint32_t)((u_done / RB) & 1), p.err) && ok;
+    if (!tc::bar_wait(&fullb[b], (uint32_t)((u_done / RB) & 1), p.err)) {
+      ok = false;
+      u_fail = u_done;
+    }
     if (ok) {
       tc::fence_after();
       ts::gemm_unit<K2, P>(d, a, ring_s + (uint32_t)(b * B::UNIT), acc);
       tc::mma_commit(&emptyb[b]);
     }
     ++u_done;
-    top_up();
   };
-  if (tid == 0) top_up();
+  if (tid == 32)
+    while (ok && u_issued < u_total && u_issued < RB - 1) issue_unit();
 
   for (int k = 0; k < my_tiles; ++k) {
     const int item = blockIdx.x + k * gridDim.x;
@@ -1078,11 +1094,10 @@ __global__ void __launch_bounds__(256, ts::Big<K2, P>::PER_SM) k_smooth_tsb(TsPa
       float va[CPT * 16], vb[CPT * 16];
       load_stage(va, 0, 0);
       load_stage(vb, (1 / NH), 1 % NH);
-#pragma unroll 1
-      for (int q = 0; q < Q; ++q) {
-        float(&cur)[CPT * 16] = (q & 1) ? vb : va;
+      // two stages per iteration, so that each register buffer is named
+      // statically and its loads stay in flight until the buffer is used
+      auto stage = [&](int q, float (&cur)[CPT * 16], uint32_t slot) -> bool {
         const int j = q / NH, h = q % NH;
-        const uint32_t slot = (q & 1) ? slot1 : slot0;
         if (q >= 2) wait_a(q & 1);                 // MMAs of stage q-2 have read this slot
 #pragma unroll
         for (int i = 0; i < CPT; ++i) ts::put16<KU, P>(slot + lane, 32 * i + 16 * grp, cur + 16 * i);
@@ -1090,13 +1105,23 @@ __global__ void __launch_bounds__(256, ts::Big<K2, P>::PER_SM) k_smooth_tsb(TsPa
         if (q + 2 < Q) load_stage(cur, (q + 2) / NH, (q + 2) % NH);
         tc::fence_before();
         ok = __syncthreads_and(ok);
-        if (!ok) goto fail;
+        if (!ok) return false;
+        produce(j == 0 ? 2 : 1);
         if (tid == 0) {
           tc::fence_after();
           run_unit(tX, slot, q > 0);
           if (j == 0) run_unit(tY, slot, h > 0);
           tc::mma_commit(&abar[q & 1]);
         }
+        return true;
+      };
+      {
+        int q = 0;
+        for (; q + 1 < Q; q += 2) {
+          if (!stage(q, va, slot0)) goto fail;
+          if (!stage(q + 1, vb, slot1)) goto fail;
+        }
+        if (q < Q && !stage(q, va, slot0)) goto fail;
       }
       wait_a(Q >= 2 ? ((Q - 2) & 1) : 0);
       wait_a((Q - 1) & 1);
@@ -1146,6 +1171,7 @@ __global__ void __launch_bounds__(256, ts::Big<K2, P>::PER_SM) k_smooth_tsb(TsPa
       tc::fence_before();
       ok = __syncthreads_and(ok);
       if (!ok) goto fail;
+      produce(NH);
       if (tid == 0) {
         tc::fence_after();
         for (int h = 0; h < NH; ++h) run_unit(tX, (NH == 2 && h) ? slot1 : slot0, h > 0);
@@ -1175,6 +1201,7 @@ __global__ void __launch_bounds__(256, ts::Big<K2, P>::PER_SM) k_smooth_tsb(TsPa
       tc::fence_before();
       ok = __syncthreads_and(ok);
       if (!ok) goto fail;
+      produce(NH);
       if (tid == 0) {
         tc::fence_after();
         for (int h = 0; h < NH; ++h) run_unit(tY, NH == 2 ? (h ? slot1 : slot0) : slot1, h > 0);
@@ -1211,9 +1238,13 @@ fail:
   // a bounded wait ran out: record it; thread 0 lets its weight copies land
   // and its MMAs finish (bounded), then the tensor memory is released
   if (p.err && tid == 0) atomicOr(p.err, 1);
-  if (tid == 0) {
-    for (int u = u_done; u < u_issued; ++u)
+  if (tid == 32) {                     // copies not consumed yet
+    for (int u = u_seen; u < u_issued; ++u)
       tc::bar_wait(&fullb[u % RB], (uint32_t)((u / RB) & 1), nullptr);
+  }
+  if (tid == 0) {
+    if (u_fail >= 0)
+      tc::bar_wait(&fullb[u_fail % RB], (uint32_t)((u_fail / RB) & 1), nullptr);
     if (u_done > 0)
       tc::bar_wait(&emptyb[(u_done - 1) % RB], (uint32_t)(((u_done - 1) / RB) & 1), nullptr);
   }

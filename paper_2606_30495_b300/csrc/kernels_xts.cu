@@ -17,11 +17,14 @@
 // The structure is that of the streamed-weight smoothing step (kernels_ts.cu):
 // 256 threads, thread t owning row 32 (w % 4) + lane of warp w and every
 // other 16-column chunk of it; each (tap, K-part) is one A stage gathered
-// into registers two stages ahead, converted and written to one of two A
-// slots in tensor memory; the weight matrices stream per (tap, K-part) unit
-// through a ring of shared-memory buffers filled by bulk asynchronous copies;
-// one thread issues the MMAs into the accumulator D.  The epilogue stores D
-// (restriction) or adds it to the fine field (prolongation).  Every mbarrier
+// into registers two stages ahead (two stages per loop iteration, so that
+// both register buffers are named statically), converted and written to one
+// of two A slots in tensor memory; the weight matrices stream per (tap,
+// K-part) unit through a ring of shared-memory buffers filled by bulk
+// asynchronous copies that thread 32 issues; thread 0 issues the MMAs.  Each
+// tap accumulates apart and the tap partials are summed in FP32 registers;
+// the epilogue stores the sum (restriction) or adds it to the fine field
+// (prolongation).  Every mbarrier
 // wait is bounded and the block votes on the outcome at its next barrier.
 #include <algorithm>
 #include <cstring>
@@ -248,21 +251,32 @@ __global__ void __launch_bounds__(xts::THREADS, xts::Cfg<KI, KO, P>::PER_SM)
     ++u_issued;
     if (++ui_idx == item_taps(item) * NH) { ui_idx = 0; ++ui_k; }
   };
-  auto top_up = [&]() {
-    while (ok && u_issued < u_total && u_issued < u_done + RB - 1) issue_unit();
+  // thread 32 issues the copies after each block barrier (one unit per
+  // stage); u_seen counts the units consumed before that barrier, and a
+  // refill waits for the MMAs of unit u_issued - RB <= u_seen - 2, which
+  // thread 0 issued before the barrier
+  int u_seen = 0;
+  auto produce = [&]() {               // every thread; only thread 32 acts
+    if (tid == 32)
+      while (ok && u_issued < u_total && u_issued < u_seen + RB - 1) issue_unit();
+    ++u_seen;
   };
+  int u_fail = -1;                     // a unit whose arrival thread 0 gave up on
   auto run_unit = [&](uint32_t d, uint32_t a, bool acc) {   // thread 0
     const int b = u_done % RB;
-    ok = tc::bar_wait(&fullb[b], (uint32_t)((u_done / RB) & 1), p.err) && ok;
+    if (!tc::bar_wait(&fullb[b], (uint32_t)((u_done / RB) & 1), p.err)) {
+      ok = false;
+      u_fail = u_done;
+    }
     if (ok) {
       tc::fence_after();
       xts::gemm_unit<KI, KO, P>(d, a, ring_s + (uint32_t)(b * G::UNIT), acc);
       tc::mma_commit(&emptyb[b]);
     }
     ++u_done;
-    top_up();
   };
-  if (tid == 0) top_up();
+  if (tid == 32)
+    while (ok && u_issued < u_total && u_issued < RB - 1) issue_unit();
 
   for (int k = 0; k < my_items; ++k) {
     const int item = blockIdx.x + k * gridDim.x;
@@ -331,14 +345,10 @@ __global__ void __launch_bounds__(xts::THREADS, xts::Cfg<KI, KO, P>::PER_SM)
     };
     const int TAPS = item_taps(item);
     const int Q = TAPS * NH;                // stages of this item (>= 1)
-    float va[16], vb[16];
-    load_stage(va, 0);
-    if (Q > 1) load_stage(vb, 1);
-#pragma unroll 1
-    for (int q = 0; q < Q; ++q) {
-      float(&cur)[16] = (q & 1) ? vb : va;
-      const uint32_t slot = (q & 1) ? slot1 : slot0;
-      const int tap = q / NH, h = q - tap * NH;
+    // two stages per iteration, so that each register buffer is named
+    // statically and its loads stay in flight until the buffer is used
+    auto stage = [&](int q, float (&cur)[16], uint32_t slot) -> bool {
+      const int tap = q / NH, h = q - (q / NH) * NH;
       if (q >= 2) wait_a(q & 1);
       // the MMAs of stage q - 2 and all before it are complete: tap - 2's
       // accumulator is final and is about to be reused by this tap
@@ -351,12 +361,25 @@ __global__ void __launch_bounds__(xts::THREADS, xts::Cfg<KI, KO, P>::PER_SM)
       if (q + 2 < Q) load_stage(cur, q + 2);
       tc::fence_before();
       ok = __syncthreads_and(ok);
-      if (!ok) goto fail;
+      if (!ok) return false;
+      produce();
       if (tid == 0) {
         tc::fence_after();
         run_unit(tmem + (uint32_t)((tap & 1) * KO), slot, h > 0);
         tc::mma_commit(&abar[q & 1]);
       }
+      return true;
+    };
+    float va[16], vb[16];
+    load_stage(va, 0);
+    if (Q > 1) load_stage(vb, 1);
+    {
+      int q = 0;
+      for (; q + 1 < Q; q += 2) {
+        if (!stage(q, va, slot0)) goto fail;
+        if (!stage(q + 1, vb, slot1)) goto fail;
+      }
+      if (q < Q && !stage(q, va, slot0)) goto fail;
     }
     if (Q >= 2) wait_a((Q - 2) & 1);
     wait_a((Q - 1) & 1);
@@ -406,9 +429,13 @@ __global__ void __launch_bounds__(xts::THREADS, xts::Cfg<KI, KO, P>::PER_SM)
 
 fail:
   if (p.err && tid == 0) atomicOr(p.err, 1);
-  if (tid == 0) {
-    for (int u = u_done; u < u_issued; ++u)
+  if (tid == 32) {                     // copies not consumed yet
+    for (int u = u_seen; u < u_issued; ++u)
       tc::bar_wait(&fullb[u % RB], (uint32_t)((u / RB) & 1), nullptr);
+  }
+  if (tid == 0) {
+    if (u_fail >= 0)
+      tc::bar_wait(&fullb[u_fail % RB], (uint32_t)((u_fail / RB) & 1), nullptr);
     if (u_done > 0)
       tc::bar_wait(&emptyb[(u_done - 1) % RB], (uint32_t)(((u_done - 1) / RB) & 1), nullptr);
   }
