@@ -369,9 +369,14 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Cfg<K2, P>::PER_SM) k_smooth_
       return row_ok && c + sgn >= 0 && c + sgn < ext;
     };
 
+    // Two register rows: the stencil taps two ahead, and after the last two
+    // taps the epilogue operands (r and a, then s and e) as soon as a row
+    // frees up, so that their loads overlap the MMAs and the other epilogues.
+    float va[K2], vb[K2];
+    float(&rbuf)[K2] = ((NT - 2) & 1) ? vb : va;      // r, then s
+    float(&abuf)[K2] = ((NT - 1) & 1) ? vb : va;      // a, then e
     if (ein) {
       // ---- phase 1: X = sum_tap E_tap W~_tap^T, Y = E_0 K~_A^T
-      float va[K2], vb[K2];
       {
         long long nb;
         bool v = nbr(0, nb);
@@ -391,6 +396,8 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Cfg<K2, P>::PER_SM) k_smooth_
           long long nb;
           const bool v = nbr(j + 2, nb);
           ts::load_row<K2>(cur, ein, nb, v);
+        } else {
+          ts::load_row<K2>(cur, j == NT - 2 ? r : tv.a, nc, true);   // rbuf, abuf
         }
         tc::fence_before();
         ok = __syncthreads_and(ok);
@@ -408,11 +415,11 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Cfg<K2, P>::PER_SM) k_smooth_
       // ---- epilogue 1: t = r - X - a (.) Y
 #pragma unroll
       for (int c0 = 0; c0 < K2; c0 += 16) {
-        float xv[16], yv[16], rv[16], av[16], t[16];
+        float xv[16], yv[16], t[16];
+        const float* rv = rbuf + c0;
+        const float* av = abuf + c0;
         tc::tmem_ld16(tX + lane + c0, xv);
         tc::tmem_ld16(tY + lane + c0, yv);
-        ts::load16(rv, r, C, nc, c0);
-        ts::load16(av, tv.a, C, nc, c0);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           t[2 * k] = rv[2 * k] - xv[2 * k] - (av[2 * k] * yv[2 * k] - av[2 * k + 1] * yv[2 * k + 1]);
@@ -429,16 +436,19 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Cfg<K2, P>::PER_SM) k_smooth_
           ts::put16<K2, P>(slot0 + lane, c0, t);
         }
       }
+      if constexpr (MODE == 0) {
+        ts::load_row<K2>(rbuf, tv.s, nc, true);     // s for epilogue 2
+        ts::load_row<K2>(abuf, ein, nc, true);      // e for epilogue 3
+      }
     } else {
       // first pre-smoothing step: t = r
+      ts::load_row<K2>(abuf, r, nc, true);
+      ts::load_row<K2>(rbuf, tv.s, nc, true);
 #pragma unroll
       for (int c0 = 0; c0 < K2; c0 += 16) {
         float rv[16];
-        ts::load16(rv, r, C, nc, c0);
-        if (!row_ok) {
 #pragma unroll
-          for (int k = 0; k < 16; ++k) rv[k] = 0.f;
-        }
+        for (int k = 0; k < 16; ++k) rv[k] = row_ok ? abuf[c0 + k] : 0.f;
         ts::put16<K2, P>(slot0 + lane, c0, rv);
       }
     }
@@ -458,9 +468,9 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Cfg<K2, P>::PER_SM) k_smooth_
       tc::fence_after();
 #pragma unroll
       for (int c0 = 0; c0 < K2; c0 += 16) {
-        float zv[16], sv[16], zz[16];
+        float zv[16], zz[16];
+        const float* sv = rbuf + c0;
         tc::tmem_ld16(tX + lane + c0, zv);
-        ts::load16(sv, tv.s, C, nc, c0);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           zz[2 * k] = sv[2 * k] * zv[2 * k] - sv[2 * k + 1] * zv[2 * k + 1];
@@ -489,10 +499,8 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Cfg<K2, P>::PER_SM) k_smooth_
         float uv[16];
         tc::tmem_ld16(tY + lane + c0, uv);
         if (ein) {
-          float ev[16];
-          ts::load16(ev, ein, C, nc, c0);
 #pragma unroll
-          for (int k = 0; k < 16; ++k) uv[k] += ev[k];
+          for (int k = 0; k < 16; ++k) uv[k] += abuf[c0 + k];
         }
         if (row_ok) ts::store16(out, C, n, c0, uv);
       }
