@@ -522,11 +522,29 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
       const size_t per = (tf ? 2 * sizeof(float) : sizeof(uint16_t)) * (size_t)(2 * C) * (2 * Cn);
       std::vector<unsigned char> hr(per * T3), hp(per * T3);
       std::vector<float2> mat((size_t)C * Cn);
+      if (C == 8) {
+        // restriction from 8 channels runs two taps per stage: matrix k is
+        // [R_2k | R_2k+1] (Cn x 16, the second zero past the last tap)
+        const int npair = (T3 + 1) / 2;
+        const size_t per2 = (tf ? 2 * sizeof(float) : sizeof(uint16_t)) * (size_t)32 * (2 * Cn);
+        hr.assign(per2 * npair, 0);
+        std::vector<float2> pm((size_t)Cn * 16);
+        for (int k = 0; k < npair; ++k) {
+          for (int co = 0; co < Cn; ++co)
+            for (int ci = 0; ci < 16; ++ci) {
+              const int t = 2 * k + (ci >> 3);
+              const double* rs = lb[l].R + (size_t)2 * ((size_t)t * Cn * C + (size_t)co * C + (ci & 7));
+              pm[(size_t)co * 16 + ci] =
+                  t < T3 ? make_float2((float)rs[0], (float)rs[1]) : make_float2(0.f, 0.f);
+            }
+          pack_ts_rect(pm.data(), Cn, 16, tf, hr.data() + per2 * k);
+        }
+      }
       for (int t = 0; t < T3; ++t) {
         const double* rs = lb[l].R + (size_t)2 * t * Cn * C;
         for (size_t i = 0; i < (size_t)C * Cn; ++i)
           mat[i] = make_float2((float)rs[2 * i], (float)rs[2 * i + 1]);
-        pack_ts_rect(mat.data(), Cn, C, tf, hr.data() + per * t);
+        if (C != 8) pack_ts_rect(mat.data(), Cn, C, tf, hr.data() + per * t);
         const double* ps = lb[l].P + (size_t)2 * t * C * Cn;
         for (size_t i = 0; i < (size_t)C * Cn; ++i)
           mat[i] = make_float2((float)ps[2 * i], (float)ps[2 * i + 1]);
@@ -540,6 +558,39 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
       MCMG_CUDA(cudaMemcpy(dp, hp.data(), hp.size(), cudaMemcpyHostToDevice));
       lv.ts_R = dr;
       lv.ts_P = dp;
+      if (xts_block_pair(lv.g.d, Cn, C)) {
+        // source s: rows [p C, (p + 1) C) hold P_o, o = p - 2 s per axis, for
+        // every class p that reads s (s_a <= p_a), zeros for the others
+        const int ncls = 1 << lv.g.d;
+        const size_t perb = (tf ? 2 * sizeof(float) : sizeof(uint16_t)) * (size_t)(2 * Cn) *
+                            (2 * C * ncls);
+        std::vector<unsigned char> hb(perb * ncls);
+        std::vector<float2> sm((size_t)ncls * C * Cn);
+        for (int sv = 0; sv < ncls; ++sv) {
+          for (int pc = 0; pc < ncls; ++pc) {
+            int t = 0, mul = 1;
+            bool used = true;
+            for (int a = 0; a < lv.g.d; ++a, mul *= 3) {
+              const int pa = (pc >> a) & 1, sa = (sv >> a) & 1;
+              if (sa > pa) used = false;
+              const int o = pa ? (sa ? -1 : 1) : 0;
+              t += (o + 1) * mul;
+            }
+            const double* ps = lb[l].P + (size_t)2 * t * C * Cn;
+            for (int cf = 0; cf < C; ++cf)
+              for (int cc = 0; cc < Cn; ++cc) {
+                const size_t i = (size_t)cf * Cn + cc;
+                sm[((size_t)pc * C + cf) * Cn + cc] =
+                    used ? make_float2((float)ps[2 * i], (float)ps[2 * i + 1]) : make_float2(0.f, 0.f);
+              }
+          }
+          pack_ts_rect(sm.data(), ncls * C, Cn, tf, hb.data() + perb * sv);
+        }
+        uint4* db = nullptr;
+        if ((s = dev_alloc(h, h->arena, (void**)&db, hb.size()))) return cleanup(), s;
+        MCMG_CUDA(cudaMemcpy(db, hb.data(), hb.size(), cudaMemcpyHostToDevice));
+        lv.ts_Pb = db;
+      }
     }
   }
   {

@@ -783,9 +783,11 @@ static constexpr TShape kTShapes[] = {{0, 0, 0}, {1, 4, 4}, {2, 4, 4}, {1, 4, 8}
                                      {1, 4, 2}, {1, 2, -1}, {1, 4, -1}, {1, 8, -1}};
 static constexpr int kNumTShapes = sizeof(kTShapes) / sizeof(kTShapes[0]);
 // The shape after the table: the tensor-core transfer (kernels_xts.cu), on
-// tensor-core levels whose input side has at least 16 channels.
+// tensor-core levels whose input side has at least 16 channels (restriction: 8).
 static constexpr int kXtsShape = kNumTShapes;
-static constexpr int kNumXShapes = kNumTShapes + 1;
+// and, prolongation only, the block form of it (all parity classes at once)
+static constexpr int kXtsBlockShape = kNumTShapes + 1;
+static constexpr int kNumXShapes = kNumTShapes + 2;
 
 // Register-tiled transfers are built for channel pairs (fine, coarse) with
 // the coarse count equal to or twice the fine one; other pairs use shape 0.
@@ -867,6 +869,7 @@ static TransferParams transfer_params(const Level& L, bool restrict_, const floa
 static bool xshape_ok(int s, const Level& L, bool restrict_) {
   if (s == 0) return true;
   if (s == kXtsShape) return xts_supported(L, restrict_);
+  if (s == kXtsBlockShape) return !restrict_ && xts_block_supported(L);
   if (!xt_pair(L.C, L.Cn)) return false;
   const TShape& k = kTShapes[s];
   const int CI = restrict_ ? L.C : L.Cn, CO = restrict_ ? L.Cn : L.C;
@@ -877,6 +880,7 @@ static bool xshape_ok(int s, const Level& L, bool restrict_) {
 static mcmg_status transfer_run(const Level& L, const TransferParams& p, bool restrict_, int shape,
                                 int nrhs, cudaStream_t st) {
   if (shape == kXtsShape) return launch_transfer_ts(L, restrict_, p.src, p.dst, nrhs, st);
+  if (shape == kXtsBlockShape) return launch_prolong_block_ts(L, p.src, p.dst, nrhs, st);
   if (shape > 0)
     return transfer_rt_launch(p, L.C, L.Cn, L.g.d, restrict_, kTShapes[shape].tn,
                               kTShapes[shape].cv, kTShapes[shape].kq, nrhs, st);

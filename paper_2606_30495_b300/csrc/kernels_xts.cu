@@ -59,6 +59,10 @@ struct Cfg {
   static_assert(KI % KU == 0 && RB >= 2 && NEED <= COLS, "transfer shape");
 };
 
+// K of one stage's weight matrix: a tap's 2 C_in, or two taps' for the
+// restriction from 8 channels
+__host__ __device__ constexpr int stage_k(int ki, int dir) { return dir == 0 && ki == 16 ? 32 : ki; }
+
 struct XParams {
   const float2* src;      // restriction: fine x; prolongation: coarse e_c
   float2* dst;            // restriction: coarse r_c (written); prolongation: fine e (+=)
@@ -172,9 +176,14 @@ __host__ __device__ constexpr int popc_cls(int cls) {
 }  // namespace xts
 
 template <int KI, int KO, int D, int P, int DIR>
-__global__ void __launch_bounds__(xts::THREADS, xts::Cfg<KI, KO, P>::PER_SM)
+__global__ void __launch_bounds__(xts::THREADS, xts::Cfg<xts::stage_k(KI, DIR), KO, P>::PER_SM)
     k_transfer_ts(xts::XParams p) {
-  using G = xts::Cfg<KI, KO, P>;
+  // restriction from 8 channels: two taps per stage, each thread group (grp)
+  // gathering the 16 floats of one of the two fine rows, against the pair's
+  // matrices concatenated along K (KI = 16 per tap, 32 per stage)
+  constexpr bool PAIR = DIR == 0 && KI == 16;
+  constexpr int KIE = xts::stage_k(KI, DIR);       // K of one stage's weights
+  using G = xts::Cfg<KIE, KO, P>;
   constexpr int CI = KI / 2, CO = KO / 2;
   constexpr int NH = G::NH, KU = G::KU, RB = G::RB, NCH = G::NCH;
   constexpr int T3 = D == 3 ? 27 : 9;
@@ -224,7 +233,7 @@ __global__ void __launch_bounds__(xts::THREADS, xts::Cfg<KI, KO, P>::PER_SM)
     else return (item / p.tiles) % NCLS;
   };
   auto item_taps = [&](int item) -> int {
-    if constexpr (DIR == 0) return T3;
+    if constexpr (DIR == 0) return PAIR ? (T3 + 1) / 2 : T3;
     else return 1 << xts::popc_cls<D>(item_class(item));
   };
   // ---- weight stream (thread 0): units (tap, K part) of every item in order
@@ -239,14 +248,14 @@ __global__ void __launch_bounds__(xts::THREADS, xts::Cfg<KI, KO, P>::PER_SM)
       ok = tc::bar_wait(&emptyb[b], (uint32_t)(((u_issued / RB) - 1) & 1), p.err) && ok;
     const int item = blockIdx.x + ui_k * gridDim.x;
     const int tap = ui_idx / NH, h = ui_idx % NH;
-    int t, o[3], dj[3];
-    xts::tap_of<D, DIR>(item_class(item), tap, t, o, dj);
+    int t = tap, o[3], dj[3];
+    if constexpr (!PAIR) xts::tap_of<D, DIR>(item_class(item), tap, t, o, dj);
     const uint8_t* src = reinterpret_cast<const uint8_t*>(p.mats) + (size_t)t * G::MATB;
     const uint32_t dst = ring_s + (uint32_t)(b * G::UNIT);
     xts::expect_tx(&fullb[b], (uint32_t)G::UNIT);
     xts::bulk_copy(dst, src + (size_t)h * G::SUB, G::SUB, &fullb[b]);
     if constexpr (P == 1)
-      xts::bulk_copy(dst + G::SUB, src + (size_t)KO * KI * 4 + (size_t)h * G::SUB, G::SUB,
+      xts::bulk_copy(dst + G::SUB, src + (size_t)KO * KIE * 4 + (size_t)h * G::SUB, G::SUB,
                      &fullb[b]);
     ++u_issued;
     if (++ui_idx == item_taps(item) * NH) { ui_idx = 0; ++ui_k; }
@@ -270,7 +279,7 @@ __global__ void __launch_bounds__(xts::THREADS, xts::Cfg<KI, KO, P>::PER_SM)
     }
     if (ok) {
       tc::fence_after();
-      xts::gemm_unit<KI, KO, P>(d, a, ring_s + (uint32_t)(b * G::UNIT), acc);
+      xts::gemm_unit<KIE, KO, P>(d, a, ring_s + (uint32_t)(b * G::UNIT), acc);
       tc::mma_commit(&emptyb[b]);
     }
     ++u_done;
@@ -310,8 +319,9 @@ __global__ void __launch_bounds__(xts::THREADS, xts::Cfg<KI, KO, P>::PER_SM)
     };
     auto load_stage = [&](float (&v)[16], int q) {
       long long s = 0;
-      const bool ok_n = source(q / NH, s);
-      const int c0 = (q % NH) * KU + 16 * grp;
+      const int stap = PAIR ? 2 * q + grp : q / NH;      // PAIR: NH = 1
+      const bool ok_n = (!PAIR || stap < T3) && source(stap, s);
+      const int c0 = PAIR ? 0 : (q % NH) * KU + 16 * grp;
       const float4* qp = reinterpret_cast<const float4*>(src + s * CI + c0 / 2);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -448,6 +458,262 @@ fail:
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Prolongation in block form: an item is a tile of 128 coarse nodes j and
+// all 2^d parity classes of their fine nodes 2j + p.  The stages are the 2^d
+// source rows e_c[j + s] (s in {0,1}^d; per K part), and each stage is ONE
+// MMA group of N = 2^d x 2C columns: the block of class p holds P_o with
+// o = p - 2s per axis (-1, 0 or +1) when s is inside p (s_a <= p_a), zeros
+// otherwise.  So the 27 (class, tap) products of a 3D block run as 8 wide
+// MMA groups instead of 27 narrow ones, and every source row is gathered
+// once instead of once per class.  Each class accumulates 2^d x K/8 x 3 MMAs
+// at most (fine for the truncating accumulation, no fold).
+// ---------------------------------------------------------------------------
+namespace xts {
+
+template <int KI, int KO, int D, int P>
+struct BlockCfg {
+  static constexpr int NCLS = 1 << D;
+  static constexpr int N = NCLS * KO;                         // MMA N: all classes
+  static constexpr int KU = 32;
+  static constexpr int NH = KI / KU;
+  static constexpr int AW = P ? 2 * KU : KU / 2;
+  static constexpr int NEED = N + 2 * AW;
+  static constexpr int COLS = NEED <= 256 ? 256 : 512;
+  static constexpr int PER_SM = 512 / COLS;
+  static constexpr int SUB = KU * N * (P ? 4 : 2);
+  static constexpr int UNIT = P ? 2 * SUB : SUB;
+  static constexpr int MATB = P ? 2 * N * KI * 4 : N * KI * 2;  // one source's stacked matrix
+  static constexpr int RB = (PER_SM == 1 ? 192 * 1024 : 96 * 1024) / UNIT;
+  static_assert(KI % KU == 0 && N <= 256 && RB >= 3 && NEED <= COLS, "block prolongation shape");
+};
+
+// D (+)= A B^T over one unit (KU of K), N output columns
+template <int N, int KU, int SUB, int P>
+__device__ __forceinline__ void gemm_n(uint32_t d, uint32_t a, uint32_t b, bool accumulate) {
+  constexpr uint32_t lbo = N * 16;
+  constexpr uint64_t kstep = (2 * lbo) >> 4;
+  if constexpr (P == 0) {
+    constexpr uint32_t idesc = tc::make_idesc(M, N);
+    const uint64_t b0 = tc::make_desc(b, lbo, 128);
+#pragma unroll
+    for (int s = 0; s < KU / 16; ++s)
+      tc::mma_bf16_ts(d, a + 8 * s, b0 + s * kstep, idesc, (accumulate || s > 0) ? 1u : 0u);
+  } else {
+    constexpr uint32_t idesc = tc::make_idesc_tf32(M, N);
+    const uint64_t bh0 = tc::make_desc(b, lbo, 128);
+    const uint64_t bl0 = bh0 + (SUB >> 4);
+#pragma unroll
+    for (int s = 0; s < KU / 8; ++s) {
+      const uint32_t ahi = a + 8 * s, alo = a + KU + 8 * s;
+      tc::mma_tf32_ts(d, alo, bh0 + s * kstep, idesc, (accumulate || s > 0) ? 1u : 0u);
+      tc::mma_tf32_ts(d, ahi, bl0 + s * kstep, idesc, 1u);
+      tc::mma_tf32_ts(d, ahi, bh0 + s * kstep, idesc, 1u);
+    }
+  }
+}
+
+}  // namespace xts
+
+template <int KI, int KO, int D, int P>
+__global__ void __launch_bounds__(xts::THREADS, xts::BlockCfg<KI, KO, D, P>::PER_SM)
+    k_prolong_block_ts(xts::XParams p) {
+  using G = xts::BlockCfg<KI, KO, D, P>;
+  constexpr int CI = KI / 2, CO = KO / 2;
+  constexpr int NH = G::NH, KU = G::KU, RB = G::RB, NCLS = G::NCLS, N = G::N;
+  constexpr int UPI = NCLS * NH;                  // units (= stages) per item
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t abar[2];
+  __shared__ uint64_t fullb[RB];
+  __shared__ uint64_t emptyb[RB];
+  __shared__ uint32_t tmem_base_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lanei = tid & 31;
+  const int row = 32 * (warp & 3) + lanei;
+  const int grp = warp >> 2;
+
+  if (tid == 0) {
+    tc::bar_init(&abar[0], 1);
+    tc::bar_init(&abar[1], 1);
+    for (int b = 0; b < RB; ++b) {
+      tc::bar_init(&fullb[b], 1);
+      tc::bar_init(&emptyb[b], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     tc::smem_u32(&tmem_base_sh)),
+                 "r"((uint32_t)G::COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const uint32_t lane = (uint32_t)(32 * (warp & 3)) << 16;
+  const uint32_t tD = tmem, slot0 = tmem + N, slot1 = slot0 + G::AW;
+  const uint32_t ring_s = tc::smem_u32(smem);
+  uint32_t aph[2] = {0, 0};
+  bool ok = true;
+  auto wait_a = [&](int s) {
+    ok = tc::bar_wait(&abar[s], aph[s], p.err) && ok;
+    aph[s] ^= 1;
+  };
+  const int my_items = blockIdx.x < p.items ? (p.items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  // ---- weight stream: unit u of an item = (source u / NH, K part u % NH);
+  // thread 32 issues after each block barrier, u_seen = units consumed before it
+  const int u_total = my_items * UPI;
+  int u_issued = 0, u_done = 0, u_seen = 0, u_fail = -1;
+  auto issue_unit = [&]() {
+    const int b = u_issued % RB;
+    if (u_issued >= RB)
+      ok = tc::bar_wait(&emptyb[b], (uint32_t)(((u_issued / RB) - 1) & 1), p.err) && ok;
+    const int w = u_issued % UPI, src_i = w / NH, h = w % NH;
+    const uint8_t* src = reinterpret_cast<const uint8_t*>(p.mats) + (size_t)src_i * G::MATB;
+    const uint32_t dst = ring_s + (uint32_t)(b * G::UNIT);
+    xts::expect_tx(&fullb[b], (uint32_t)G::UNIT);
+    xts::bulk_copy(dst, src + (size_t)h * G::SUB, G::SUB, &fullb[b]);
+    if constexpr (P == 1)
+      xts::bulk_copy(dst + G::SUB, src + (size_t)N * KI * 4 + (size_t)h * G::SUB, G::SUB,
+                     &fullb[b]);
+    ++u_issued;
+  };
+  auto produce = [&]() {
+    if (tid == 32)
+      while (ok && u_issued < u_total && u_issued < u_seen + RB - 1) issue_unit();
+    ++u_seen;
+  };
+  auto run_unit = [&](uint32_t a, bool acc) {   // thread 0
+    const int b = u_done % RB;
+    if (!tc::bar_wait(&fullb[b], (uint32_t)((u_done / RB) & 1), p.err)) {
+      ok = false;
+      u_fail = u_done;
+    }
+    if (ok) {
+      tc::fence_after();
+      xts::gemm_n<N, KU, G::SUB, P>(tD, a, ring_s + (uint32_t)(b * G::UNIT), acc);
+      tc::mma_commit(&emptyb[b]);
+    }
+    ++u_done;
+  };
+  if (tid == 32)
+    while (ok && u_issued < u_total && u_issued < RB - 1) issue_unit();
+
+  const long long cnodes = (long long)p.cx * p.cy * p.cz;
+  for (int k = 0; k < my_items; ++k) {
+    const int item = blockIdx.x + k * gridDim.x;
+    const int field = item / p.tiles;
+    const int tile = item - field * p.tiles;
+    const float2* src = p.src + (size_t)field * (size_t)p.src_nodes * CI;
+    float2* dst = p.dst + (size_t)field * (size_t)p.dst_nodes * CO;
+    const long long j = (long long)tile * xts::M + row;
+    const bool row_ok = j < cnodes;
+    int jx, jy, jz;
+    node_xyz(row_ok ? j : 0, p.cx, p.cy, jx, jy, jz);
+    // stage q: source s = q / NH (row j + s), columns (q % NH) KU + 16 grp
+    auto load_stage = [&](float (&v)[16], int q) {
+      const int sv = q / NH;
+      const int dx = sv & 1, dy = (sv >> 1) & 1, dz = D == 3 ? (sv >> 2) & 1 : 0;
+      const bool ok_n = row_ok && jx + dx < p.cx && jy + dy < p.cy && jz + dz < p.cz;
+      const long long sidx = ((long long)(jz + dz) * p.cy + (jy + dy)) * p.cx + (jx + dx);
+      const int c0 = (q % NH) * KU + 16 * grp;
+      const float4* qp = reinterpret_cast<const float4*>(src + (ok_n ? sidx : 0) * CI + c0 / 2);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 w = ok_n ? __ldg(qp + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[4 * u] = w.x;
+        v[4 * u + 1] = w.y;
+        v[4 * u + 2] = w.z;
+        v[4 * u + 3] = w.w;
+      }
+    };
+    // two stages per iteration: both register buffers named statically
+    auto stage = [&](int q, float (&cur)[16], uint32_t slot) -> bool {
+      if (q >= 2) wait_a(q & 1);
+      xts::put16<KU, P>(slot + lane, 16 * grp, cur);
+      tc::tmem_st_wait();
+      if (q + 2 < UPI) load_stage(cur, q + 2);
+      tc::fence_before();
+      ok = __syncthreads_and(ok);
+      if (!ok) return false;
+      produce();
+      if (tid == 0) {
+        tc::fence_after();
+        run_unit(slot, q > 0);
+        tc::mma_commit(&abar[q & 1]);
+      }
+      return true;
+    };
+    float va[16], vb[16];
+    load_stage(va, 0);
+    if (UPI > 1) load_stage(vb, 1);
+    {
+      int q = 0;
+      for (; q + 1 < UPI; q += 2) {
+        if (!stage(q, va, slot0)) goto fail;
+        if (!stage(q + 1, vb, slot1)) goto fail;
+      }
+      if (q < UPI && !stage(q, va, slot0)) goto fail;
+    }
+    if (UPI >= 2) wait_a((UPI - 2) & 1);
+    wait_a((UPI - 1) & 1);
+    tc::fence_after();
+    // ---- epilogue: e[2j + p] += D[class p]; the thread group grp takes the
+    // classes whose highest parity bit equals grp
+#pragma unroll
+    for (int pc = 0; pc < NCLS / 2; ++pc) {
+      const int pcls = grp * (NCLS / 2) + pc;
+      const int px = pcls & 1, py = (pcls >> 1) & 1, pz = D == 3 ? (pcls >> 2) & 1 : 0;
+      const long long o_row =
+          ((long long)(2 * jz + pz) * p.fy + (2 * jy + py)) * p.fx + (2 * jx + px);
+#pragma unroll
+      for (int c = 0; c < KO / 16; ++c) {
+        float dv[16];
+        tc::tmem_ld16(tD + lane + (uint32_t)(pcls * KO + 16 * c), dv);
+        if (row_ok) {
+          float4* op = reinterpret_cast<float4*>(dst + o_row * CO + 8 * c);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 e = op[u];
+            op[u] = make_float4(e.x + dv[4 * u], e.y + dv[4 * u + 1], e.z + dv[4 * u + 2],
+                                e.w + dv[4 * u + 3]);
+          }
+        }
+      }
+    }
+    tc::fence_before();
+  }
+  ok = __syncthreads_and(ok);
+  if (!ok) goto fail;
+  if (warp == 0) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"((uint32_t)G::COLS));
+  }
+  return;
+
+fail:
+  if (p.err && tid == 0) atomicOr(p.err, 1);
+  if (tid == 32) {
+    for (int u = u_seen; u < u_issued; ++u)
+      tc::bar_wait(&fullb[u % RB], (uint32_t)((u / RB) & 1), nullptr);
+  }
+  if (tid == 0) {
+    if (u_fail >= 0)
+      tc::bar_wait(&fullb[u_fail % RB], (uint32_t)((u_fail / RB) & 1), nullptr);
+    if (u_done > 0)
+      tc::bar_wait(&emptyb[(u_done - 1) % RB], (uint32_t)(((u_done - 1) / RB) & 1), nullptr);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"((uint32_t)G::COLS));
+  }
+}
+
 namespace {
 
 int xsm_count() {
@@ -463,7 +729,7 @@ int xsm_count() {
 
 template <int KI, int KO, int D, int P, int DIR>
 mcmg_status xts_launch(xts::XParams p, int nrhs, cudaStream_t st) {
-  using G = xts::Cfg<KI, KO, P>;
+  using G = xts::Cfg<xts::stage_k(KI, DIR), KO, P>;
   auto kern = k_transfer_ts<KI, KO, D, P, DIR>;
   static bool attr = false;
   // ring; at most PER_SM CTAs on one SM so that their tensor memory fits
@@ -484,13 +750,36 @@ mcmg_status xts_launch(xts::XParams p, int nrhs, cudaStream_t st) {
   return MCMG_OK;
 }
 
+template <int KI, int KO, int D, int P>
+mcmg_status block_launch(xts::XParams p, int nrhs, cudaStream_t st) {
+  using G = xts::BlockCfg<KI, KO, D, P>;
+  auto kern = k_prolong_block_ts<KI, KO, D, P>;
+  static bool attr = false;
+  const size_t guard = (size_t)(228 * 1024) / (G::PER_SM + 1) + 16 - 2048;
+  size_t smem = std::max((size_t)G::RB * G::UNIT, guard);
+  smem = (smem + 127) & ~(size_t)127;
+  if (!attr) {
+    MCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    attr = true;
+  }
+  const long long cn = (long long)p.cx * p.cy * p.cz;
+  p.tiles = (int)((cn + xts::M - 1) / xts::M);
+  p.items = p.tiles * nrhs;
+  const int grid = std::min(p.items, xsm_count() * G::PER_SM);
+  kern<<<grid, xts::THREADS, smem, st>>>(p);
+  MCMG_CHECK_LAUNCH("prolong_block_ts");
+  return MCMG_OK;
+}
+
 template <int D, int P, int DIR>
-mcmg_status xts_pair(int CI, int CO, const xts::XParams& p, int nrhs, cudaStream_t st) {
+mcmg_status xts_channels(int CI, int CO, const xts::XParams& p, int nrhs, cudaStream_t st) {
   // (input channels, output channels): restriction C -> C', prolongation C' -> C
 #define XTS_CASE(ci, co)                                          \
   if (CI == ci && CO == co) return xts_launch<2 * ci, 2 * co, D, P, DIR>(p, nrhs, st);
   if constexpr (DIR == 0) {
-    XTS_CASE(16, 32) XTS_CASE(16, 16) XTS_CASE(32, 64) XTS_CASE(32, 32) XTS_CASE(64, 64)
+    XTS_CASE(8, 16) XTS_CASE(8, 8) XTS_CASE(16, 32) XTS_CASE(16, 16) XTS_CASE(32, 64)
+    XTS_CASE(32, 32) XTS_CASE(64, 64)
   } else {
     XTS_CASE(16, 8) XTS_CASE(16, 16) XTS_CASE(32, 16) XTS_CASE(32, 32) XTS_CASE(64, 32)
     XTS_CASE(64, 64)
@@ -506,8 +795,8 @@ bool xts_supported(const Level& L, bool restrict_) {
   if (!L.use_ts || !L.ts_R || !L.ts_P) return false;
   const int CI = restrict_ ? L.C : L.Cn, CO = restrict_ ? L.Cn : L.C;
   if (restrict_)
-    return (CI == 16 && (CO == 32 || CO == 16)) || (CI == 32 && (CO == 64 || CO == 32)) ||
-           (CI == 64 && CO == 64);
+    return (CI == 8 && (CO == 16 || CO == 8)) || (CI == 16 && (CO == 32 || CO == 16)) ||
+           (CI == 32 && (CO == 64 || CO == 32)) || (CI == 64 && CO == 64);
   return (CI == 16 && (CO == 8 || CO == 16)) || (CI == 32 && (CO == 16 || CO == 32)) ||
          (CI == 64 && (CO == 32 || CO == 64));
 }
@@ -535,11 +824,62 @@ mcmg_status launch_transfer_ts(const Level& L, bool restrict_, const float2* src
   const int CI = restrict_ ? L.C : L.Cn, CO = restrict_ ? L.Cn : L.C;
   const bool d3 = L.g.d == 3, tf = L.ts_prec == MCMG_FP32_TC;
   if (restrict_) {
-    if (tf) return d3 ? xts_pair<3, 1, 0>(CI, CO, p, nrhs, st) : xts_pair<2, 1, 0>(CI, CO, p, nrhs, st);
-    return d3 ? xts_pair<3, 0, 0>(CI, CO, p, nrhs, st) : xts_pair<2, 0, 0>(CI, CO, p, nrhs, st);
+    if (tf) return d3 ? xts_channels<3, 1, 0>(CI, CO, p, nrhs, st) : xts_channels<2, 1, 0>(CI, CO, p, nrhs, st);
+    return d3 ? xts_channels<3, 0, 0>(CI, CO, p, nrhs, st) : xts_channels<2, 0, 0>(CI, CO, p, nrhs, st);
   }
-  if (tf) return d3 ? xts_pair<3, 1, 1>(CI, CO, p, nrhs, st) : xts_pair<2, 1, 1>(CI, CO, p, nrhs, st);
-  return d3 ? xts_pair<3, 0, 1>(CI, CO, p, nrhs, st) : xts_pair<2, 0, 1>(CI, CO, p, nrhs, st);
+  if (tf) return d3 ? xts_channels<3, 1, 1>(CI, CO, p, nrhs, st) : xts_channels<2, 1, 1>(CI, CO, p, nrhs, st);
+  return d3 ? xts_channels<3, 0, 1>(CI, CO, p, nrhs, st) : xts_channels<2, 0, 1>(CI, CO, p, nrhs, st);
+}
+
+// Block prolongation: (C_n, C) with C_n in {16, 32, 64}, C = C_n or C_n / 2,
+// and all 2^d classes in one MMA (2^d x 2C <= 256 columns).
+bool xts_block_pair(int d, int Cn, int C) {
+  if (!((Cn == 16 || Cn == 32 || Cn == 64) && (C == Cn || 2 * C == Cn))) return false;
+  return (1 << d) * 2 * C <= 256;
+}
+
+bool xts_block_supported(const Level& L) {
+  return L.use_ts && L.ts_Pb && xts_block_pair(L.g.d, L.Cn, L.C);
+}
+
+namespace {
+template <int D, int P>
+mcmg_status block_channels(int Cn, int C, const xts::XParams& p, int nrhs, cudaStream_t st) {
+#define XTB_CASE(cn, c)                                                            \
+  if (Cn == cn && C == c) {                                                         \
+    if constexpr ((1 << D) * 2 * c <= 256) return block_launch<2 * cn, 2 * c, D, P>(p, nrhs, st); \
+  }
+  XTB_CASE(16, 8) XTB_CASE(16, 16) XTB_CASE(32, 16) XTB_CASE(32, 32) XTB_CASE(64, 32)
+  XTB_CASE(64, 64)
+#undef XTB_CASE
+  set_error("block prolongation: no variant for %d -> %d channels", Cn, C);
+  return MCMG_ERR_SHAPE;
+}
+}  // namespace
+
+mcmg_status launch_prolong_block_ts(const Level& L, const float2* ec, float2* e, int nrhs,
+                                    cudaStream_t st) {
+  if (!xts_block_supported(L)) {
+    set_error("block prolongation not available on this level");
+    return MCMG_ERR_SHAPE;
+  }
+  const Grid gc = L.g.coarse();
+  xts::XParams p{};
+  p.src = ec;
+  p.dst = e;
+  p.mats = L.ts_Pb;
+  p.fx = L.g.nx;
+  p.fy = L.g.ny;
+  p.fz = L.g.nz;
+  p.cx = gc.nx;
+  p.cy = gc.ny;
+  p.cz = gc.nz;
+  p.src_nodes = gc.nodes();
+  p.dst_nodes = L.g.nodes();
+  p.err = L.err;
+  const bool d3 = L.g.d == 3, tf = L.ts_prec == MCMG_FP32_TC;
+  if (tf) return d3 ? block_channels<3, 1>(L.Cn, L.C, p, nrhs, st) : block_channels<2, 1>(L.Cn, L.C, p, nrhs, st);
+  return d3 ? block_channels<3, 0>(L.Cn, L.C, p, nrhs, st) : block_channels<2, 0>(L.Cn, L.C, p, nrhs, st);
 }
 
 // Host: a complex Cout x Cin matrix M[co][ci] (float2, row-major) -> its real

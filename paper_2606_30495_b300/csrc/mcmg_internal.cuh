@@ -91,6 +91,9 @@ struct Level {
   // layout, for the tensor-core transfers (null where those do not apply)
   const uint4* ts_R = nullptr;
   const uint4* ts_P = nullptr;
+  // per coarse source offset s in {0,1}^d: the prolongation matrices of all
+  // 2^d parity classes stacked (zero where a class does not read s)
+  const uint4* ts_Pb = nullptr;
   // signatures of the arithmetic of one smoothing step (stencil, K_A, K_S,
   // W^(i)) and of the residual (stencil, K_A), with precision and C: launches
   // of different handles may be batched when these agree
@@ -141,6 +144,12 @@ mcmg_status launch_transfer_ts(const Level& L, bool restrict_, const float2* src
 // complex Cout x Cin matrix [co][ci] -> real block form (2 Cout x 2 Cin) as
 // a B operand: BF16 (4 Cout Cin values) or TF32 hi and lo (2 * 4 Cout Cin)
 void pack_ts_rect(const float2* Mc, int Cout, int Cin, bool tf32, void* out);
+// block prolongation (kernels_xts.cu): all parity classes of a coarse tile
+// in one pass; available where xts_block_pair(d, C_n, C) holds
+bool xts_block_pair(int d, int Cn, int C);
+bool xts_block_supported(const Level& L);
+mcmg_status launch_prolong_block_ts(const Level& L, const float2* ec, float2* e, int nrhs,
+                                    cudaStream_t st);
 
 // Launchers used by the V-cycle (kernels_vcycle.cu), asynchronous on `st`.
 // mode 0: e_out = e_in + S^(step)(r - A e_in); mode 1: e_out = r - A e_in.

@@ -138,27 +138,40 @@ def test_residual_restrict(case):
 
 
 def _xts_supported(C, Cn, restrict_):
-    """Channel pairs of the tensor-core transfer: input side >= 16 channels,
-    output equal to or half / twice the input (the library's model family)."""
+    """Channel pairs of the tensor-core transfer: input side >= 16 channels
+    (restriction: >= 8), output equal to or half / twice the input (the
+    library's model family)."""
     ci, co = (C, Cn) if restrict_ else (Cn, C)
-    if restrict_:
-        return (ci, co) in {(16, 32), (16, 16), (32, 64), (32, 32), (64, 64)}
+    if restrict_:       # from 8 channels: two taps per 32-wide stage
+        return (ci, co) in {(8, 16), (8, 8), (16, 32), (16, 16), (32, 64), (32, 32), (64, 64)}
     return (ci, co) in {(16, 8), (16, 16), (32, 16), (32, 32), (64, 32), (64, 64)}
+
+
+def _block_supported(d, C, Cn):
+    """Block prolongation: C_n in {16, 32, 64}, C = C_n or C_n / 2, all 2^d
+    parity classes within one 256-column MMA."""
+    return Cn in (16, 32, 64) and C in (Cn, Cn // 2) and (2 ** d) * 2 * C <= 256
 
 
 def test_transfer_every_shape(case):
     """Restriction R_l and prolongation P_l in every kernel shape, the
-    tensor-core one (the last shape) included where the level's channels
-    allow it, against the oracle; then V-cycles with the tensor-core
-    transfers forced on every level that has them."""
+    tensor-core ones (the last two shapes: per parity class, and the block
+    form of the prolongation) included where the level's channels allow
+    them, against the oracle; then V-cycles with the tensor-core transfers
+    forced on every level that has them."""
     from paper_2606_30495_b300 import mcmg
     prec, m, h = case
     w = m["w"]
     L = w["levels"]
     tol = _tols(prec)[0]
-    xts = mcmg.kernel_shape_count(mcmg.OP_RESTRICT) - 1
-    assert xts == mcmg.kernel_shape_count(mcmg.OP_PROLONG) - 1
+    # the last two shapes: the tensor-core transfer, then (prolongation only)
+    # its block form over all parity classes
+    xts = mcmg.kernel_shape_count(mcmg.OP_RESTRICT) - 2
+    blk = xts + 1
+    assert blk == mcmg.kernel_shape_count(mcmg.OP_PROLONG) - 1
+    d = len(m["shape"])
     ran_xts = 0
+    ran_blk = 0
     try:
         for l in range(L - 1):
             C, Cn = w["channels"][l], w["channels"][l + 1]
@@ -177,6 +190,9 @@ def test_transfer_every_shape(case):
                     ran = h.set_kernel_shape(l, op, sh)
                     if sh == xts:
                         assert ran == ok_xts, (l, op, C, Cn)
+                    if sh == blk:
+                        assert ran == (op == mcmg.OP_PROLONG and _block_supported(d, C, Cn)
+                                       and prec in ("fp32tc", "bf16")), (l, op, C, Cn)
                     if not ran:
                         continue
                     if op == mcmg.OP_RESTRICT:
@@ -189,13 +205,18 @@ def test_transfer_every_shape(case):
                         got = host(ef)
                     assert relerr(got, want) < tol, (l, op, sh)
                     ran_xts += sh == xts
+                    ran_blk += sh == blk
                 h.set_kernel_shape(l, op, -1)
         if any(_xts_supported(w["channels"][l], w["channels"][l + 1], rr)
                for l in range(L - 1) for rr in (True, False)):
             assert ran_xts > 0
+            if any(_block_supported(d, w["channels"][l], w["channels"][l + 1])
+                   for l in range(L - 1)):
+                assert ran_blk > 0
             for l in range(L - 1):
-                for op in (mcmg.OP_RESTRICT, mcmg.OP_PROLONG):
-                    h.set_kernel_shape(l, op, xts)   # False where not available
+                h.set_kernel_shape(l, mcmg.OP_RESTRICT, xts)   # False where not available
+                if not h.set_kernel_shape(l, mcmg.OP_PROLONG, blk):
+                    h.set_kernel_shape(l, mcmg.OP_PROLONG, xts)
             rv = I.complex_normal((2,) + m["shape"], rng(73))
             want_v = np.stack([O.vcycle(w, m["feats"], ri) for ri in rv])
             ev = torch.zeros(rv.shape, dtype=torch.complex64, device="cuda")
@@ -210,6 +231,8 @@ def test_transfer_every_shape(case):
 
 @pytest.mark.parametrize("prec,shape,channels", [
     ("fp32tc", (94, 80, 70), [16, 32]),     # restriction 514.1 tiles, prolongation 8 classes
+    ("fp32tc", (94, 80, 70), [8, 16]),      # restriction with two taps per stage
+    ("bf16", (500, 330), [8, 16]),
     ("bf16", (94, 80, 70), [32, 32]),
     ("fp32tc", (62, 48, 40), [64, 64]),     # four K parts per tap (TF32)
     ("fp32tc", (500, 330), [16, 32]),       # 2D: 322.3 tiles, 4 classes
@@ -218,8 +241,9 @@ def test_transfer_every_shape(case):
 def test_transfer_ts_many_items(ctx, prec, shape, channels):
     """The tensor-core transfers with more items than CTAs (each persistent
     CTA walks several tiles and parity classes) and a ragged last tile,
-    nrhs = 2, against the oracle.  Setup features are not needed: the
-    restriction is taken through the residual with e = 0."""
+    nrhs = 2, against the oracle, the prolongation also in its block form.
+    Setup features are not needed: the restriction is taken through the
+    residual with e = 0."""
     from paper_2606_30495_b300 import mcmg
     d = len(shape)
     pre, post = I.nu_schedule(2)
@@ -227,7 +251,7 @@ def test_transfer_ts_many_items(ctx, prec, shape, channels):
     c = I.grf(shape, 4.0, 1.0, 3.0, rng(109))
     omega = I.omega_for_ppw(c.min(), 8.0, shape[0])
     h = mcmg.Handle(ctx, c, omega, 4, 1.0, w, precision=_prec(prec))
-    xts = mcmg.kernel_shape_count(mcmg.OP_RESTRICT) - 1
+    xts = mcmg.kernel_shape_count(mcmg.OP_RESTRICT) - 2
     try:
         C, Cn = channels
         lv = w["lvl"][0]
@@ -241,13 +265,15 @@ def test_transfer_ts_many_items(ctx, prec, shape, channels):
                                                        device="cuda"), rc, nrhs=2)
             want = np.stack([O.restrict(lv["R"], r[k]) for k in range(2)])
             assert relerr(host(rc), want) < tol
-        assert h.set_kernel_shape(0, mcmg.OP_PROLONG, xts)
         ec = I.complex_normal((2,) + cshp + (Cn,), rng(81))
         e = I.complex_normal((2,) + shape + (C,), rng(82))
-        ef = dev(e)
-        h.prolong_add(0, dev(ec), ef, nrhs=2)
         want = np.stack([e[k] + O.prolong(lv["P"], ec[k], shape) for k in range(2)])
-        assert relerr(host(ef), want) < tol
+        shapes = [xts] + ([xts + 1] if _block_supported(d, C, Cn) else [])
+        for sh in shapes:
+            assert h.set_kernel_shape(0, mcmg.OP_PROLONG, sh)
+            ef = dev(e)
+            h.prolong_add(0, dev(ec), ef, nrhs=2)
+            assert relerr(host(ef), want) < tol, sh
         assert h.device_error() == 0
     finally:
         h.close()
