@@ -432,6 +432,9 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
   if ((s = dev_alloc(h, h->arena, (void**)&h->q64, sizeof(double2) * N))) return cleanup(), s;
   if ((s = launch_make_q(c_dev, omega, m->sponge_width, m->gamma_max, g0, h->q32, h->q64, st)))
     return cleanup(), s;
+  if ((s = dev_alloc(h, h->arena, (void**)&h->qdf, sizeof(float4) * N)) ||
+      (s = launch_make_qdf(h->q64, h->qdf, g0, st)))
+    return cleanup(), s;
   // ---- weights to device layouts
   for (int l = 0; l < L; ++l) {
     Level& lv = h->lv[l];

@@ -114,11 +114,11 @@ mcmg_status launch_apply_A64(const double2* q, const double2* x, double2* y, con
 // The Arnoldi product of the Krylov loop.  FP64 arithmetic runs at a small
 // fraction of the FP32 rate on this part, so the operator is evaluated as
 // double-float (an unevaluated sum hi + lo of two FP32 values, 48 significand
-// bits): (2d - q) and q's imaginary part are split once per node, their
-// products with the FP32 x are exact up to the lo * lo term (Dekker's product
-// through the FMA), sums use Knuth's two-sum, and the result is rounded once
-// to FP64.  Relative error ~2^-44 of the largest term, far below the FP32
-// rounding already in x.
+// bits) and the result stays double-float: (2d - Re q) and Im q come split
+// from a table made once at setup, their products with the FP32 x are exact
+// up to the lo * lo term (Dekker's product through the FMA), sums use Knuth's
+// two-sum.  Relative error ~2^-44 of the largest term, far below the FP32
+// rounding already in x; no FP64 instruction per node.
 namespace {
 struct DFh {
   float hi, lo;
@@ -146,53 +146,66 @@ __device__ __forceinline__ DFh dfh_split(double v) {
 }
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_apply_A_df(const double2* __restrict__ q,
-                                                    const float2* __restrict__ x,
-                                                    double2* __restrict__ y, Grid g) {
-  const int N = (int)g.nodes();                  // below 2^31 (checked by the launcher)
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  const size_t off = (size_t)blockIdx.y * N;
-  const float2* xx = x + off;
-  const int rest = n / g.nx;
-  const int ix = n - rest * g.nx;
-  const int iy = rest % g.ny;
-  const int iz = rest / g.ny;
-  const float2 u = xx[n];
-  const double2 qq = q[n];
-  const DFh a = dfh_split((double)(2 * g.d) - qq.x);   // 2d - Re q
+__global__ void k_make_qdf(const double2* __restrict__ q, float4* __restrict__ qdf, int d,
+                           long long n) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const double2 qq = q[p];
+  const DFh a = dfh_split((double)(2 * d) - qq.x);   // 2d - Re q
   const DFh b = dfh_split(qq.y);                      // Im q
-  // (2d - q) u = (a ur + b ui) + i (a ui - b ur)
-  DFh re = dfh_mul(u.x, a.hi, a.lo), im = dfh_mul(u.y, a.hi, a.lo);
-  dfh_add(re, dfh_mul(u.y, b.hi, b.lo));
-  dfh_add(im, dfh_mul(-u.x, b.hi, b.lo));
-  const int sxy = g.nx * g.ny;
+  qdf[p] = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
+mcmg_status launch_make_qdf(const double2* q64, float4* qdf, const Grid& g, cudaStream_t st) {
+  const long long n = g.nodes();
+  k_make_qdf<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(q64, qdf, g.d, n);
+  MCMG_CHECK_LAUNCH("make_qdf");
+  return MCMG_OK;
+}
+
+// IT: index type (32-bit below 2^31 nodes)
+template <typename IT>
+__global__ void __launch_bounds__(256) k_apply_A_arnoldi(const float4* __restrict__ qdf,
+                                                         const float2* __restrict__ x,
+                                                         float4* __restrict__ y, Grid g) {
+  const IT N = (IT)g.nodes();
+  const IT n = (IT)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const IT rest = n / g.nx;
+  const int ix = (int)(n - rest * g.nx);
+  const int iy = (int)(rest % g.ny);
+  const int iz = (int)(rest / g.ny);
+  const float2 u = x[n];
+  const float4 c = qdf[n];
+  // (2d - q) u = (a ur + b ui) + i (a ui - b ur), a = 2d - Re q, b = Im q
+  DFh re = dfh_mul(u.x, c.x, c.y), im = dfh_mul(u.y, c.x, c.y);
+  dfh_add(re, dfh_mul(u.y, c.z, c.w));
+  dfh_add(im, dfh_mul(-u.x, c.z, c.w));
+  const IT sxy = (IT)g.nx * g.ny;
   auto sub = [&](float2 v) {
     dfh_add(re, -v.x);
     dfh_add(im, -v.y);
   };
-  if (ix > 0) sub(xx[n - 1]);
-  if (ix < g.nx - 1) sub(xx[n + 1]);
-  if (iy > 0) sub(xx[n - g.nx]);
-  if (iy < g.ny - 1) sub(xx[n + g.nx]);
+  if (ix > 0) sub(x[n - 1]);
+  if (ix < g.nx - 1) sub(x[n + 1]);
+  if (iy > 0) sub(x[n - g.nx]);
+  if (iy < g.ny - 1) sub(x[n + g.nx]);
   if (g.d == 3) {
-    if (iz > 0) sub(xx[n - sxy]);
-    if (iz < g.nz - 1) sub(xx[n + sxy]);
+    if (iz > 0) sub(x[n - sxy]);
+    if (iz < g.nz - 1) sub(x[n + sxy]);
   }
-  y[off + n] = make_double2((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo);
+  y[n] = make_float4(re.hi, re.lo, im.hi, im.lo);
 }
 
-mcmg_status launch_apply_A_mixed(const double2* q, const float2* x, double2* y, const Grid& g,
-                                 int nrhs, cudaStream_t st) {
-  long long N = g.nodes();
-  dim3 grid((unsigned)((N + 255) / 256), (unsigned)nrhs);
-  if (N < (1ll << 31)) {
-    k_apply_A_df<<<grid, 256, 0, st>>>(q, x, y, g);
-    MCMG_CHECK_LAUNCH("apply_A_df");
-  } else {
-    k_apply_A<double2, float2><<<grid, 256, 0, st>>>(q, x, y, g);
-    MCMG_CHECK_LAUNCH("apply_A_mixed");
-  }
+mcmg_status launch_apply_A_arnoldi(const float4* qdf, const float2* x, float4* w, const Grid& g,
+                                   cudaStream_t st) {
+  const long long N = g.nodes();
+  const unsigned grid = (unsigned)((N + 255) / 256);
+  if (N < (1ll << 31))
+    k_apply_A_arnoldi<int><<<grid, 256, 0, st>>>(qdf, x, w, g);
+  else
+    k_apply_A_arnoldi<long long><<<grid, 256, 0, st>>>(qdf, x, w, g);
+  MCMG_CHECK_LAUNCH("apply_A_arnoldi");
   return MCMG_OK;
 }
 

@@ -3,10 +3,12 @@
 //
 // Precision split: the Krylov basis V and the preconditioned vectors Z are
 // complex64 (the V-cycle's input and output precision).  The Arnoldi work
-// vector w = A z_j is formed in FP64 from the complex64 z_j and stays FP64
-// through Gram-Schmidt; every inner product, update and norm accumulates in
-// double-float (FP64-class, 48 significand bits, on the FP32 units) and the
-// block partials in FP64.  The Hessenberg matrix, Givens rotations and the
+// vector w = A z_j is formed in double-float from the complex64 z_j (an
+// unevaluated sum hi + lo of two FP32 values per real number, 48 significand
+// bits: FP64-class on the FP32 units, which on this part run many times the
+// FP64 rate) and stays double-float through Gram-Schmidt; every inner
+// product, update and norm accumulates in double-float and the block
+// partials in FP64.  The Hessenberg matrix, Givens rotations and the
 // least-squares solve are FP64 on the host, fed by the step's inner products
 // (mirrored to mapped memory).  The solution u and the true residual f - A u
 // (at every restart) are complex128.
@@ -25,6 +27,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <type_traits>
 
 #include "mcmg_internal.cuh"
 
@@ -41,6 +44,9 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 __device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
 __device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float4 v) {
+  return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
 __device__ __forceinline__ void store_w(float2* p, double re, double im) {
   *p = make_float2((float)re, (float)im);
 }
@@ -82,6 +88,14 @@ __device__ __forceinline__ DF df_from(double v) {
   return {h, __double2float_rn(v - (double)h)};
 }
 __device__ __forceinline__ DF df_from(float v) { return {v, 0.f}; }
+// real and imaginary part of a complex w as double-float: float2 and double2
+// values are converted, float4 ones (re hi, re lo, im hi, im lo) already are
+__device__ __forceinline__ DF df_re(float2 w) { return {w.x, 0.f}; }
+__device__ __forceinline__ DF df_im(float2 w) { return {w.y, 0.f}; }
+__device__ __forceinline__ DF df_re(double2 w) { return df_from(w.x); }
+__device__ __forceinline__ DF df_im(double2 w) { return df_from(w.y); }
+__device__ __forceinline__ DF df_re(float4 w) { return {w.x, w.y}; }
+__device__ __forceinline__ DF df_im(float4 w) { return {w.z, w.w}; }
 __device__ __forceinline__ double df_to(DF x) { return (double)x.hi + (double)x.lo; }
 __device__ __forceinline__ DF df_shfl_xor(DF x, int o) {
   return {__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
@@ -104,7 +118,7 @@ __global__ void __launch_bounds__(RED_T) k_multidot(const float2* __restrict__ V
   // that twice as many loads are in flight per thread
   const long long stride = (long long)gridDim.x * RED_T;
   auto accumulate = [&](const WT wv, const float2 (&vv)[KV]) {
-    const DF wx = df_from(wv.x), wy = df_from(wv.y);
+    const DF wx = df_re(wv), wy = df_im(wv);
 #pragma unroll
     for (int i = 0; i < KV; ++i) {
       const int ii = i0 + i;
@@ -238,11 +252,22 @@ __global__ void __launch_bounds__(RED_T) k_update(const float2* __restrict__ V, 
       for (int q = 0; q < 4; ++q) acc(v4[q], i + q);
     }
     for (; i < k; ++i) acc(V[(long long)i * ldv + p], i);
-    const double2 wd = to_d2(w[p]);
-    store_w(w + p, wd.x - df_to(sr), wd.y - df_to(si));
-    const double2 o = to_d2(w[p]);
-    df_add(nn, df_sq(df_from(o.x)));
-    df_add(nn, df_sq(df_from(o.y)));
+    if constexpr (std::is_same<WT, float4>::value) {
+      // double-float w: the difference and the norm without FP64
+      const float4 wv = w[p];
+      DF wr{wv.x, wv.y}, wi{wv.z, wv.w};
+      df_add(wr, DF{-sr.hi, -sr.lo});
+      df_add(wi, DF{-si.hi, -si.lo});
+      w[p] = make_float4(wr.hi, wr.lo, wi.hi, wi.lo);
+      df_add(nn, df_sq(wr));
+      df_add(nn, df_sq(wi));
+    } else {
+      const double2 wd = to_d2(w[p]);
+      store_w(w + p, wd.x - df_to(sr), wd.y - df_to(si));
+      const double2 o = to_d2(w[p]);
+      df_add(nn, df_sq(df_from(o.x)));
+      df_add(nn, df_sq(df_from(o.y)));
+    }
   }
   __shared__ DF sh[RED_T / 32];
 #pragma unroll
@@ -333,14 +358,15 @@ struct Stat {
   double rr, ff;  // |f - A u|^2, |f|^2 at the last restart
 };
 
-// v_{j+1} = w / sqrt(nrm2)
-__global__ void k_scale(const double2* __restrict__ w, const double* __restrict__ dsc,
+// v_{j+1} = w / sqrt(nrm2), rounded to complex64 (FP32 arithmetic on the
+// double-float parts: the result is FP32 anyway)
+__global__ void k_scale(const float4* __restrict__ w, const double* __restrict__ dsc,
                         float2* __restrict__ v, long long n) {
-  const double inv = block_inv_sqrt(dsc + 3);
+  const float inv = (float)block_inv_sqrt(dsc + 3);
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
-  const double2 x = w[p];
-  v[p] = make_float2((float)(x.x * inv), (float)(x.y * inv));
+  const float4 x = w[p];
+  v[p] = make_float2(__fmaf_rn(x.x, inv, x.y * inv), __fmaf_rn(x.z, inv, x.w * inv));
 }
 
 // Stationary step: u += beta * z, beta = ||r|| (the V-cycle ran on r / beta).
@@ -379,7 +405,7 @@ struct Krylov {
   VWork* vw = nullptr;
   float2* V = nullptr;
   float2* Z = nullptr;
-  double2* w = nullptr;     // Arnoldi work vector, FP64
+  float4* w = nullptr;      // Arnoldi work vector, complex double-float
   double2* r64 = nullptr;
   double* part = nullptr;
   double2* d1 = nullptr;
@@ -439,7 +465,7 @@ mcmg_status krylov_create(mcmg_handle_s* h, int m, Krylov** out, bool own_vcycle
   mcmg_status s = MCMG_OK;
   if ((s = A((void**)&k->V, sizeof(float2) * (size_t)(m + 1) * n)) ||
       (s = A((void**)&k->Z, sizeof(float2) * (size_t)m * n)) ||
-      (s = A((void**)&k->w, sizeof(double2) * (size_t)n)) ||
+      (s = A((void**)&k->w, sizeof(float4) * (size_t)n)) ||
       (s = A((void**)&k->r64, sizeof(double2) * (size_t)n)) ||
       (s = A((void**)&k->part, sizeof(double) * 2 * (size_t)k->nblk * (m + 2))) ||
       (s = A((void**)&k->d1, sizeof(double2) * (m + 2))) ||
@@ -505,7 +531,7 @@ static mcmg_status enqueue_restart(Krylov* k) {
 static mcmg_status multidot(Krylov* k, int nv, bool self, double2* out, double2* out_host) {
   const int ktot = nv + (self ? 1 : 0);
   dim3 grid((unsigned)k->nblk, (unsigned)((ktot + KV - 1) / KV));
-  k_multidot<double2><<<grid, RED_T, 0, k->st>>>(k->V, k->n, nv, ktot, k->w, k->n, k->part);
+  k_multidot<float4><<<grid, RED_T, 0, k->st>>>(k->V, k->n, nv, ktot, k->w, k->n, k->part);
   MCMG_CHECK_LAUNCH("multidot");
   k_reduce_parts<<<ktot, RED_T, 0, k->st>>>(k->part, k->nblk, ktot, out, out_host);
   MCMG_CHECK_LAUNCH("reduce_parts");
@@ -518,7 +544,7 @@ static mcmg_status enqueue_arnoldi(Krylov* k, int j) {
   mcmg_handle_s* h = k->h;
   const long long n = k->n;
   float2* zj = k->Z + (size_t)j * n;
-  MCMG_TRY(launch_apply_A_mixed(h->q64, zj, k->w, h->g0, 1, k->st));
+  MCMG_TRY(launch_apply_A_arnoldi(h->qdf, zj, k->w, h->g0, k->st));
   double2* mir = k->mir_d + (size_t)j * k->mir_stride;
   MCMG_TRY(multidot(k, j + 1, true, k->d1, mir));
   MCMG_TRY(launch_update(k->V, n, j + 1, k->d1, k->w, n, k->part, k->nblk, k->st));

@@ -185,8 +185,12 @@ mcmg_status launch_apply_A32(const float2* q, const float2* x, float2* y, const 
 mcmg_status launch_apply_A64(const double2* q, const double2* x, double2* y, const Grid& g,
                              int nrhs, cudaStream_t st);
 // complex64 x, FP64 arithmetic, complex128 y
-mcmg_status launch_apply_A_mixed(const double2* q, const float2* x, double2* y, const Grid& g,
-                                 int nrhs, cudaStream_t st);
+// w = A x for the Arnoldi step: x complex64, w complex double-float
+// (float4 per node: re hi, re lo, im hi, im lo), coefficients from qdf
+mcmg_status launch_apply_A_arnoldi(const float4* qdf, const float2* x, float4* w, const Grid& g,
+                                   cudaStream_t st);
+// qdf from q64 (once, at setup)
+mcmg_status launch_make_qdf(const double2* q64, float4* qdf, const Grid& g, cudaStream_t st);
 mcmg_status launch_residual64(const double2* q, const double2* f, const double2* x, double2* r,
                               double* part, int nblk, const Grid& g, int nrhs, cudaStream_t st);
 
@@ -299,6 +303,9 @@ struct mcmg_handle_s {
   mcmg::Grid g0;
   float2* q32 = nullptr;        // (kh)^2 (1 - i gamma), c64 [nodes]
   double2* q64 = nullptr;       // same, c128
+  // (2d - Re q, Im q) as double-float pairs (hi, lo, hi, lo): the Arnoldi
+  // operator's coefficients without FP64 arithmetic per application
+  float4* qdf = nullptr;
   float2* lift = nullptr;       // [C0]
   float2* proj = nullptr;       // [C0]
   mcmg::Level lv[MCMG_MAX_LEVELS];
