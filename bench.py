@@ -68,6 +68,10 @@ def parse():
     p.add_argument("--precision", default="fp32tc", choices=["native", "fp32", "bf16", "fp32tc"],
                    help="channel-mixing precision ('native': the workload's own)")
     p.add_argument("--no-bf16", action="store_true", help="skip the BF16 comparison solves")
+    p.add_argument("--profile-solve", type=int, default=0,
+                   help="profiling aid: after setup, one solve of at most this many FGMRES "
+                        "iterations inside the NVTX range 'solve' (ncu --nvtx --nvtx-include "
+                        "'solve/'), then exit")
     p.add_argument("--profile-launch", default="",
                    help="LEVEL,KIND[,REPS]: after setup, run only that smoothing launch class "
                         "(KIND first | step | residual) REPS times (default 5) and exit; for "
@@ -384,6 +388,32 @@ def profile_launch(args, h, wl, torch, mcmg, ctx):
     ctx.close()
 
 
+def profile_solve(args, h, c, wl, torch, mcmg, ctx):
+    """One warm-up solve of a few iterations, then one of args.profile_solve
+    iterations inside the NVTX range 'solve'; prints its CUDA-event time."""
+    from paper_2606_30495_b300 import inputs as I
+    f = torch.from_numpy(I.point_source(c.shape)).to("cuda", torch.complex128)
+    u = torch.zeros(c.shape, dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h.solve(f, u, tol=wl["tol"], restart_m=wl["restart"], max_iters=4, stream=stream)
+        u.zero_()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("solve")
+    e0.record(stream)
+    st, info = h.solve(f, u, tol=wl["tol"], restart_m=wl["restart"], max_iters=args.profile_solve,
+                       stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_solve": {"workload": args.workload, "precision": wl["precision"],
+                                        "iters": info["iters"], "ms": e0.elapsed_time(e1)}}))
+    h.close()
+    ctx.close()
+
+
 def config_of(args, wl, restart):
     return {"workload": args.workload, "grid": [wl["n"]] * wl["dim"], "levels": wl["levels"],
             "channels": wl["channels"], "nu_pre": wl["nu_pre"], "nu_post": wl["nu_post"],
@@ -582,6 +612,8 @@ def main():
     t_setup = time.perf_counter() - t0
     if args.profile_launch:
         return profile_launch(args, h, wl, torch, mcmg, ctx)
+    if args.profile_solve:
+        return profile_solve(args, h, c, wl, torch, mcmg, ctx)
     if args.shapes:
         for l, ops in enumerate(json.loads(args.shapes)):
             for op, sh in enumerate(ops):

@@ -15,8 +15,13 @@
 // Forming A z in FP32 would lose up to ||A|| ||z|| / ||A z|| times the FP32
 // rounding, which for an indefinite Helmholtz operator and a preconditioned
 // z is large enough to separate the implicit and true residuals.
-// Orthogonalisation is classical Gram-Schmidt with one full
-// re-orthogonalisation (CGS2): two passes of (h = V^H w, w -= V h).
+// Orthogonalisation is classical Gram-Schmidt with one re-orthogonalisation
+// (CGS2) in one sweep over the basis: the sweep returns h1 = V^H w and the
+// Gram row V^H v_j, the second pass h2 = V^H (w - V h1) = -(V^H V - I) h1 is
+// formed from the kept Gram matrix, and one update applies h1 + h2.  The
+// basis is complex64, so V^H V - I (its storage rounding) is what the second
+// pass has to remove; the sweep's double-float dots are far below it.
+// (mcmg_cgs2 keeps the explicit two-pass form for its callers.)
 //
 // The solve is a resumable state machine so that a server can interleave many
 // solves on separate streams: every stage enqueues device work, records an
@@ -178,6 +183,137 @@ __global__ void __launch_bounds__(RED_T) k_multidot(const float2* __restrict__ V
     for (int o = 16; o > 0; o >>= 1) df_add(acc, df_shfl_xor(acc, o));
     const int vec = i0 + val / 2;
     if (lane == 0 && vec < ktot) part[((size_t)blockIdx.x * ktot + vec) * 2 + (val & 1)] = df_to(acc);
+  }
+}
+
+// One pass over the basis for Arnoldi step j (double-float w): for every
+// basis vector i <= j, a_i = conj(v_i) w and b_i = conj(v_i) v_j (a row of the
+// Gram matrix V^H V), and |w|^2.  Partials part[(bx * width + idx) * 2 + {0,1}]
+// with width = 2j + 3: idx i -> a_i, j + 1 -> |w|^2, j + 2 + i -> b_i.
+// Double-float accumulation (the products of two FP32 values are exact);
+// each warp sums its values by shuffles and warp partials are added in warp
+// order, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(RED_T, 2) k_multidot_gram(const float2* __restrict__ V, long long ldv,
+                                                         int j, const float4* __restrict__ w,
+                                                         long long n, double* __restrict__ part) {
+  const int k = j + 1, width = 2 * j + 3;
+  const int i0 = blockIdx.y * KV;
+  DF ar[KV], ai[KV], br[KV], bi[KV];
+#pragma unroll
+  for (int i = 0; i < KV; ++i) ar[i] = ai[i] = br[i] = bi[i] = DF{0.f, 0.f};
+  const float2* vj = V + (long long)j * ldv;
+  auto accumulate = [&](const float4 wv, const float2 uj, const float2 (&vv)[KV]) {
+    const DF wx{wv.x, wv.y}, wy{wv.z, wv.w};
+#pragma unroll
+    for (int i = 0; i < KV; ++i) {
+      const int ii = i0 + i;
+      if (ii < k) {
+        const float2 v = vv[i];
+        // conj(v) w = (vx wx + vy wy) + i (vx wy - vy wx)
+        df_add(ar[i], df_mul(v.x, wx.hi, wx.lo));
+        df_add(ar[i], df_mul(v.y, wy.hi, wy.lo));
+        df_add(ai[i], df_mul(v.x, wy.hi, wy.lo));
+        df_add(ai[i], df_mul(-v.y, wx.hi, wx.lo));
+        // conj(v) v_j, exact products of FP32 values
+        df_add(br[i], df_mul(v.x, uj.x, 0.f));
+        df_add(br[i], df_mul(v.y, uj.y, 0.f));
+        df_add(bi[i], df_mul(v.x, uj.y, 0.f));
+        df_add(bi[i], df_mul(-v.y, uj.x, 0.f));
+      } else if (ii == k) {  // |w|^2
+        df_add(ar[i], df_sq(wx));
+        df_add(ar[i], df_sq(wy));
+      }
+    }
+  };
+  // one element per iteration (the four accumulators per vector leave no
+  // registers for a second one); two blocks per SM keep the loads in flight
+  const long long stride = (long long)gridDim.x * RED_T;
+  for (long long p = (long long)blockIdx.x * RED_T + threadIdx.x; p < n; p += stride) {
+    const float4 wa = w[p];
+    const float2 ua = vj[p];
+    float2 va[KV];
+#pragma unroll
+    for (int i = 0; i < KV; ++i) {
+      const int ii = i0 + i < k ? i0 + i : 0;
+      va[i] = V[(long long)ii * ldv + p];
+    }
+    accumulate(wa, ua, va);
+  }
+  // 4 KV values per thread: warp sums by shuffles, then the warps in order
+  __shared__ DF sh[4 * KV][RED_T / 32];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto warp_reduce = [&](DF v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) df_add(v, df_shfl_xor(v, o));
+    return v;
+  };
+#pragma unroll
+  for (int i = 0; i < KV; ++i) {
+    const DF r0 = warp_reduce(ar[i]), r1 = warp_reduce(ai[i]);
+    const DF r2 = warp_reduce(br[i]), r3 = warp_reduce(bi[i]);
+    if (lane == 0) {
+      sh[4 * i][wid] = r0;
+      sh[4 * i + 1][wid] = r1;
+      sh[4 * i + 2][wid] = r2;
+      sh[4 * i + 3][wid] = r3;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 * KV) {
+    const int val = threadIdx.x;
+    DF acc = sh[val][0];
+#pragma unroll
+    for (int q = 1; q < RED_T / 32; ++q) df_add(acc, sh[val][q]);
+    const int ii = i0 + val / 4, comp = val & 1;
+    const bool second = (val & 2) != 0;       // b_i
+    int idx = -1;
+    if (!second && ii <= k) idx = ii;          // a_i, or |w|^2 at ii == k
+    if (second && ii < k) idx = j + 2 + ii;
+    if (idx >= 0) part[((size_t)blockIdx.x * width + idx) * 2 + comp] = df_to(acc);
+  }
+}
+
+// Second Gram-Schmidt pass from the Gram matrix (one block, FP64):
+// red[0..j] = h1 = V^H w, red[j+1] = |w|^2, red[j+2+i] = v_i^H v_j.  Row j of
+// G = V^H V is stored (Gd[j][i] = v_i^H v_j, i <= j), then
+// h2 = V^H (w - V h1) = -(G - I) h1, which the two-pass form would compute
+// from a second sweep over the basis.  d1 / d2 (and the host mirror) get h1
+// with |w|^2 and h2; dsum = h1 + h2 is the update's coefficient vector.
+__global__ void k_gram_correct(const double2* __restrict__ red, int j, int ldg,
+                               double2* __restrict__ Gd, double2* __restrict__ d1,
+                               double2* __restrict__ d2, double2* __restrict__ dsum,
+                               double2* __restrict__ mir, int m) {
+  const int t = threadIdx.x;
+  for (int i = t; i <= j; i += blockDim.x) Gd[(size_t)j * ldg + i] = red[j + 2 + i];
+  __syncthreads();
+  for (int l = t; l <= j; l += blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int q = 0; q <= j; ++q) {
+      // G[l][q] = v_l^H v_q: stored as row max(l, q)
+      double2 g;
+      if (l <= q) {
+        g = Gd[(size_t)q * ldg + l];
+      } else {
+        const double2 c = Gd[(size_t)l * ldg + q];
+        g = make_double2(c.x, -c.y);
+      }
+      if (l == q) g.x -= 1.0;
+      const double2 h = red[q];
+      sr += g.x * h.x - g.y * h.y;
+      si += g.x * h.y + g.y * h.x;
+    }
+    const double2 h1 = red[l], h2 = make_double2(-sr, -si);
+    d1[l] = h1;
+    d2[l] = h2;
+    dsum[l] = make_double2(h1.x + h2.x, h1.y + h2.y);
+    if (mir) {
+      mir[l] = h1;
+      mir[m + 2 + l] = h2;
+    }
+  }
+  if (t == 0) {
+    d1[j + 1] = red[j + 1];
+    if (mir) mir[j + 1] = red[j + 1];
   }
 }
 
@@ -410,6 +546,9 @@ struct Krylov {
   double* part = nullptr;
   double2* d1 = nullptr;
   double2* d2 = nullptr;
+  double2* dsum = nullptr;          // h1 + h2, the update's coefficients
+  double2* red = nullptr;           // reduced one-pass dots: 2m + 3 values
+  double2* Gd = nullptr;            // rows of the Gram matrix V^H V, (m+1) x (m+1)
   double2* y = nullptr;             // device copy of the least-squares solution
   // Host side of the Arnoldi process (FP64): Hessenberg columns, Givens
   // rotations, rotated right-hand side, and the least-squares solution.
@@ -467,9 +606,12 @@ mcmg_status krylov_create(mcmg_handle_s* h, int m, Krylov** out, bool own_vcycle
       (s = A((void**)&k->Z, sizeof(float2) * (size_t)m * n)) ||
       (s = A((void**)&k->w, sizeof(float4) * (size_t)n)) ||
       (s = A((void**)&k->r64, sizeof(double2) * (size_t)n)) ||
-      (s = A((void**)&k->part, sizeof(double) * 2 * (size_t)k->nblk * (m + 2))) ||
+      (s = A((void**)&k->part, sizeof(double) * 2 * (size_t)k->nblk * (2 * m + 3))) ||
       (s = A((void**)&k->d1, sizeof(double2) * (m + 2))) ||
       (s = A((void**)&k->d2, sizeof(double2) * (m + 2))) ||
+      (s = A((void**)&k->dsum, sizeof(double2) * (m + 2))) ||
+      (s = A((void**)&k->red, sizeof(double2) * (2 * m + 3))) ||
+      (s = A((void**)&k->Gd, sizeof(double2) * (size_t)(m + 1) * (m + 1))) ||
       (s = A((void**)&k->y, sizeof(double2) * (m + 1))) ||
       (s = A((void**)&k->dsc, sizeof(double) * 8))) {
     krylov_destroy(h, k);
@@ -528,16 +670,6 @@ static mcmg_status enqueue_restart(Krylov* k) {
   return MCMG_OK;
 }
 
-static mcmg_status multidot(Krylov* k, int nv, bool self, double2* out, double2* out_host) {
-  const int ktot = nv + (self ? 1 : 0);
-  dim3 grid((unsigned)k->nblk, (unsigned)((ktot + KV - 1) / KV));
-  k_multidot<float4><<<grid, RED_T, 0, k->st>>>(k->V, k->n, nv, ktot, k->w, k->n, k->part);
-  MCMG_CHECK_LAUNCH("multidot");
-  k_reduce_parts<<<ktot, RED_T, 0, k->st>>>(k->part, k->nblk, ktot, out, out_host);
-  MCMG_CHECK_LAUNCH("reduce_parts");
-  return MCMG_OK;
-}
-
 // The Arnoldi part of step j once z_j = MG(v_j) is in Z: w = A z_j, CGS2,
 // Givens, v_{j+1}.  No event.
 static mcmg_status enqueue_arnoldi(Krylov* k, int j) {
@@ -546,10 +678,18 @@ static mcmg_status enqueue_arnoldi(Krylov* k, int j) {
   float2* zj = k->Z + (size_t)j * n;
   MCMG_TRY(launch_apply_A_arnoldi(h->qdf, zj, k->w, h->g0, k->st));
   double2* mir = k->mir_d + (size_t)j * k->mir_stride;
-  MCMG_TRY(multidot(k, j + 1, true, k->d1, mir));
-  MCMG_TRY(launch_update(k->V, n, j + 1, k->d1, k->w, n, k->part, k->nblk, k->st));
-  MCMG_TRY(multidot(k, j + 1, false, k->d2, mir + (k->m + 2)));
-  MCMG_TRY(launch_update(k->V, n, j + 1, k->d2, k->w, n, k->part, k->nblk, k->st));
+  // one sweep over the basis: h1 = V^H w, |w|^2 and the Gram row V^H v_j;
+  // the second pass's coefficients from the Gram matrix; one update
+  const int width = 2 * j + 3;
+  dim3 grid((unsigned)k->nblk, (unsigned)((j + 2 + KV - 1) / KV));
+  k_multidot_gram<<<grid, RED_T, 0, k->st>>>(k->V, n, j, k->w, n, k->part);
+  MCMG_CHECK_LAUNCH("multidot_gram");
+  k_reduce_parts<<<width, RED_T, 0, k->st>>>(k->part, k->nblk, width, k->red, nullptr);
+  MCMG_CHECK_LAUNCH("reduce_parts");
+  k_gram_correct<<<1, 64, 0, k->st>>>(k->red, j, k->m + 1, k->Gd, k->d1, k->d2, k->dsum, mir,
+                                      k->m);
+  MCMG_CHECK_LAUNCH("gram_correct");
+  MCMG_TRY(launch_update(k->V, n, j + 1, k->dsum, k->w, n, k->part, k->nblk, k->st));
   k_reduce_scalar<<<1, RED_T, 0, k->st>>>(k->part, k->nblk, k->dsc + 3,
                                           &mir[2 * k->m + 4].x);
   MCMG_CHECK_LAUNCH("reduce_scalar");
