@@ -53,7 +53,7 @@ GPU_ITERS = {"helm3d_n256_grf": 227, "helm2d_n1024_layers": 8690}
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # (workload, precision, level, kind); the profile summaries record the
 # command and the scaling.  A key is dropped when its kernel changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("helm3d_n256_grf", "fp32tc", 1, "step"): 1074503936 + 253044736}
 FP32_LANES_PER_SM = 128
 NUM_SMS = 148
 
