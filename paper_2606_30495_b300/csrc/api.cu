@@ -340,10 +340,18 @@ static std::vector<float2> transpose_blocks(const double* src, int nb, int co_n,
   return v;
 }
 
+// Host -> device upload ordered on the setup stream st.  A synchronous
+// cudaMemcpy from pageable memory returns once the data is staged, and the
+// setup kernels run on a non-blocking stream that does not wait for the
+// legacy stream's copy: with the GPU busy (other requests' solves) a kernel
+// could read the buffer before the copy had landed.  cudaMemcpyAsync on st
+// orders the copy before the kernels that read it (the pageable source is
+// staged before the call returns, so it may be released at once).
 template <typename T>
-static mcmg_status upload(mcmg_handle_s* h, DevArena& a, const std::vector<T>& v, T** out) {
+static mcmg_status upload(mcmg_handle_s* h, DevArena& a, const std::vector<T>& v, T** out,
+                          cudaStream_t st) {
   MCMG_TRY(dev_alloc(h, a, (void**)out, sizeof(T) * std::max<size_t>(v.size(), 1)));
-  MCMG_CUDA(cudaMemcpy(*out, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  MCMG_CUDA(cudaMemcpyAsync(*out, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
   return MCMG_OK;
 }
 
@@ -427,7 +435,7 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
   auto cleanup = [&]() { arena_free(h, tmp); };
   mcmg_status s;
   if ((s = dev_alloc(h, tmp, (void**)&c_dev, sizeof(double) * N))) return cleanup(), s;
-  MCMG_CUDA(cudaMemcpy(c_dev, m->c, sizeof(double) * N, cudaMemcpyHostToDevice));
+  MCMG_CUDA(cudaMemcpyAsync(c_dev, m->c, sizeof(double) * N, cudaMemcpyHostToDevice, st));
   if ((s = dev_alloc(h, h->arena, (void**)&h->q32, sizeof(float2) * N))) return cleanup(), s;
   if ((s = dev_alloc(h, h->arena, (void**)&h->q64, sizeof(double2) * N))) return cleanup(), s;
   if ((s = launch_make_q(c_dev, omega, m->sponge_width, m->gamma_max, g0, h->q32, h->q64, st)))
@@ -455,15 +463,15 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
       for (int i = 0; i < ns && i < 2 * 8 + 1; ++i)
         lv.ssig[i] = fnv(base, lb[l].Ws + (size_t)2 * i * C * C, sizeof(double) * 2 * C * C);
     }
-    if ((s = upload(h, h->arena, transpose_blocks(lb[l].W, T, C, C), &lv.Wt)) ||
-        (s = upload(h, h->arena, transpose_blocks(lb[l].KA, 1, C, C), &lv.KAt)) ||
-        (s = upload(h, h->arena, transpose_blocks(lb[l].KS, 1, C, C), &lv.KSt)) ||
-        (s = upload(h, h->arena, transpose_blocks(lb[l].Ws, std::max(ns, 1), C, C), &lv.Wsmt)))
+    if ((s = upload(h, h->arena, transpose_blocks(lb[l].W, T, C, C), &lv.Wt, st)) ||
+        (s = upload(h, h->arena, transpose_blocks(lb[l].KA, 1, C, C), &lv.KAt, st)) ||
+        (s = upload(h, h->arena, transpose_blocks(lb[l].KS, 1, C, C), &lv.KSt, st)) ||
+        (s = upload(h, h->arena, transpose_blocks(lb[l].Ws, std::max(ns, 1), C, C), &lv.Wsmt, st)))
       return cleanup(), s;
     if (l < L - 1) {
       const int Cn = lv.Cn;
-      if ((s = upload(h, h->arena, transpose_blocks(lb[l].R, T3, Cn, C), &lv.Rt)) ||
-          (s = upload(h, h->arena, transpose_blocks(lb[l].P, T3, C, Cn), &lv.Pt)))
+      if ((s = upload(h, h->arena, transpose_blocks(lb[l].R, T3, Cn, C), &lv.Rt, st)) ||
+          (s = upload(h, h->arena, transpose_blocks(lb[l].P, T3, C, Cn), &lv.Pt, st)))
         return cleanup(), s;
     }
     if ((s = dev_alloc(h, h->arena, (void**)&lv.a, sizeof(float2) * lv.g.nodes() * C)) ||
@@ -489,8 +497,8 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
       uint4* dst = nullptr;
       if ((s = dev_alloc(h, h->arena, (void**)&dst, host.size() * sizeof(uint16_t))))
         return cleanup(), s;
-      MCMG_CUDA(cudaMemcpy(dst, host.data(), host.size() * sizeof(uint16_t),
-                           cudaMemcpyHostToDevice));
+      MCMG_CUDA(cudaMemcpyAsync(dst, host.data(), host.size() * sizeof(uint16_t),
+                                cudaMemcpyHostToDevice, st));
       lv.use_ts = true;
       lv.ts_prec = MCMG_BF16;
       lv.ts_mats = dst;
@@ -513,7 +521,8 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
       uint4* dst = nullptr;
       if ((s = dev_alloc(h, h->arena, (void**)&dst, host.size() * sizeof(float))))
         return cleanup(), s;
-      MCMG_CUDA(cudaMemcpy(dst, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice));
+      MCMG_CUDA(cudaMemcpyAsync(dst, host.data(), host.size() * sizeof(float),
+                                cudaMemcpyHostToDevice, st));
       lv.use_ts = true;
       lv.ts_prec = MCMG_FP32_TC;
       lv.ts_mats = dst;
@@ -557,8 +566,8 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
       if ((s = dev_alloc(h, h->arena, (void**)&dr, hr.size())) ||
           (s = dev_alloc(h, h->arena, (void**)&dp, hp.size())))
         return cleanup(), s;
-      MCMG_CUDA(cudaMemcpy(dr, hr.data(), hr.size(), cudaMemcpyHostToDevice));
-      MCMG_CUDA(cudaMemcpy(dp, hp.data(), hp.size(), cudaMemcpyHostToDevice));
+      MCMG_CUDA(cudaMemcpyAsync(dr, hr.data(), hr.size(), cudaMemcpyHostToDevice, st));
+      MCMG_CUDA(cudaMemcpyAsync(dp, hp.data(), hp.size(), cudaMemcpyHostToDevice, st));
       lv.ts_R = dr;
       lv.ts_P = dp;
       if (xts_block_pair(lv.g.d, Cn, C)) {
@@ -591,7 +600,7 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
         }
         uint4* db = nullptr;
         if ((s = dev_alloc(h, h->arena, (void**)&db, hb.size()))) return cleanup(), s;
-        MCMG_CUDA(cudaMemcpy(db, hb.data(), hb.size(), cudaMemcpyHostToDevice));
+        MCMG_CUDA(cudaMemcpyAsync(db, hb.data(), hb.size(), cudaMemcpyHostToDevice, st));
         lv.ts_Pb = db;
       }
     }
@@ -602,7 +611,7 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
       vl[c2] = make_float2((float)gl[2 * c2], (float)gl[2 * c2 + 1]);
       vp[c2] = make_float2((float)gp[2 * c2], (float)gp[2 * c2 + 1]);
     }
-    if ((s = upload(h, h->arena, vl, &h->lift)) || (s = upload(h, h->arena, vp, &h->proj)))
+    if ((s = upload(h, h->arena, vl, &h->lift, st)) || (s = upload(h, h->arena, vp, &h->proj, st)))
       return cleanup(), s;
   }
   // ---- Algorithm 1 on the device
@@ -612,7 +621,7 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
   if ((s = launch_setup_input(h->q64, m_in, g0, st))) return cleanup(), s;
   {
     std::vector<float> wv = to_f32(flw, (size_t)2 * C0 * 2 * T3), bv = to_f32(flb, 2 * C0);
-    if ((s = upload(h, tmp, wv, &fw)) || (s = upload(h, tmp, bv, &fb))) return cleanup(), s;
+    if ((s = upload(h, tmp, wv, &fw, st)) || (s = upload(h, tmp, bv, &fb, st))) return cleanup(), s;
     if ((s = dev_alloc(h, tmp, (void**)&net_a, sizeof(float) * 2 * C0 * N))) return cleanup(), s;
     if ((s = launch_conv3_gelu(m_in, 2, net_a, 2 * C0, fw, fb, g0, 1, st))) return cleanup(), s;
   }
@@ -623,7 +632,7 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
     const long long nl = lv.g.nodes();
     std::vector<float> sw = to_f32(lb[l].fsw, (size_t)2 * C * 2 * C * T3), sb = to_f32(lb[l].fsb, 2 * C);
     float *dsw, *dsb;
-    if ((s = upload(h, tmp, sw, &dsw)) || (s = upload(h, tmp, sb, &dsb))) return cleanup(), s;
+    if ((s = upload(h, tmp, sw, &dsw, st)) || (s = upload(h, tmp, sb, &dsb, st))) return cleanup(), s;
     if ((s = dev_alloc(h, tmp, (void**)&net_s, sizeof(float) * 2 * C * nl))) return cleanup(), s;
     if ((s = launch_conv3_gelu(net_a, 2 * C, net_s, 2 * C, dsw, dsb, lv.g, 1, st)))
       return cleanup(), s;
@@ -635,7 +644,7 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
       const Grid gc = lv.g.coarse();
       std::vector<float> aw = to_f32(lb[l].faw, (size_t)2 * Cn * 2 * C * T3), ab = to_f32(lb[l].fab, 2 * Cn);
       float *daw, *dab;
-      if ((s = upload(h, tmp, aw, &daw)) || (s = upload(h, tmp, ab, &dab))) return cleanup(), s;
+      if ((s = upload(h, tmp, aw, &daw, st)) || (s = upload(h, tmp, ab, &dab, st))) return cleanup(), s;
       if ((s = dev_alloc(h, tmp, (void**)&net_n, sizeof(float) * 2 * Cn * gc.nodes())))
         return cleanup(), s;
       if ((s = launch_conv3_gelu(net_a, 2 * C, net_n, 2 * Cn, daw, dab, lv.g, 2, st)))

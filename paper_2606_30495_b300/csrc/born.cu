@@ -184,10 +184,14 @@ mcmg_status born_prepare(mcmg_handle_s* h) {
       tw[k] = make_double2(std::cos(2.0 * M_PI * k / N), -std::sin(2.0 * M_PI * k / N));
     MCMG_TRY(dev_alloc(h, h->arena, (void**)&h->born_sym[a], sizeof(double) * N));
     MCMG_TRY(dev_alloc(h, h->arena, (void**)&h->born_tw[a], sizeof(double2) * tw.size()));
-    MCMG_CUDA(cudaMemcpy(h->born_sym[a], s.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
-    MCMG_CUDA(cudaMemcpy(h->born_tw[a], tw.data(), sizeof(double2) * tw.size(),
-                         cudaMemcpyHostToDevice));
+    // ordered on the handle's stream and waited below: a synchronous copy
+    // from pageable memory may still be in flight when it returns
+    MCMG_CUDA(cudaMemcpyAsync(h->born_sym[a], s.data(), sizeof(double) * N,
+                              cudaMemcpyHostToDevice, h->stream));
+    MCMG_CUDA(cudaMemcpyAsync(h->born_tw[a], tw.data(), sizeof(double2) * tw.size(),
+                              cudaMemcpyHostToDevice, h->stream));
   }
+  MCMG_CUDA(cudaStreamSynchronize(h->stream));
   // the largest pass asks for 64 KB of shared memory
   MCMG_CUDA(cudaFuncSetAttribute(k_fft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  64 * 1024));

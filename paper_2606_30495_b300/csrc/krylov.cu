@@ -190,17 +190,24 @@ __global__ void __launch_bounds__(RED_T) k_multidot(const float2* __restrict__ V
 // basis vector i <= j, a_i = conj(v_i) w and b_i = conj(v_i) v_j (a row of the
 // Gram matrix V^H V), and |w|^2.  Partials part[(bx * width + idx) * 2 + {0,1}]
 // with width = 2j + 3: idx i -> a_i, j + 1 -> |w|^2, j + 2 + i -> b_i.
-// Double-float accumulation (the products of two FP32 values are exact);
-// each warp sums its values by shuffles and warp partials are added in warp
-// order, so the result does not depend on scheduling.
+// a_i and |w|^2 accumulate in double-float.  b_i only has to resolve the
+// basis' storage rounding (~6e-8) to well below it: each thread sums its few
+// dozen products in FP32 (error ~1e-13 of the unit norms), and the thread
+// partials are added in double-float.  Each warp sums its values by shuffles
+// and warp partials are added in warp order, so the result does not depend
+// on scheduling.
 __global__ void __launch_bounds__(RED_T, 2) k_multidot_gram(const float2* __restrict__ V, long long ldv,
                                                          int j, const float4* __restrict__ w,
                                                          long long n, double* __restrict__ part) {
   const int k = j + 1, width = 2 * j + 3;
   const int i0 = blockIdx.y * KV;
-  DF ar[KV], ai[KV], br[KV], bi[KV];
+  DF ar[KV], ai[KV];
+  float br[KV], bi[KV];
 #pragma unroll
-  for (int i = 0; i < KV; ++i) ar[i] = ai[i] = br[i] = bi[i] = DF{0.f, 0.f};
+  for (int i = 0; i < KV; ++i) {
+    ar[i] = ai[i] = DF{0.f, 0.f};
+    br[i] = bi[i] = 0.f;
+  }
   const float2* vj = V + (long long)j * ldv;
   auto accumulate = [&](const float4 wv, const float2 uj, const float2 (&vv)[KV]) {
     const DF wx{wv.x, wv.y}, wy{wv.z, wv.w};
@@ -214,21 +221,32 @@ __global__ void __launch_bounds__(RED_T, 2) k_multidot_gram(const float2* __rest
         df_add(ar[i], df_mul(v.y, wy.hi, wy.lo));
         df_add(ai[i], df_mul(v.x, wy.hi, wy.lo));
         df_add(ai[i], df_mul(-v.y, wx.hi, wx.lo));
-        // conj(v) v_j, exact products of FP32 values
-        df_add(br[i], df_mul(v.x, uj.x, 0.f));
-        df_add(br[i], df_mul(v.y, uj.y, 0.f));
-        df_add(bi[i], df_mul(v.x, uj.y, 0.f));
-        df_add(bi[i], df_mul(-v.y, uj.x, 0.f));
+        // conj(v) v_j in FP32 per thread
+        br[i] = __fmaf_rn(v.x, uj.x, __fmaf_rn(v.y, uj.y, br[i]));
+        bi[i] = __fmaf_rn(v.x, uj.y, __fmaf_rn(-v.y, uj.x, bi[i]));
       } else if (ii == k) {  // |w|^2
         df_add(ar[i], df_sq(wx));
         df_add(ar[i], df_sq(wy));
       }
     }
   };
-  // one element per iteration (the four accumulators per vector leave no
-  // registers for a second one); two blocks per SM keep the loads in flight
+  // two elements per iteration, every load issued before the arithmetic
   const long long stride = (long long)gridDim.x * RED_T;
-  for (long long p = (long long)blockIdx.x * RED_T + threadIdx.x; p < n; p += stride) {
+  long long p = (long long)blockIdx.x * RED_T + threadIdx.x;
+  for (; p + stride < n; p += 2 * stride) {
+    const float4 wa = w[p], wb = w[p + stride];
+    const float2 ua = vj[p], ub = vj[p + stride];
+    float2 va[KV], vb[KV];
+#pragma unroll
+    for (int i = 0; i < KV; ++i) {
+      const int ii = i0 + i < k ? i0 + i : 0;
+      va[i] = V[(long long)ii * ldv + p];
+      vb[i] = V[(long long)ii * ldv + p + stride];
+    }
+    accumulate(wa, ua, va);
+    accumulate(wb, ub, vb);
+  }
+  if (p < n) {
     const float4 wa = w[p];
     const float2 ua = vj[p];
     float2 va[KV];
@@ -250,7 +268,7 @@ __global__ void __launch_bounds__(RED_T, 2) k_multidot_gram(const float2* __rest
 #pragma unroll
   for (int i = 0; i < KV; ++i) {
     const DF r0 = warp_reduce(ar[i]), r1 = warp_reduce(ai[i]);
-    const DF r2 = warp_reduce(br[i]), r3 = warp_reduce(bi[i]);
+    const DF r2 = warp_reduce(DF{br[i], 0.f}), r3 = warp_reduce(DF{bi[i], 0.f});
     if (lane == 0) {
       sh[4 * i][wid] = r0;
       sh[4 * i + 1][wid] = r1;
@@ -517,19 +535,39 @@ __global__ void k_stationary_update(const float2* __restrict__ z, const double* 
 }
 
 // u += sum_{i<k} y_i Z_i (complex128 accumulate)
+// (double-float accumulation: y is split once per block into shared memory,
+// the products with the FP32 z are exact up to lo * lo, and only the final
+// sum is added to u in FP64)
 __global__ void k_update_x(const float2* __restrict__ Z, long long ldz, int k,
                            const double2* __restrict__ y, double2* __restrict__ u, long long n) {
-  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
-  double sr = 0.0, si = 0.0;
-  for (int i = 0; i < k; ++i) {
-    const float2 z = Z[(long long)i * ldz + p];
-    const double2 yy = y[i];
-    sr += yy.x * z.x - yy.y * z.y;
-    si += yy.x * z.y + yy.y * z.x;
+  constexpr int CH = 64;                 // coefficients staged per chunk
+  __shared__ DF ys[2 * CH];
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = p < n;
+  DF sr{0.f, 0.f}, si{0.f, 0.f};
+  for (int base = 0; base < k; base += CH) {
+    const int cnt = k - base < CH ? k - base : CH;
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const double2 yy = y[base + i];
+      ys[2 * i] = df_from(yy.x);
+      ys[2 * i + 1] = df_from(yy.y);
+    }
+    __syncthreads();
+    if (!live) continue;
+    for (int i = 0; i < cnt; ++i) {
+      const float2 z = Z[(long long)(base + i) * ldz + p];
+      const DF yx = ys[2 * i], yy = ys[2 * i + 1];
+      // y z = (yx zx - yy zy) + i (yx zy + yy zx)
+      df_add(sr, df_mul(z.x, yx.hi, yx.lo));
+      df_add(sr, df_mul(-z.y, yy.hi, yy.lo));
+      df_add(si, df_mul(z.y, yx.hi, yx.lo));
+      df_add(si, df_mul(z.x, yy.hi, yy.lo));
+    }
   }
+  if (!live) return;
   const double2 o = u[p];
-  u[p] = make_double2(o.x + sr, o.y + si);
+  u[p] = make_double2(o.x + df_to(sr), o.y + df_to(si));
 }
 
 // ---------------------------------------------------------------------------

@@ -229,3 +229,52 @@ def test_several_frequencies_of_one_medium_share_batched_vcycles():
         for h in hs:
             h.close()
         ctx.close()
+
+
+def test_setup_while_the_server_runs_gives_the_features_of_an_idle_setup():
+    """Requests set up and submitted one after another while the earlier ones
+    run (as a server's arrivals are): every handle computes the same features
+    (bit for bit) as a handle of the same medium set up on an idle GPU, and
+    every request converges.  Setup uploads its weights and medium on the
+    stream its kernels run on; copies left to the legacy stream could land
+    after the kernels had read the buffers once the GPU was busy, which
+    corrupted coarse-level features and failed requests at their first step."""
+    from paper_2606_30495_b300 import mcmg
+    base = I.serving_weights()
+    reqs = [r for r in I.serving_requests(count=256) if r["n"] <= 512][:24]
+    data = [I.serving_request_inputs(r, base) for r in reqs]
+    ctx = mcmg.Context(0)
+    hs, bufs, tickets = [], [], []
+    try:
+        for r, (c, om, w, f) in zip(reqs, data):
+            h = mcmg.Handle(ctx, c, om, 16, 1.0, w, precision=mcmg.BF16)
+            fd = torch.from_numpy(f).cuda()
+            u = torch.zeros_like(fd)
+            torch.cuda.synchronize()
+            tickets.append(ctx.submit(h, fd, u, tol=1e-6, restart_m=30, max_iters=5000,
+                                      nrhs=r["nrhs"]))
+            hs.append(h)
+            bufs.append((fd, u))
+        ctx.drain()
+        for k, t in enumerate(tickets):
+            st, info = ctx.poll(t)
+            assert st == 0 and info["converged"], (k, reqs[k]["n"], st, info)
+        for r, h, (c, om, w, f) in zip(reqs, hs, data):
+            fresh = mcmg.Handle(ctx, c, om, 16, 1.0, w, precision=mcmg.BF16)
+            try:
+                for l in range(r["levels"]):
+                    n = (r["n"] >> l) ** 2
+                    C = w["channels"][l]
+                    for which in (0, 1):
+                        a1 = torch.zeros((n, C), dtype=torch.complex64, device="cuda")
+                        a2 = torch.zeros_like(a1)
+                        h.get_feature(l, which, a1)
+                        fresh.get_feature(l, which, a2)
+                        torch.cuda.synchronize()
+                        assert torch.equal(a1, a2), (r["n"], l, which)
+            finally:
+                fresh.close()
+    finally:
+        for h in hs:
+            h.close()
+        ctx.close()
