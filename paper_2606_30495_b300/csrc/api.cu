@@ -108,6 +108,13 @@ void arena_free(mcmg_handle_s* h, DevArena& a) {
 mcmg_status vwork_create(mcmg_handle_s* h, int nrhs, VWork** out) {
   VWork* w = new VWork();
   w->nrhs = nrhs;
+  {
+    mcmg_status s = dev_alloc(h, w->arena, (void**)&w->cells, 2 * sizeof(float2*));
+    if (s != MCMG_OK) {
+      vwork_destroy(h, w);
+      return s;
+    }
+  }
   for (int l = 0; l < h->L; ++l) {
     const Level& L = h->lv[l];
     size_t b = sizeof(float2) * (size_t)L.g.nodes() * L.C * nrhs;
@@ -132,18 +139,33 @@ void vwork_destroy(mcmg_handle_s* h, VWork* w) {
   delete w;
 }
 
+// Whether a one-field V-cycle of h can take the lift and the projection
+// inside its level-0 steps (see TsParams::r_cell).
+static bool can_fuse_io(const mcmg_handle_s* h) {
+  return h->L > 1 && h->lv[0].nu_post >= 1 && ts_fused_io_supported(h->lv[0]);
+}
+
 // The level sequence of Algorithm 2 on workspace w, nrhs fields, after r_1
-// has been written to w->r[0].  Returns the buffer that holds e_1.
+// has been written to w->r[0].  Returns the buffer that holds e_1.  With
+// `fused` (one field, can_fuse_io): level 0 reads the scalar r through
+// w->cells[0] and lifts it, and its last post-smoothing step writes the
+// projected e through w->cells[1]; *e1_out is then null.
 static mcmg_status enqueue_levels(mcmg_handle_s* h, VWork* w, int nrhs, cudaStream_t st,
-                                  float2** e1_out) {
+                                  float2** e1_out, bool fused = false) {
   const int L = h->L;
   float2* ecur[MCMG_MAX_LEVELS];
+  const float2* const* rcell = w->cells;
+  float2* const* zcell = w->cells + 1;
   for (int l = 0; l < L; ++l) {                       // down cycle
     const Level& lv = h->lv[l];
+    const bool io = fused && l == 0;
     float2* cur = nullptr;
     for (int i = 0; i < lv.nu_pre; ++i) {
       float2* out = (cur == w->e[l]) ? w->e2[l] : w->e[l];
-      MCMG_TRY(launch_smooth(lv, i, w->r[l], cur, out, 0, nrhs, st));
+      if (io)
+        MCMG_TRY(launch_smooth_ts_io(lv, i, rcell, h->lift, cur, out, nullptr, nullptr, 0, st));
+      else
+        MCMG_TRY(launch_smooth(lv, i, w->r[l], cur, out, 0, nrhs, st));
       cur = out;
     }
     if (!cur) {
@@ -152,26 +174,36 @@ static mcmg_status enqueue_levels(mcmg_handle_s* h, VWork* w, int nrhs, cudaStre
     }
     ecur[l] = cur;
     if (l < L - 1) {                                  // residual + restriction
-      MCMG_TRY(launch_smooth(lv, 0, w->r[l], cur, w->t[l], 1, nrhs, st));
+      if (io)
+        MCMG_TRY(launch_smooth_ts_io(lv, 0, rcell, h->lift, cur, w->t[l], nullptr, nullptr, 1, st));
+      else
+        MCMG_TRY(launch_smooth(lv, 0, w->r[l], cur, w->t[l], 1, nrhs, st));
       MCMG_TRY(launch_restrict(lv, w->t[l], w->r[l + 1], nrhs, st));
     }
   }
   for (int l = L - 2; l >= 0; --l) {                  // up cycle
     const Level& lv = h->lv[l];
+    const bool io = fused && l == 0;
     MCMG_TRY(launch_prolong_add(lv, ecur[l + 1], ecur[l], nrhs, st));
     for (int i = 0; i < lv.nu_post; ++i) {
       float2* out = (ecur[l] == w->e[l]) ? w->e2[l] : w->e[l];
-      MCMG_TRY(launch_smooth(lv, lv.nu_pre + i, w->r[l], ecur[l], out, 0, nrhs, st));
+      if (io) {
+        const bool last = i == lv.nu_post - 1;
+        MCMG_TRY(launch_smooth_ts_io(lv, lv.nu_pre + i, rcell, h->lift, ecur[l], out,
+                                     last ? zcell : nullptr, last ? h->proj : nullptr, 0, st));
+      } else {
+        MCMG_TRY(launch_smooth(lv, lv.nu_pre + i, w->r[l], ecur[l], out, 0, nrhs, st));
+      }
       ecur[l] = out;
     }
   }
-  *e1_out = ecur[0];
+  *e1_out = fused ? nullptr : ecur[0];
   return MCMG_OK;
 }
 
 // Capture the level sequence for `count` fields of workspace w as a graph.
 static mcmg_status capture_levels_n(mcmg_handle_s* h, VWork* w, int count, cudaGraphExec_t* exec,
-                                    unsigned long long* kernels) {
+                                    unsigned long long* kernels, bool fused = false) {
   cudaStream_t cs;
   MCMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
@@ -182,7 +214,7 @@ static mcmg_status capture_levels_n(mcmg_handle_s* h, VWork* w, int count, cudaG
     return cuda_fail(e, "cudaStreamBeginCapture");
   }
   const unsigned long long before = g_launches.load();
-  mcmg_status s = enqueue_levels(h, w, count, cs, &e1);
+  mcmg_status s = enqueue_levels(h, w, count, cs, &e1, fused);
   *kernels = g_launches.load() - before;
   g_launches.fetch_sub(*kernels);   // counted when the graph runs
   e = cudaStreamEndCapture(cs, &graph);
@@ -195,7 +227,7 @@ static mcmg_status capture_levels_n(mcmg_handle_s* h, VWork* w, int count, cudaG
   e = cudaGraphInstantiate(exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-  w->e1 = e1;
+  if (!fused) w->e1 = e1;
   return MCMG_OK;
 }
 
@@ -204,13 +236,29 @@ static void refresh_graphs(mcmg_handle_s* h, VWork* w) {
   if (w->shape_gen == h->shape_gen) return;
   if (w->graph) cudaGraphExecDestroy(w->graph);
   w->graph = nullptr;
+  w->graph_fused = false;
   for (auto& kv : w->sub) cudaGraphExecDestroy(kv.second.first);
   w->sub.clear();
   w->shape_gen = h->shape_gen;
 }
 
-static mcmg_status capture_levels(mcmg_handle_s* h, VWork* w) {
-  return capture_levels_n(h, w, w->nrhs, &w->graph, &w->graph_kernels);
+// The graph of all w->nrhs fields, captured fused or not as asked (a graph
+// of the other kind is dropped first).
+static mcmg_status ensure_graph(mcmg_handle_s* h, VWork* w, bool fused) {
+  if (w->graph && w->graph_fused != fused) {
+    cudaGraphExecDestroy(w->graph);
+    w->graph = nullptr;
+  }
+  if (!w->graph) {
+    MCMG_TRY(capture_levels_n(h, w, w->nrhs, &w->graph, &w->graph_kernels, fused));
+    w->graph_fused = fused;
+  }
+  return MCMG_OK;
+}
+
+__global__ void k_set_cells(float2** cells, const float2* r, float2* e) {
+  cells[0] = const_cast<float2*>(r);
+  cells[1] = e;
 }
 
 mcmg_status vcycle_run_batch(mcmg_handle_s* h, VWork* w, const float2* const* srcs,
@@ -225,7 +273,7 @@ mcmg_status vcycle_run_batch(mcmg_handle_s* h, VWork* w, const float2* const* sr
   cudaGraphExec_t exec;
   unsigned long long kernels;
   if (count == w->nrhs) {
-    if (!w->graph) MCMG_TRY(capture_levels(h, w));
+    MCMG_TRY(ensure_graph(h, w, false));
     exec = w->graph;
     kernels = w->graph_kernels;
   } else {
@@ -253,11 +301,18 @@ mcmg_status vcycle_run(mcmg_handle_s* h, VWork* w, const float2* r, float2* e, i
   }
   const Level& l0 = h->lv[0];
   refresh_graphs(h, w);
-  MCMG_TRY(launch_lift(r, h->lift, w->r[0], l0.C, l0.g.nodes(), nrhs, st));
-  if (!w->graph) MCMG_TRY(capture_levels(h, w));
+  const bool fused = nrhs == 1 && can_fuse_io(h);
+  if (fused) {
+    // level 0 lifts r and projects e itself: only their addresses change
+    k_set_cells<<<1, 1, 0, st>>>(w->cells, r, e);
+    MCMG_CHECK_LAUNCH("set_cells");
+  } else {
+    MCMG_TRY(launch_lift(r, h->lift, w->r[0], l0.C, l0.g.nodes(), nrhs, st));
+  }
+  MCMG_TRY(ensure_graph(h, w, fused));
   MCMG_CUDA(cudaGraphLaunch(w->graph, st));
   count_launch(w->graph_kernels);
-  MCMG_TRY(launch_project(w->e1, h->proj, e, l0.C, l0.g.nodes(), nrhs, st));
+  if (!fused) MCMG_TRY(launch_project(w->e1, h->proj, e, l0.C, l0.g.nodes(), nrhs, st));
   return MCMG_OK;
 }
 

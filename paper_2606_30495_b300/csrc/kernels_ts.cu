@@ -86,6 +86,17 @@ struct TsParams {
   // that e_in is non-null exactly when every descriptor's e_in is
   const TsField* fields;
   int nfields;
+  // Level 0 of a one-field V-cycle (k_smooth_ts only; null otherwise): the
+  // lift and the projection of Algorithm 2 folded into the step.  r_cell
+  // holds the address of the scalar residual r and the step reads
+  // r_1 = lift (x) r[n] in place of p.r; z_cell holds the address of the
+  // scalar output, and the step writes sum_c proj[c] e'[n][c] there in place
+  // of e'.  The addresses sit in device cells so that a captured graph
+  // follows the caller's buffers.
+  const float2* const* r_cell;
+  const float2* lift;
+  float2* const* z_cell;
+  const float2* proj;
 };
 
 namespace ts {
@@ -349,7 +360,20 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Cfg<K2, P>::PER_SM) k_smooth_
 
   for (int item = blockIdx.x; item < p.items; item += gridDim.x) {
     const ts::Tile tv = ts::tile_of(p, item, C);
-    const float2* r = tv.r;
+    // r_1 row of node nn: read, or lifted from the scalar residual
+    auto load_r = [&](float (&v)[K2], long long nn) {
+      if (p.r_cell) {
+        const float2 rs = (*p.r_cell)[nn];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {       // as k_lift: bit for bit
+          const float2 t = cmul_rn(__ldg(p.lift + c), rs);
+          v[2 * c] = t.x;
+          v[2 * c + 1] = t.y;
+        }
+      } else {
+        ts::load_row<K2>(v, tv.r, nn, true);
+      }
+    };
     const float2* ein = tv.e_in;
     float2* out = tv.out;
     const long long n = tv.n0 + tid;
@@ -397,7 +421,8 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Cfg<K2, P>::PER_SM) k_smooth_
           const bool v = nbr(j + 2, nb);
           ts::load_row<K2>(cur, ein, nb, v);
         } else {
-          ts::load_row<K2>(cur, j == NT - 2 ? r : tv.a, nc, true);   // rbuf, abuf
+          if (j == NT - 2) load_r(cur, nc);                          // rbuf
+          else ts::load_row<K2>(cur, tv.a, nc, true);                 // abuf
         }
         tc::fence_before();
         ok = __syncthreads_and(ok);
@@ -442,7 +467,7 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Cfg<K2, P>::PER_SM) k_smooth_
       }
     } else {
       // first pre-smoothing step: t = r
-      ts::load_row<K2>(abuf, r, nc, true);
+      load_r(abuf, nc);
       ts::load_row<K2>(rbuf, tv.s, nc, true);
 #pragma unroll
       for (int c0 = 0; c0 < K2; c0 += 16) {
@@ -494,6 +519,7 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Cfg<K2, P>::PER_SM) k_smooth_
       }
       ok = wait_bar(1) && ok;
       tc::fence_after();
+      float2 zsum = make_float2(0.f, 0.f);          // projection (z_cell)
 #pragma unroll
       for (int c0 = 0; c0 < K2; c0 += 16) {
         float uv[16];
@@ -502,8 +528,15 @@ __global__ void __launch_bounds__(ts::THREADS, ts::Cfg<K2, P>::PER_SM) k_smooth_
 #pragma unroll
           for (int k = 0; k < 16; ++k) uv[k] += abuf[c0 + k];
         }
-        if (row_ok) ts::store16(out, C, n, c0, uv);
+        if (p.z_cell) {                     // as k_project: channels in order
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            cfma(zsum, __ldg(p.proj + c0 / 2 + k), make_float2(uv[2 * k], uv[2 * k + 1]));
+        } else if (row_ok) {
+          ts::store16(out, C, n, c0, uv);
+        }
       }
+      if (p.z_cell && row_ok) (*p.z_cell)[n] = zsum;
     }
     tc::fence_before();   // this tile's TMEM reads precede the next tile's MMAs
   }
@@ -1412,6 +1445,45 @@ mcmg_status launch_smooth_ts(const Level& L, int step, const float2* r, const fl
   }
   if (tf) return d3 ? ts_dispatch<3, 1, 1>(L.C, p, nrhs, st) : ts_dispatch<2, 1, 1>(L.C, p, nrhs, st);
   return d3 ? ts_dispatch<3, 0, 1>(L.C, p, nrhs, st) : ts_dispatch<2, 0, 1>(L.C, p, nrhs, st);
+}
+
+bool ts_fused_io_supported(const Level& L) {
+  // the levels whose step runs k_smooth_ts (one thread per row, all channels)
+  return L.use_ts && (L.C == 8 || (L.C == 16 && L.ts_prec == MCMG_FP32_TC));
+}
+
+mcmg_status launch_smooth_ts_io(const Level& L, int step, const float2* const* r_cell,
+                                const float2* lift, const float2* e_in, float2* out,
+                                float2* const* z_cell, const float2* proj, int mode,
+                                cudaStream_t st) {
+  if (!ts_fused_io_supported(L) || (mode == 1 && !e_in) || (mode == 1 && z_cell)) {
+    set_error("fused lift / projection not available on this level");
+    return MCMG_ERR_ARG;
+  }
+  TsParams p{};
+  p.r_cell = r_cell;
+  p.lift = lift;
+  p.z_cell = z_cell;
+  p.proj = proj;
+  p.e_in = e_in;
+  p.out = out;
+  p.a = L.a;
+  p.s = L.s;
+  p.mats = L.ts_mats;
+  p.wi = 2 * L.g.d + 1 + 2 + step;
+  p.nx = L.g.nx;
+  p.ny = L.g.ny;
+  p.nz = L.g.nz;
+  p.nodes = L.g.nodes();
+  p.err = L.err;
+  const bool d3 = L.g.d == 3;
+  const bool tf = L.ts_prec == MCMG_FP32_TC;
+  if (mode == 0) {
+    if (tf) return d3 ? ts_dispatch<3, 1, 0>(L.C, p, 1, st) : ts_dispatch<2, 1, 0>(L.C, p, 1, st);
+    return d3 ? ts_dispatch<3, 0, 0>(L.C, p, 1, st) : ts_dispatch<2, 0, 0>(L.C, p, 1, st);
+  }
+  if (tf) return d3 ? ts_dispatch<3, 1, 1>(L.C, p, 1, st) : ts_dispatch<2, 1, 1>(L.C, p, 1, st);
+  return d3 ? ts_dispatch<3, 0, 1>(L.C, p, 1, st) : ts_dispatch<2, 0, 1>(L.C, p, 1, st);
 }
 
 mcmg_status launch_smooth_ts_fields(const Level& L, int step, const TsField* fields_dev,

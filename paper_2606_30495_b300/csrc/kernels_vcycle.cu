@@ -964,7 +964,7 @@ __global__ void k_lift(const float2* __restrict__ r, const float2* __restrict__ 
   long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= N * C) return;
   size_t off = (size_t)blockIdx.y * N;
-  r1[off * C + id] = cmul(lift[id % C], r[off + id / C]);
+  r1[off * C + id] = cmul_rn(lift[id % C], r[off + id / C]);
 }
 
 __global__ void k_project(const float2* __restrict__ e1, const float2* __restrict__ proj,
@@ -984,7 +984,7 @@ __global__ void k_lift_gather(const float2* const* __restrict__ srcs, const floa
   long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= N * C) return;
   const float2* r = srcs[blockIdx.y];
-  r1[(size_t)blockIdx.y * N * C + id] = cmul(lift[id % C], r[id / C]);
+  r1[(size_t)blockIdx.y * N * C + id] = cmul_rn(lift[id % C], r[id / C]);
 }
 
 __global__ void k_project_scatter(const float2* __restrict__ e1, const float2* __restrict__ proj,

@@ -21,6 +21,13 @@ namespace mcmg {
 __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+// a b with every rounding explicit, so that kernels computing the same
+// product (the lift in its own kernel and inside the level-0 step) agree bit
+// for bit whatever the compiler contracts elsewhere
+__device__ __forceinline__ float2 cmul_rn(float2 a, float2 b) {
+  return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)),
+                     __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
 __host__ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
   acc.x = fmaf(a.x, b.x, acc.x);
   acc.x = fmaf(-a.y, b.y, acc.x);
@@ -130,6 +137,15 @@ mcmg_status launch_smooth_ts(const Level& L, int step, const float2* r, const fl
 mcmg_status launch_smooth_ts_fields(const Level& L, int step, const TsField* fields_dev,
                                     const TsField* fields_host, int nf, bool has_e, int mode,
                                     cudaStream_t st);
+// Level 0 of a one-field V-cycle with the lift folded into the step's read
+// of r and, when z_cell is set (smoothing steps), the projection into its
+// write: r_cell and z_cell are device cells holding the scalar input and
+// output addresses.  Available where ts_fused_io_supported(L).
+bool ts_fused_io_supported(const Level& L);
+mcmg_status launch_smooth_ts_io(const Level& L, int step, const float2* const* r_cell,
+                                const float2* lift, const float2* e_in, float2* out,
+                                float2* const* z_cell, const float2* proj, int mode,
+                                cudaStream_t st);
 // complex C x C matrix -> its real 2C x 2C block form as a B operand: BF16
 // (4C^2 values), or TF32 hi and lo halves (2 * 4C^2 floats)
 void pack_ts_bf16(const float2* Mc, int C, uint16_t* out);
@@ -229,6 +245,11 @@ struct VWork {
   // graphs of the level sequence for fewer fields (batched solves), by count
   std::map<int, std::pair<cudaGraphExec_t, unsigned long long>> sub;
   unsigned shape_gen = 0;            // handle's shape generation the graphs were captured at
+  // one-field V-cycles with the lift and projection folded into level 0:
+  // cells[0] = the scalar input r, cells[1] = the scalar output e, written
+  // before each launch of a graph captured that way (graph_fused)
+  float2** cells = nullptr;
+  bool graph_fused = false;
   DevArena arena;
 };
 

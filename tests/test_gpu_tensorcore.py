@@ -279,6 +279,21 @@ def test_transfer_ts_many_items(ctx, prec, shape, channels):
         h.close()
 
 
+def test_vcycle_one_field(case):
+    """One-field V-cycles: where level 0 runs the small-channel tensor-core
+    step (C_0 = 8, or 16 with FP32-accurate mixing) the lift and the
+    projection are folded into its steps (input and output addresses through
+    device cells of the captured graph); two calls with different buffers
+    check that the graph follows them."""
+    prec, m, h = case
+    for seed in (44, 45):
+        r = I.complex_normal(m["shape"], rng(seed))
+        want = O.vcycle(m["w"], m["feats"], r)
+        e = torch.zeros(r.shape, dtype=torch.complex64, device="cuda")
+        h.vcycle(dev(r), e)
+        assert relerr(host(e), want) < _tols(prec)[1], seed
+
+
 def test_vcycle(case):
     prec, m, h = case
     r = I.complex_normal((2,) + m["shape"], rng(40))
