@@ -77,9 +77,9 @@ def parse():
                         "iterations inside the NVTX range 'solve' (ncu --nvtx --nvtx-include "
                         "'solve/'), then exit")
     p.add_argument("--profile-launch", default="",
-                   help="LEVEL,KIND[,REPS]: after setup, run only that smoothing launch class "
-                        "(KIND first | step | residual) REPS times (default 5) and exit; for "
-                        "profilers")
+                   help="LEVEL,KIND[,REPS]: after setup, run only that launch class of the "
+                        "V-cycle (KIND first | step | residual | restrict | prolong) REPS times "
+                        "(default 5) and exit; for profilers")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-iters", type=int, default=3)
     p.add_argument("--n", type=int, default=0,
@@ -373,9 +373,16 @@ def profile_launch(args, h, wl, torch, mcmg, ctx):
     e = torch.randn(shp, dtype=torch.complex64, device="cuda")
     o = torch.empty_like(e)
     stream = torch.cuda.Stream()
+    if kind in ("restrict", "prolong"):          # the level's transfer (setup's kernel)
+        Cn = wl["channels"][level + 1]
+        cshp = tuple(n >> (level + 1) for n in (wl["n"],) * wl["dim"]) + (Cn,)
+        rc = torch.empty(cshp, dtype=torch.complex64, device="cuda")
+        ec = torch.randn(cshp, dtype=torch.complex64, device="cuda")
     run = {"first": lambda: h.smooth(level, 0, r, None, o, stream=stream),
            "step": lambda: h.smooth(level, 0, r, e, o, stream=stream),
-           "residual": lambda: h.residual(level, r, e, o, stream=stream)}[kind]
+           "residual": lambda: h.residual(level, r, e, o, stream=stream),
+           "restrict": lambda: h.residual_restrict(level, r, e, rc, stream=stream),
+           "prolong": lambda: h.prolong_add(level, ec, e, stream=stream)}[kind]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):

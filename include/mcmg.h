@@ -330,14 +330,16 @@ mcmg_status mcmg_cgs2_noalloc(const void* V_dev, int k, size_t n, void* w_dev,
  * 2 restriction R_l, 3 prolongation P_l (ops 2 and 3 exist for
  * level < levels-1).  Each has several interchangeable kernels and thread
  * shapes with the same results up to FP32 rounding order; setup times them
- * on every level and keeps the fastest.  The last two shapes of ops 2 and 3
- * run on the tensor cores of tensor-core handles (MCMG_BF16, MCMG_FP32_TC),
- * with that handle's mixing precision: count-2 is the transfer per parity
- * class, where its input has 16, 32 or 64 channels (a restriction also 8)
- * and its output as many, half or twice as many; count-1 (prolongation
- * only) computes all parity classes of a coarse tile at once, where
- * C_{l+1} is 16, 32 or 64, C_l = C_{l+1} or C_{l+1} / 2 and
- * 2^d x 2 C_l <= 256.
+ * on every level and keeps the fastest.  The last three shapes of ops 2 and
+ * 3 run on the tensor cores of tensor-core handles (MCMG_BF16,
+ * MCMG_FP32_TC), with that handle's mixing precision: count-3 is the
+ * transfer per parity class, where its input has 16, 32 or 64 channels (a
+ * restriction also 8) and its output as many, half or twice as many;
+ * count-2 (prolongation only) computes all parity classes of a coarse tile
+ * at once, where C_{l+1} is 16, 32 or 64, C_l = C_{l+1} or C_{l+1} / 2 and
+ * 2^d x 2 C_l <= 256; count-1 (restriction only) stages the fine lines in
+ * shared memory, where C_l = 8, C_{l+1} is 8 or 16 and the coarse x extent
+ * is a multiple of 32.
  *   mcmg_kernel_shape_count: number of shapes of op (indices 0 .. count-1),
  *                            0 for an unknown op.
  *   mcmg_get_kernel_shape:   the shape `level` uses for op (*shape).

@@ -606,6 +606,25 @@ static mcmg_status setup_impl(mcmg_ctx c, const mcmg_medium* m, double omega,
             }
           pack_ts_rect(pm.data(), Cn, 16, tf, hr.data() + per2 * k);
         }
+        // and, for the line-staged kernel, three taps per stage: matrix k is
+        // [R_3k | R_3k+1 | R_3k+2] (o_x = -1, 0, +1 of stage (o_y, o_z) = k)
+        const int nst = T3 / 3;
+        const size_t per3 = (tf ? 2 * sizeof(float) : sizeof(uint16_t)) * (size_t)48 * (2 * Cn);
+        std::vector<unsigned char> h3(per3 * nst, 0);
+        std::vector<float2> tm((size_t)Cn * 24);
+        for (int k = 0; k < nst; ++k) {
+          for (int co = 0; co < Cn; ++co)
+            for (int ci = 0; ci < 24; ++ci) {
+              const int t = 3 * k + ci / 8;
+              const double* rs = lb[l].R + (size_t)2 * ((size_t)t * Cn * C + (size_t)co * C + ci % 8);
+              tm[(size_t)co * 24 + ci] = make_float2((float)rs[0], (float)rs[1]);
+            }
+          pack_ts_rect(tm.data(), Cn, 24, tf, h3.data() + per3 * k);
+        }
+        uint4* d3 = nullptr;
+        if ((s = dev_alloc(h, h->arena, (void**)&d3, h3.size()))) return cleanup(), s;
+        MCMG_CUDA(cudaMemcpyAsync(d3, h3.data(), h3.size(), cudaMemcpyHostToDevice, st));
+        lv.ts_R3 = d3;
       }
       for (int t = 0; t < T3; ++t) {
         const double* rs = lb[l].R + (size_t)2 * t * Cn * C;

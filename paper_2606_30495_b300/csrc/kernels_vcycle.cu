@@ -787,7 +787,9 @@ static constexpr int kNumTShapes = sizeof(kTShapes) / sizeof(kTShapes[0]);
 static constexpr int kXtsShape = kNumTShapes;
 // and, prolongation only, the block form of it (all parity classes at once)
 static constexpr int kXtsBlockShape = kNumTShapes + 1;
-static constexpr int kNumXShapes = kNumTShapes + 2;
+// and, restriction from 8 channels only, the line-staged form
+static constexpr int kXtsLineShape = kNumTShapes + 2;
+static constexpr int kNumXShapes = kNumTShapes + 3;
 
 // Register-tiled transfers are built for channel pairs (fine, coarse) with
 // the coarse count equal to or twice the fine one; other pairs use shape 0.
@@ -870,6 +872,7 @@ static bool xshape_ok(int s, const Level& L, bool restrict_) {
   if (s == 0) return true;
   if (s == kXtsShape) return xts_supported(L, restrict_);
   if (s == kXtsBlockShape) return !restrict_ && xts_block_supported(L);
+  if (s == kXtsLineShape) return restrict_ && xts_lines_supported(L);
   if (!xt_pair(L.C, L.Cn)) return false;
   const TShape& k = kTShapes[s];
   const int CI = restrict_ ? L.C : L.Cn, CO = restrict_ ? L.Cn : L.C;
@@ -881,6 +884,7 @@ static mcmg_status transfer_run(const Level& L, const TransferParams& p, bool re
                                 int nrhs, cudaStream_t st) {
   if (shape == kXtsShape) return launch_transfer_ts(L, restrict_, p.src, p.dst, nrhs, st);
   if (shape == kXtsBlockShape) return launch_prolong_block_ts(L, p.src, p.dst, nrhs, st);
+  if (shape == kXtsLineShape) return launch_restrict_lines_ts(L, p.src, p.dst, nrhs, st);
   if (shape > 0)
     return transfer_rt_launch(p, L.C, L.Cn, L.g.d, restrict_, kTShapes[shape].tn,
                               kTShapes[shape].cv, kTShapes[shape].kq, nrhs, st);

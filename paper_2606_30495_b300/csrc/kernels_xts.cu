@@ -27,6 +27,7 @@
 // (prolongation).  Every mbarrier
 // wait is bounded and the block votes on the outcome at its next barrier.
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 
 #include "mcmg_internal.cuh"
@@ -714,6 +715,335 @@ fail:
   }
 }
 
+// ---------------------------------------------------------------------------
+// Restriction from 8 channels with the fine lines staged in shared memory.
+//
+// The per-tap gather above reads, for one tap, every other fine node of a
+// line (64 bytes per lane at a 128-byte stride), so each warp load touches
+// 32 cache lines.  Here a stage is one (o_y, o_z): for each warp's 32 coarse
+// nodes J (consecutive along x, one coarse line) the fine nodes
+// 2 J_x0 - 1 .. 2 J_x0 + 63 of fine line (2 J_y + o_y, 2 J_z + o_z) are
+// staged in shared memory by coalesced 16-byte asynchronous copies that all
+// threads of the pipeline issue (zero-filled outside the grid), and the three
+// taps o_x = -1, 0, +1 are read from there by three thread groups (tap o_x in
+// group o_x + 1: fine node 2 J + o_x is slot 2 (J_x - J_x0) + o_x + 1 of the
+// segment).  A stage is K = 48 (three taps of 2 x 8) against
+// [R_(-1) | R_0 | R_(+1)] of its (o_y, o_z); all 3^(d-1) stage matrices stay
+// in shared memory for the whole kernel.  Two independent tile pipelines of
+// 384 threads share the CTA (and its 512 tensor-memory columns and the
+// weights), each with its own ring of staged stages, A slots, accumulators
+// and named barrier, so one pipeline's MMA and fold latency overlaps the
+// other's work.  Each stage sums into its own accumulator (stages alternate
+// between two) and the partials are added in FP32 registers, as in
+// k_transfer_ts; the fold of a tile's last stages and its store happen during
+// the next tile's first stages.
+// ---------------------------------------------------------------------------
+namespace xts {
+
+template <int KO, int D, int P>
+struct LineCfg {
+  static constexpr int KS = 48;                       // K of a stage: three taps of 2 x 8
+  static constexpr int S = D == 3 ? 9 : 3;            // stages (o_y, o_z) per tile
+  static constexpr int PIPES = 2;
+  static constexpr int PT = 384;                      // threads per pipeline: 3 taps x 4 warps
+  static constexpr int THREADS = PIPES * PT;
+  static constexpr int AW = P ? 2 * KS : KS / 2;      // A slot columns (TF32 hi + lo, or BF16 pairs)
+  static constexpr int COLS = 256;                    // tensor memory per pipeline
+  static constexpr int MATB = P ? 2 * KO * KS * 4 : KO * KS * 2;   // one stage's matrix
+  static constexpr int CH = 65 * 4;                   // 16-byte chunks of a warp's 65 fine nodes
+  static constexpr int SEGU = 33 * 8;                 // their 16-byte units in shared memory
+  static constexpr int DBUF = 4 * SEGU * 16;          // one staged stage: four warp segments
+  static constexpr int NBUF = 3;                      // staged stages per pipeline
+  static constexpr int LPT = (4 * CH + PT - 1) / PT;  // chunks one thread stages per stage
+  static constexpr int WBYTES = S * MATB;
+  static constexpr int SMEM = WBYTES + PIPES * NBUF * DBUF;
+  static_assert(2 * KO + 2 * AW <= COLS && SMEM <= 226 * 1024 && MATB % 16 == 0 &&
+                    WBYTES % 16 == 0,
+                "line restriction shape");
+};
+
+// 16-byte unit of chunk c of fine slot s in a staged segment: slots pair up
+// in 128-byte rows, and the half and the chunk are XOR-swizzled by the row,
+// so that the 8 lanes of a quarter warp reading slots 2 l + g (consecutive l)
+// reach 8 different bank groups
+__device__ __forceinline__ int line_unit(int s, int c) {
+  const int row = s >> 1;
+  return 8 * row + 4 * ((s & 1) ^ (row & 1)) + (c ^ ((row >> 1) & 3));
+}
+
+// AND of `v` over the `n` threads of named barrier `id` (a barrier for them)
+__device__ __forceinline__ bool bar_and(bool v, int id, int n) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
+// 16 bytes global -> shared, asynchronous; `bytes` 0 writes zeros
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes)
+               : "memory");
+}
+
+// one arrival on `bar` once this thread's earlier asynchronous copies have landed
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(tc::smem_u32(bar))
+               : "memory");
+}
+
+}  // namespace xts
+
+template <int KO, int D, int P>
+__global__ void __launch_bounds__(xts::LineCfg<KO, D, P>::THREADS, 1)
+    k_restrict_lines_ts(xts::XParams p) {
+  using G = xts::LineCfg<KO, D, P>;
+  constexpr int S = G::S, KS = G::KS, NBUF = G::NBUF, CO = KO / 2, LPT = G::LPT;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t wbar;
+  __shared__ uint64_t dfull[G::PIPES][NBUF];
+  __shared__ uint64_t abar[G::PIPES][2];
+  __shared__ uint32_t tmem_base_sh;
+  const int tid = threadIdx.x;
+  const int pi = tid / G::PT, lt = tid - pi * G::PT;
+  const int lw = lt >> 5, lanei = lt & 31;
+  const int g = lw >> 2;               // tap o_x = g - 1
+  const int ws = lw & 3;               // warp segment: rows 32 ws .. 32 ws + 31
+  const int row = 32 * ws + lanei;
+
+  if (tid == 0) {
+    tc::bar_init(&wbar, 1);
+    for (int q = 0; q < G::PIPES; ++q) {
+      for (int b = 0; b < NBUF; ++b) tc::bar_init(&dfull[q][b], G::PT);
+      tc::bar_init(&abar[q][0], 1);
+      tc::bar_init(&abar[q][1], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     tc::smem_u32(&tmem_base_sh)),
+                 "r"((uint32_t)(G::PIPES * G::COLS)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base_sh + (uint32_t)(pi * G::COLS);
+  const uint32_t lane = (uint32_t)(32 * ws) << 16;
+  const uint32_t slot0 = tmem + 2 * KO;          // A slots after the two accumulators
+  const uint32_t wts = tc::smem_u32(smem);
+  const int ring_off = G::WBYTES + pi * NBUF * G::DBUF;
+  if (tid == 0) {                                // the stage matrices, once
+    xts::expect_tx(&wbar, (uint32_t)G::WBYTES);
+    for (int st = 0; st < S; ++st)
+      xts::bulk_copy(wts + (uint32_t)(st * G::MATB),
+                     reinterpret_cast<const uint8_t*>(p.mats) + (size_t)st * G::MATB,
+                     (uint32_t)G::MATB, &wbar);
+  }
+  const int NV = G::PIPES * (int)gridDim.x;
+  const int vp = pi * (int)gridDim.x + (int)blockIdx.x;
+  const int my_items = vp < p.items ? (p.items - 1 - vp) / NV + 1 : 0;
+  const int Q = my_items * S;                    // stages of this pipeline
+  const long long cnodes = (long long)p.cx * p.cy * p.cz;
+  const int bar_id = 1 + pi;
+  bool ok = true;
+  uint32_t aph[2] = {0, 0};
+  int q_issued = 0, q_fail = -1, q_commit = -1;
+
+  // ---- staging: this thread copies chunks lt + PT k (k < LPT) of each
+  // stage's 4 x CH; per item it keeps, for each, the 16-byte index of the
+  // chunk at (o_y, o_z) = (0, 0) and flags: bit 0 its segment exists, bit 1
+  // J_y0 = 0, bit 2 J_z0 = 0, bit 3 its fine node is inside (x >= 0)
+  long long cbase[LPT];
+  int cflag[LPT];
+  int cache_kk = -1;
+  auto plan = [&](int kk) {
+    const int item = vp + kk * NV;
+    const int field = item / p.tiles, tile = item - field * p.tiles;
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      const int i = lt + G::PT * k;
+      const int w = i / G::CH, within = i - w * G::CH;
+      const int sl = within >> 2, c = within & 3;
+      const long long j0 = (long long)tile * xts::M + 32 * w;
+      cflag[k] = 0;
+      cbase[k] = 0;
+      if (i < 4 * G::CH && j0 < cnodes) {
+        int jx0, jy0, jz0;
+        node_xyz(j0, p.cx, p.cy, jx0, jy0, jz0);
+        const long long node =
+            ((long long)(2 * jz0) * p.fy + 2 * jy0) * p.fx + 2 * jx0 - 1 + sl;
+        cbase[k] = ((long long)field * p.src_nodes + node) * 4 + c;
+        cflag[k] = 1 | (jy0 == 0 ? 2 : 0) | (jz0 == 0 ? 4 : 0) | (jx0 > 0 || sl > 0 ? 8 : 0);
+      }
+    }
+    cache_kk = kk;
+  };
+  auto issue = [&](int q) {            // every thread: its chunks of stage q
+    const int kk = q / S, st = q - kk * S;
+    if (kk != cache_kk) plan(kk);
+    const int oy = st % 3 - 1, oz = D == 3 ? st / 3 - 1 : 0;
+    const long long delta = ((long long)oz * p.fy + oy) * p.fx * 4;
+    const int b = q % NBUF;
+    const uint32_t dst0 = wts + (uint32_t)(ring_off + b * G::DBUF);
+    const float4* src = reinterpret_cast<const float4*>(p.src);
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      const int i = lt + G::PT * k;
+      if (i < 4 * G::CH) {
+        const int w = i / G::CH, within = i - w * G::CH;
+        const uint32_t dst = dst0 + (uint32_t)(16 * (w * G::SEGU + xts::line_unit(within >> 2, within & 3)));
+        const int f = cflag[k];
+        const bool in = (f & 1) && (f & 8) && !(oy < 0 && (f & 2)) && !(oz < 0 && (f & 4));
+        xts::cp_async16(dst, in ? src + cbase[k] + delta : src, in ? 16u : 0u);
+      }
+    }
+    xts::cp_async_arrive(&dfull[pi][b]);
+  };
+  for (; q_issued < Q && q_issued < NBUF; ++q_issued) issue(q_issued);
+
+  // ---- per-thread sums of the stage partials (groups 0 and 1: columns
+  // 16 g .. 16 g + 15 of the KO outputs)
+  float acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+  auto fold = [&](int par) {
+    if (16 * g < KO) {
+      float dv[16];
+      tc::tmem_ld16(tmem + lane + (uint32_t)(par * KO + 16 * g), dv);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) acc[u] += dv[u];
+    }
+  };
+  auto store = [&](int kk) {            // the sums of this pipeline's item kk
+    const int item = vp + kk * NV;
+    const int field = item / p.tiles, tile = item - field * p.tiles;
+    const long long j = (long long)tile * xts::M + row;
+    if (16 * g < KO && j < cnodes) {
+      float4* op = reinterpret_cast<float4*>(p.dst + (size_t)field * (size_t)p.dst_nodes * CO +
+                                             (size_t)j * CO + 8 * g);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        op[u] = make_float4(acc[4 * u], acc[4 * u + 1], acc[4 * u + 2], acc[4 * u + 3]);
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+  };
+  auto retire = [&](int qd) {           // stage qd's MMAs are complete: fold, store at a tile's end
+    ok = tc::bar_wait(&abar[pi][qd & 1], aph[qd & 1], p.err) && ok;
+    aph[qd & 1] ^= 1;
+    tc::fence_after();
+    fold(qd & 1);
+    if (qd % S == S - 1) store(qd / S);
+  };
+  // the staged slot of this thread's A row: fine node 2 J + o_x
+  const int rslot = 2 * lanei + g;
+
+  // the pipeline leaves its loops only together, on a failed vote
+  for (int kk = 0; kk < my_items && q_fail < 0; ++kk) {
+    for (int st = 0; st < S; ++st) {
+      const int q = kk * S + st;
+      const int b = q % NBUF;
+      if (q >= 2) retire(q - 2);
+      ok = tc::bar_wait(&dfull[pi][b], (uint32_t)((q / NBUF) & 1), p.err) && ok;
+      const uint8_t* rp = smem + ring_off + b * G::DBUF + ws * (G::SEGU * 16);
+      float4 c4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        c4[u] = *reinterpret_cast<const float4*>(rp + 16 * xts::line_unit(rslot, u));
+      const uint32_t slot = slot0 + (uint32_t)((q & 1) * G::AW);
+      if constexpr (P == 1) {
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          const float x[8] = {c4[2 * hf].x, c4[2 * hf].y, c4[2 * hf].z, c4[2 * hf].w,
+                              c4[2 * hf + 1].x, c4[2 * hf + 1].y, c4[2 * hf + 1].z,
+                              c4[2 * hf + 1].w};
+          uint32_t hi[8], lo[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            hi[i] = tc::to_tf32(x[i]);
+            lo[i] = tc::to_tf32(x[i] - __uint_as_float(hi[i]));
+          }
+          tc::tmem_st8(slot + lane + (uint32_t)(16 * g + 8 * hf), hi);
+          tc::tmem_st8(slot + lane + (uint32_t)(KS + 16 * g + 8 * hf), lo);
+        }
+      } else {
+        uint32_t pk[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          pk[2 * i] = tc::pack_bf16(c4[i].x, c4[i].y);
+          pk[2 * i + 1] = tc::pack_bf16(c4[i].z, c4[i].w);
+        }
+        tc::tmem_st8(slot + lane + (uint32_t)(8 * g), pk);
+      }
+      tc::tmem_st_wait();
+      tc::fence_before();
+      ok = xts::bar_and(ok, bar_id, G::PT);
+      if (!ok) {
+        q_fail = q;
+        break;
+      }
+      // every thread of the pipeline has read buffer b: it takes stage q + NBUF
+      if (q_issued < Q) issue(q_issued++);
+      if (lt == 0) {
+        tc::fence_after();
+        if (q == 0 && !tc::bar_wait(&wbar, 0, p.err)) ok = false;
+        if (ok) {
+          const uint32_t d = tmem + (uint32_t)((q & 1) * KO);
+          const uint32_t bw = wts + (uint32_t)(st * G::MATB);
+          constexpr uint32_t lbo = KO * 16;
+          constexpr uint64_t kstep = (2 * lbo) >> 4;
+          if constexpr (P == 1) {
+            constexpr uint32_t idesc = tc::make_idesc_tf32(xts::M, KO);
+            const uint64_t bh0 = tc::make_desc(bw, lbo, 128);
+            const uint64_t bl0 = bh0 + ((KO * KS * 4) >> 4);
+#pragma unroll
+            for (int k8 = 0; k8 < KS / 8; ++k8) {
+              const uint32_t ahi = slot + 8 * k8, alo = slot + KS + 8 * k8;
+              tc::mma_tf32_ts(d, alo, bh0 + k8 * kstep, idesc, k8 > 0 ? 1u : 0u);
+              tc::mma_tf32_ts(d, ahi, bl0 + k8 * kstep, idesc, 1u);
+              tc::mma_tf32_ts(d, ahi, bh0 + k8 * kstep, idesc, 1u);
+            }
+          } else {
+            constexpr uint32_t idesc = tc::make_idesc(xts::M, KO);
+            const uint64_t b0 = tc::make_desc(bw, lbo, 128);
+#pragma unroll
+            for (int k16 = 0; k16 < KS / 16; ++k16)
+              tc::mma_bf16_ts(d, slot + 8 * k16, b0 + k16 * kstep, idesc, k16 > 0 ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(&abar[pi][q & 1]);
+        q_commit = q;
+      }
+    }
+  }
+  if (q_fail < 0) ok = xts::bar_and(ok, bar_id, G::PT);
+  if (q_fail < 0 && ok) {                // the last two stages
+    if (Q >= 2) retire(Q - 2);
+    if (Q >= 1) retire(Q - 1);
+    tc::fence_before();
+    ok = xts::bar_and(ok, bar_id, G::PT);
+  }
+  if (!ok) {
+    if (p.err && lt == 0) atomicOr(p.err, 1);
+    if (lt == 0 && q_commit >= 0)
+      tc::bar_wait(&abar[pi][q_commit & 1], (uint32_t)((q_commit >> 1) & 1), nullptr);
+    tc::fence_before();
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");   // this thread's copies have landed
+  if (tid == 0) tc::bar_wait(&wbar, 0, nullptr);       // and the weight copies
+  __syncthreads();
+  if (tid < 32) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem_base_sh),
+                 "r"((uint32_t)(G::PIPES * G::COLS)));
+  }
+}
+
 namespace {
 
 int xsm_count() {
@@ -880,6 +1210,71 @@ mcmg_status launch_prolong_block_ts(const Level& L, const float2* ec, float2* e,
   const bool d3 = L.g.d == 3, tf = L.ts_prec == MCMG_FP32_TC;
   if (tf) return d3 ? block_channels<3, 1>(L.Cn, L.C, p, nrhs, st) : block_channels<2, 1>(L.Cn, L.C, p, nrhs, st);
   return d3 ? block_channels<3, 0>(L.Cn, L.C, p, nrhs, st) : block_channels<2, 0>(L.Cn, L.C, p, nrhs, st);
+}
+
+// Line-staged restriction from 8 channels: C_n in {8, 16}, and a coarse x
+// extent that is a multiple of 32, so that each warp's 32 coarse nodes lie
+// on one coarse line.
+bool xts_lines_pair(int C, int Cn, int cx) {
+  return C == 8 && (Cn == 16 || Cn == 8) && cx >= 32 && cx % 32 == 0;
+}
+
+bool xts_lines_supported(const Level& L) {
+  return L.use_ts && L.ts_R3 && xts_lines_pair(L.C, L.Cn, L.g.coarse().nx);
+}
+
+namespace {
+template <int KO, int D, int P>
+mcmg_status lines_launch(xts::XParams p, int nrhs, cudaStream_t st) {
+  using G = xts::LineCfg<KO, D, P>;
+  auto kern = k_restrict_lines_ts<KO, D, P>;
+  static bool attr = false;
+  // one CTA per SM (it allocates all 512 tensor-memory columns)
+  const size_t smem = std::max((size_t)G::SMEM, (size_t)120 * 1024);
+  if (!attr) {
+    MCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    attr = true;
+  }
+  const long long cn = (long long)p.cx * p.cy * p.cz;
+  p.tiles = (int)((cn + xts::M - 1) / xts::M);
+  p.items = p.tiles * nrhs;
+  const int grid = std::min((p.items + G::PIPES - 1) / G::PIPES, xsm_count());
+  kern<<<grid, G::THREADS, smem, st>>>(p);
+  MCMG_CHECK_LAUNCH("restrict_lines_ts");
+  return MCMG_OK;
+}
+}  // namespace
+
+mcmg_status launch_restrict_lines_ts(const Level& L, const float2* src, float2* dst, int nrhs,
+                                     cudaStream_t st) {
+  if (!xts_lines_supported(L)) {
+    set_error("line-staged restriction not available on this level");
+    return MCMG_ERR_SHAPE;
+  }
+  // the bulk copies of the fine lines need a 16-byte aligned field
+  if (reinterpret_cast<uintptr_t>(src) % 16) return launch_transfer_ts(L, true, src, dst, nrhs, st);
+  const Grid gc = L.g.coarse();
+  xts::XParams p{};
+  p.src = src;
+  p.dst = dst;
+  p.mats = L.ts_R3;
+  p.fx = L.g.nx;
+  p.fy = L.g.ny;
+  p.fz = L.g.nz;
+  p.cx = gc.nx;
+  p.cy = gc.ny;
+  p.cz = gc.nz;
+  p.src_nodes = L.g.nodes();
+  p.dst_nodes = gc.nodes();
+  p.err = L.err;
+  const bool d3 = L.g.d == 3, tf = L.ts_prec == MCMG_FP32_TC;
+  if (L.Cn == 16) {
+    if (tf) return d3 ? lines_launch<32, 3, 1>(p, nrhs, st) : lines_launch<32, 2, 1>(p, nrhs, st);
+    return d3 ? lines_launch<32, 3, 0>(p, nrhs, st) : lines_launch<32, 2, 0>(p, nrhs, st);
+  }
+  if (tf) return d3 ? lines_launch<16, 3, 1>(p, nrhs, st) : lines_launch<16, 2, 1>(p, nrhs, st);
+  return d3 ? lines_launch<16, 3, 0>(p, nrhs, st) : lines_launch<16, 2, 0>(p, nrhs, st);
 }
 
 // Host: a complex Cout x Cin matrix M[co][ci] (float2, row-major) -> its real

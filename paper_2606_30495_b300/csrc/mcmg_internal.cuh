@@ -101,6 +101,9 @@ struct Level {
   // per coarse source offset s in {0,1}^d: the prolongation matrices of all
   // 2^d parity classes stacked (zero where a class does not read s)
   const uint4* ts_Pb = nullptr;
+  // restriction from 8 channels, per stage (o_y, o_z): [R_o | R_o' | R_o'']
+  // over o_x = -1, 0, +1 (Cn x 24), for the line-staged kernel
+  const uint4* ts_R3 = nullptr;
   // signatures of the arithmetic of one smoothing step (stencil, K_A, K_S,
   // W^(i)) and of the residual (stencil, K_A), with precision and C: launches
   // of different handles may be batched when these agree
@@ -166,6 +169,13 @@ bool xts_block_pair(int d, int Cn, int C);
 bool xts_block_supported(const Level& L);
 mcmg_status launch_prolong_block_ts(const Level& L, const float2* ec, float2* e, int nrhs,
                                     cudaStream_t st);
+// restriction from 8 channels with the fine lines staged in shared memory
+// (kernels_xts.cu): tensor-core levels with C = 8, C_n in {8, 16} and a
+// coarse x extent that is a multiple of 32
+bool xts_lines_pair(int C, int Cn, int cx);
+bool xts_lines_supported(const Level& L);
+mcmg_status launch_restrict_lines_ts(const Level& L, const float2* src, float2* dst, int nrhs,
+                                     cudaStream_t st);
 
 // Launchers used by the V-cycle (kernels_vcycle.cu), asynchronous on `st`.
 // mode 0: e_out = e_in + S^(step)(r - A e_in); mode 1: e_out = r - A e_in.

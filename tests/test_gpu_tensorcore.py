@@ -77,6 +77,8 @@ CASES = [
     ("bf16", (6, 10, 14), [32, 32], "random"),
     ("bf16", (16, 12), [64, 64], "random"),
     ("bf16", (4, 6, 8), [64, 64], "random"),
+    ("fp32tc", (6, 8, 64), [8, 16], "random"),     # coarse x extent 32: line-staged restriction
+    ("bf16", (20, 64), [8, 8], "random"),
 ]
 IDS = [f"{p}-{'x'.join(map(str, s))}-C{'-'.join(map(str, c))}-{m}" for p, s, c, m in CASES]
 
@@ -153,25 +155,34 @@ def _block_supported(d, C, Cn):
     return Cn in (16, 32, 64) and C in (Cn, Cn // 2) and (2 ** d) * 2 * C <= 256
 
 
+def _line_supported(C, Cn, cx):
+    """Line-staged restriction: from 8 channels to 8 or 16, coarse x extent a
+    multiple of 32 (each warp's 32 coarse nodes on one line)."""
+    return C == 8 and Cn in (8, 16) and cx >= 32 and cx % 32 == 0
+
+
 def test_transfer_every_shape(case):
     """Restriction R_l and prolongation P_l in every kernel shape, the
-    tensor-core ones (the last two shapes: per parity class, and the block
-    form of the prolongation) included where the level's channels allow
-    them, against the oracle; then V-cycles with the tensor-core transfers
-    forced on every level that has them."""
+    tensor-core ones (the last three shapes: per parity class, the block
+    form of the prolongation, the line-staged restriction from 8 channels)
+    included where the level allows them, against the oracle; then V-cycles
+    with the tensor-core transfers forced on every level that has them."""
     from paper_2606_30495_b300 import mcmg
     prec, m, h = case
     w = m["w"]
     L = w["levels"]
     tol = _tols(prec)[0]
-    # the last two shapes: the tensor-core transfer, then (prolongation only)
-    # its block form over all parity classes
-    xts = mcmg.kernel_shape_count(mcmg.OP_RESTRICT) - 2
+    # the last three shapes: the tensor-core transfer, then (prolongation
+    # only) its block form over all parity classes, then (restriction only)
+    # the line-staged form
+    xts = mcmg.kernel_shape_count(mcmg.OP_RESTRICT) - 3
     blk = xts + 1
-    assert blk == mcmg.kernel_shape_count(mcmg.OP_PROLONG) - 1
+    line = xts + 2
+    assert line == mcmg.kernel_shape_count(mcmg.OP_PROLONG) - 1
     d = len(m["shape"])
     ran_xts = 0
     ran_blk = 0
+    ran_line = 0
     try:
         for l in range(L - 1):
             C, Cn = w["channels"][l], w["channels"][l + 1]
@@ -193,6 +204,9 @@ def test_transfer_every_shape(case):
                     if sh == blk:
                         assert ran == (op == mcmg.OP_PROLONG and _block_supported(d, C, Cn)
                                        and prec in ("fp32tc", "bf16")), (l, op, C, Cn)
+                    if sh == line:
+                        assert ran == (op == mcmg.OP_RESTRICT and _line_supported(C, Cn, cshp[-1])
+                                       and prec in ("fp32tc", "bf16")), (l, op, C, Cn)
                     if not ran:
                         continue
                     if op == mcmg.OP_RESTRICT:
@@ -206,6 +220,7 @@ def test_transfer_every_shape(case):
                     assert relerr(got, want) < tol, (l, op, sh)
                     ran_xts += sh == xts
                     ran_blk += sh == blk
+                    ran_line += sh == line
                 h.set_kernel_shape(l, op, -1)
         if any(_xts_supported(w["channels"][l], w["channels"][l + 1], rr)
                for l in range(L - 1) for rr in (True, False)):
@@ -213,8 +228,12 @@ def test_transfer_every_shape(case):
             if any(_block_supported(d, w["channels"][l], w["channels"][l + 1])
                    for l in range(L - 1)):
                 assert ran_blk > 0
+            if any(_line_supported(w["channels"][l], w["channels"][l + 1],
+                                   m["shape"][-1] >> (l + 1)) for l in range(L - 1)):
+                assert ran_line > 0
             for l in range(L - 1):
-                h.set_kernel_shape(l, mcmg.OP_RESTRICT, xts)   # False where not available
+                if not h.set_kernel_shape(l, mcmg.OP_RESTRICT, line):
+                    h.set_kernel_shape(l, mcmg.OP_RESTRICT, xts)   # False where not available
                 if not h.set_kernel_shape(l, mcmg.OP_PROLONG, blk):
                     h.set_kernel_shape(l, mcmg.OP_PROLONG, xts)
             rv = I.complex_normal((2,) + m["shape"], rng(73))
@@ -237,6 +256,10 @@ def test_transfer_every_shape(case):
     ("fp32tc", (62, 48, 40), [64, 64]),     # four K parts per tap (TF32)
     ("fp32tc", (500, 330), [16, 32]),       # 2D: 322.3 tiles, 4 classes
     ("bf16", (500, 330), [16, 16]),
+    ("fp32tc", (70, 78, 64), [8, 16]),      # line-staged: 341.25 tiles, cx = 32
+    ("fp32tc", (42, 40, 192), [8, 8]),      # line-staged: 315 tiles, three warps' lines per tile
+    ("bf16", (702, 128), [8, 16]),          # line-staged 2D: 175.5 tiles
+    ("fp32tc", (700, 256), [8, 16]),        # line-staged 2D: 350 tiles, a tile per coarse line
 ])
 def test_transfer_ts_many_items(ctx, prec, shape, channels):
     """The tensor-core transfers with more items than CTAs (each persistent
@@ -251,24 +274,29 @@ def test_transfer_ts_many_items(ctx, prec, shape, channels):
     c = I.grf(shape, 4.0, 1.0, 3.0, rng(109))
     omega = I.omega_for_ppw(c.min(), 8.0, shape[0])
     h = mcmg.Handle(ctx, c, omega, 4, 1.0, w, precision=_prec(prec))
-    xts = mcmg.kernel_shape_count(mcmg.OP_RESTRICT) - 2
+    xts = mcmg.kernel_shape_count(mcmg.OP_RESTRICT) - 3
     try:
         C, Cn = channels
         lv = w["lvl"][0]
         cshp = tuple(n >> 1 for n in shape)
         tol = _tols(prec)[0]
-        if _xts_supported(C, Cn, True):
-            assert h.set_kernel_shape(0, mcmg.OP_RESTRICT, xts)
+        rshapes = ([xts] if _xts_supported(C, Cn, True) else []) + \
+            ([xts + 2] if _line_supported(C, Cn, cshp[-1]) else [])
+        if rshapes:
             r = I.complex_normal((2,) + shape + (C,), rng(80))
-            rc = torch.zeros((2,) + cshp + (Cn,), dtype=torch.complex64, device="cuda")
+            want = np.stack([O.restrict(lv["R"], r[k]) for k in range(2)])
+        for sh in rshapes:
+            assert h.set_kernel_shape(0, mcmg.OP_RESTRICT, sh)
+            rc = torch.full((2,) + cshp + (Cn,), float("nan"), dtype=torch.complex64,
+                            device="cuda")
             h.residual_restrict(0, dev(r), torch.zeros(r.shape, dtype=torch.complex64,
                                                        device="cuda"), rc, nrhs=2)
-            want = np.stack([O.restrict(lv["R"], r[k]) for k in range(2)])
-            assert relerr(host(rc), want) < tol
+            assert relerr(host(rc), want) < tol, sh
         ec = I.complex_normal((2,) + cshp + (Cn,), rng(81))
         e = I.complex_normal((2,) + shape + (C,), rng(82))
         want = np.stack([e[k] + O.prolong(lv["P"], ec[k], shape) for k in range(2)])
-        shapes = [xts] + ([xts + 1] if _block_supported(d, C, Cn) else [])
+        shapes = ([xts] if _xts_supported(C, Cn, False) else []) + \
+            ([xts + 1] if _block_supported(d, C, Cn) else [])
         for sh in shapes:
             assert h.set_kernel_shape(0, mcmg.OP_PROLONG, sh)
             ef = dev(e)
