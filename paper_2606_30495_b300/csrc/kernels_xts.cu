@@ -24,8 +24,12 @@
 // asynchronous copies that thread 32 issues; thread 0 issues the MMAs.  Each
 // tap accumulates apart and the tap partials are summed in FP32 registers;
 // the epilogue stores the sum (restriction) or adds it to the fine field
-// (prolongation).  Every mbarrier
-// wait is bounded and the block votes on the outcome at its next barrier.
+// (prolongation).  Every mbarrier wait is bounded and the block votes on the
+// outcome at its next barrier.
+//
+// Further below: the prolongation in block form (all parity classes of a
+// coarse tile in one MMA group) and the restriction from 8 channels with the
+// fine lines staged in shared memory.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
