@@ -77,9 +77,11 @@ def parse():
                         "iterations inside the NVTX range 'solve' (ncu --nvtx --nvtx-include "
                         "'solve/'), then exit")
     p.add_argument("--profile-launch", default="",
-                   help="LEVEL,KIND[,REPS]: after setup, run only that launch class of the "
-                        "V-cycle (KIND first | step | residual | restrict | prolong) REPS times "
-                        "(default 5) and exit; for profilers")
+                   help="LEVEL,KIND[,REPS[,SHAPE]]: after setup, run only that launch class "
+                        "of the V-cycle (KIND first | step | residual | restrict | prolong; "
+                        "restrict is the residual followed by the restriction) once untimed "
+                        "and REPS times (default 5) timed, in kernel shape SHAPE (default: "
+                        "setup's choice), and exit; for profilers")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-iters", type=int, default=3)
     p.add_argument("--n", type=int, default=0,
@@ -367,6 +369,11 @@ def profile_launch(args, h, wl, torch, mcmg, ctx):
     parts = args.profile_launch.split(",")
     level, kind = int(parts[0]), parts[1]
     reps = int(parts[2]) if len(parts) > 2 else 5
+    shape = int(parts[3]) if len(parts) > 3 else -1
+    op = {"first": mcmg.OP_SMOOTH, "step": mcmg.OP_SMOOTH, "residual": mcmg.OP_RESIDUAL,
+          "restrict": mcmg.OP_RESTRICT, "prolong": mcmg.OP_PROLONG}[kind]
+    if shape >= 0 and not h.set_kernel_shape(level, op, shape):
+        raise SystemExit(f"kernel shape {shape} cannot run {kind} on level {level}")
     C = wl["channels"][level]
     shp = tuple(n >> level for n in (wl["n"],) * wl["dim"]) + (C,)
     r = torch.randn(shp, dtype=torch.complex64, device="cuda")
@@ -386,6 +393,7 @@ def profile_launch(args, h, wl, torch, mcmg, ctx):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
+        run()                                    # untimed: first-call allocations
         e0.record(stream)
         for _ in range(reps):
             run()
@@ -393,6 +401,7 @@ def profile_launch(args, h, wl, torch, mcmg, ctx):
     e1.synchronize()
     print(json.dumps({"profile_launch": {"workload": args.workload, "precision": wl["precision"],
                                          "level": level, "kind": kind, "C": C,
+                                         "shape": h.kernel_shape(level, op),
                                          "nodes": math.prod(shp[:-1]), "reps": reps,
                                          "us": e0.elapsed_time(e1) * 1e3 / reps}}))
     h.close()
